@@ -1,0 +1,172 @@
+/*
+ * dm.h -- C ABI of libdm: partitioned distance maps for fast transfer-function updates of
+ * distance-map empty-space skipping (Rauter, Zimmermann & Zeilinger, IEEE VIS 2024).
+ *
+ * The method (§3.1): cut the intensity range into K partitions; once per volume build one
+ * block-reduced occupancy map (POM) per partition and its Chebyshev distance map (PDM);
+ * on every TF change, (step 1) find the set S of partitions holding an intensity with
+ * non-zero alpha and (step 2, Eq. 1) take the element-wise min of the PDMs in S.  The
+ * plain full recompute it replaces (occupancy of the TF, then a fresh distance transform,
+ * as in Deakin & Knackstedt, §2) is provided next to it.
+ *
+ * Conventions shared by every call
+ *  - The library allocates no device memory.  The caller allocates every device buffer,
+ *    sized by dm_query_sizes(), and hands them over with dm_bind(); the library keeps only
+ *    the pointers.  Buffers stay owned by the caller and must outlive their use.
+ *  - Device pointers are plain CUDA device addresses; `stream` is a cudaStream_t (NULL =
+ *    the legacy default stream).  Work is enqueued on `stream` and the calls return
+ *    without waiting for it, except dm_update_tf_host() and dm_sync(), which wait.
+ *  - Every call returns a dm_status.  On DM_ERR_* nothing was enqueued by that call, except
+ *    DM_ERR_CUDA, which can also report a failure of earlier asynchronous work (a sticky
+ *    CUDA error).  dm_last_error_string() gives a one-line reason.  No C++ exception
+ *    crosses this interface.
+ *  - A context is not thread-safe: use it from one host thread / stream at a time.
+ *  - Layouts: the volume is [Z][Y][X], x fastest, uint8 or uint16.  The block grid is
+ *    Gx = ceil(X/b), Gy = ceil(Y/b), Gz = ceil(Z/b), G = Gx*Gy*Gz, stored [Gz][Gy][Gx].
+ *    Distance maps are uint8 [Gz][Gy][Gx]; the K PDMs are planar, plane p at byte offset
+ *    p * plane_stride (plane_stride = G rounded up to 64 bytes).  Distances are in block
+ *    units, 0 on occupied blocks, clamped to 255, and 255 for an empty map (§3.2).
+ */
+#ifndef DM_H
+#define DM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dm_status;
+#define DM_OK 0
+#define DM_ERR_INVALID_ARG 1   /* null / misaligned pointer, bad size or value */
+#define DM_ERR_UNSUPPORTED 2   /* valid but outside what this build handles */
+#define DM_ERR_CUDA 3          /* a CUDA launch or an earlier asynchronous CUDA error */
+#define DM_ERR_NOT_BOUND 4     /* buffers not bound with dm_bind() */
+
+#define DM_U8 1                /* dtype: bytes per voxel */
+#define DM_U16 2
+
+#define DM_OCC_MINMAX 0        /* full recompute: block min/max occupancy (default) */
+#define DM_OCC_EXACT 1         /* full recompute: per-voxel occupancy (re-reads volume) */
+
+#define DM_MAX_PARTITIONS 256
+#define DM_MAX_TF_SIZE 65536
+#define DM_MAX_BLOCK 16
+
+typedef struct dm_ctx dm_ctx;
+
+typedef struct dm_config {
+    int32_t dims[3];          /* X, Y, Z in voxels, each >= 1 */
+    int32_t dtype;            /* DM_U8 or DM_U16 */
+    int32_t block;            /* b, the block edge in voxels, 1..DM_MAX_BLOCK (paper: 4) */
+    int32_t apron;            /* voxels of interpolation apron added on every side of a
+                                 block's footprint (clipped at the volume), 0..block */
+    int32_t num_partitions;   /* K (the paper's n), 1..DM_MAX_PARTITIONS, K <= tf_size */
+    const int32_t *borders;   /* host, K+1 strictly increasing lower borders with
+                                 borders[0] = 0 and borders[K] = tf_size; partition p is
+                                 [borders[p], borders[p+1]-1].  NULL = uniform:
+                                 borders[p] = floor(p * tf_size / K).  Copied at create. */
+    int32_t tf_size;          /* N, entries of the 1D TF, 2..DM_MAX_TF_SIZE; entry i maps
+                                 intensity i; voxels >= N are treated as N-1 */
+    int32_t occ_mode;         /* DM_OCC_MINMAX or DM_OCC_EXACT, for dm_full_recompute */
+} dm_config;
+
+typedef struct dm_sizes {
+    size_t mask_bytes;        /* POM bit masks: G * ceil(K/64) uint64 words */
+    size_t pdm_bytes;         /* K * plane_stride; equals K*G (§5) when G % 64 == 0 */
+    size_t plane_stride;      /* bytes between PDM planes */
+    size_t minmax_bytes;      /* block footprint min/max: G pairs of the voxel type */
+    size_t scratch_bytes;     /* small per-context working memory */
+    size_t out_bytes;         /* one distance map: G */
+    int32_t grid[3];          /* Gx, Gy, Gz */
+    int32_t mask_words;       /* ceil(K/64) */
+} dm_sizes;
+
+/*
+ * Validate `cfg` and create a context (host memory only).  Returns DM_ERR_INVALID_ARG for
+ * a malformed config and DM_ERR_UNSUPPORTED for limits of this build.  *out is set only
+ * on DM_OK.  Partition borders: §3.1 (integer borders rho_min^p, rho_max^p; uniform split
+ * or not, e.g. a separate partition for the minimum intensity).
+ */
+dm_status dm_create(dm_ctx **out, const dm_config *cfg);
+
+/* Sizes of every buffer the caller must allocate for this context (host only). */
+dm_status dm_query_sizes(const dm_ctx *ctx, dm_sizes *out);
+
+/*
+ * Bind caller-owned device buffers: d_mask (mask_bytes, 16-byte aligned), d_pdm
+ * (pdm_bytes, 16-byte aligned), d_minmax (minmax_bytes, 16-byte aligned; may be NULL if
+ * the full recompute is never used in DM_OCC_MINMAX mode), d_scratch (scratch_bytes,
+ * 256-byte aligned).  d_mask is only written and read by dm_build_partitions (the POMs are
+ * an intermediate, §5) and may be released afterwards by binding NULL.  Rebinding is
+ * allowed between calls.
+ */
+dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *d_scratch);
+
+/*
+ * One-time precompute (§3.1, "one-time initialization step"): from the device volume
+ * (dims / dtype of the config) build the partition table, the K POMs as per-block bit
+ * masks over each block's footprint (b^3 voxels plus the apron), the block min/max (if
+ * d_minmax is bound), and the K PDMs as Chebyshev distance transforms of the POMs,
+ * clamped to uint8 (§3.2).  Asynchronous on `stream`.
+ */
+dm_status dm_build_partitions(dm_ctx *ctx, const void *d_volume, void *stream);
+
+/*
+ * Per-TF update (§3.1 steps 1 and 2, Eq. 1).  d_tf_rgba: device float32 [N][4] (RGBA);
+ * a partition is active when one of its intensities has alpha > 0.0f (NaN is not).
+ * d_out: device uint8 [G], D' = min over active p of PDM_p, 255 where no partition is
+ * active.  d_active_mask_out: optional device uint64 [ceil(K/64)] receiving S as a bit
+ * set.  Reads the PDMs built by dm_build_partitions.  Asynchronous; no host round trip.
+ */
+dm_status dm_update_tf(dm_ctx *ctx, const float *d_tf_rgba, uint8_t *d_out,
+                       uint64_t *d_active_mask_out, void *stream);
+
+/*
+ * The same update with HOST buffers: copies h_tf_rgba (float32 [N][4]) to the device,
+ * runs dm_update_tf into the context's scratch, copies D' back into h_out (uint8 [G]) and
+ * waits for `stream`.  Pinned host memory gives asynchronous copies; pageable works.
+ */
+dm_status dm_update_tf_host(dm_ctx *ctx, const float *h_tf_rgba, uint8_t *h_out,
+                            void *stream);
+
+/*
+ * The plain full recompute that the method replaces (§2 Deakin & Knackstedt; compared in
+ * Table 1): occupancy of the TF per block, then a fresh Chebyshev distance transform,
+ * clamped to 255.  DM_OCC_MINMAX: a block is occupied when one intensity in [min, max]
+ * of its footprint has alpha > 0 (Krueger & Westermann min/max blocks, §2); needs the
+ * min/max built by dm_build_partitions.  DM_OCC_EXACT: a block is occupied when one voxel
+ * of its footprint has alpha > 0; re-reads d_volume (ignored in DM_OCC_MINMAX mode).
+ * d_out: device uint8 [G].  Asynchronous.
+ */
+dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf_rgba,
+                            uint8_t *d_out, void *stream);
+
+/*
+ * Instrumentation: when set, dm_update_tf() records `ev_begin` on its stream right before
+ * the combine kernel (Eq. 1) is launched and `ev_end` right after it, so a caller can time
+ * that kernel alone with cudaEventElapsedTime.  Both are cudaEvent_t created by the caller
+ * (owned by the caller); pass NULL, NULL to stop.  No effect on results.
+ */
+dm_status dm_set_profile_events(dm_ctx *ctx, void *ev_begin, void *ev_end);
+
+/* Wait for `stream` and report any asynchronous CUDA error as DM_ERR_CUDA. */
+dm_status dm_sync(dm_ctx *ctx, void *stream);
+
+/* Free the context (host memory only; bound buffers stay with the caller).  NULL is ok. */
+void dm_destroy(dm_ctx *ctx);
+
+/* One-line reason for the context's last error ("" if none); valid until the next call. */
+const char *dm_last_error_string(const dm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *dm_status_string(dm_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t dm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DM_H */

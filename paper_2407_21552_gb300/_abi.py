@@ -1,0 +1,188 @@
+"""ctypes binding of libdm's C ABI (include/dm.h): same names, argument marshalling only.
+
+Loading fails loudly when libdm.so has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdm.so")
+
+DM_OK = 0
+DM_ERR_INVALID_ARG = 1
+DM_ERR_UNSUPPORTED = 2
+DM_ERR_CUDA = 3
+DM_ERR_NOT_BOUND = 4
+DM_U8 = 1
+DM_U16 = 2
+DM_OCC_MINMAX = 0
+DM_OCC_EXACT = 1
+DM_MAX_PARTITIONS = 256
+DM_MAX_TF_SIZE = 65536
+DM_MAX_BLOCK = 16
+
+#: every function declared in include/dm.h
+EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
+            "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events", "dm_sync",
+            "dm_destroy",
+            "dm_last_error_string", "dm_status_string", "dm_version")
+
+
+class dm_config(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("dtype", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("apron", ctypes.c_int32),
+                ("num_partitions", ctypes.c_int32), ("borders", ctypes.POINTER(ctypes.c_int32)),
+                ("tf_size", ctypes.c_int32), ("occ_mode", ctypes.c_int32)]
+
+
+class dm_sizes(ctypes.Structure):
+    _fields_ = [("mask_bytes", ctypes.c_size_t), ("pdm_bytes", ctypes.c_size_t),
+                ("plane_stride", ctypes.c_size_t), ("minmax_bytes", ctypes.c_size_t),
+                ("scratch_bytes", ctypes.c_size_t), ("out_bytes", ctypes.c_size_t),
+                ("grid", ctypes.c_int32 * 3), ("mask_words", ctypes.c_int32)]
+
+
+class DmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_name(status)}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdm.so (build it first with paper_2407_21552_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdm.so not found at {path}: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    S = ctypes.c_int32
+    lib.dm_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(dm_config)]
+    lib.dm_query_sizes.argtypes = [P, ctypes.POINTER(dm_sizes)]
+    lib.dm_bind.argtypes = [P, P, P, P, P]
+    lib.dm_build_partitions.argtypes = [P, P, P]
+    lib.dm_update_tf.argtypes = [P, P, P, P, P]
+    lib.dm_update_tf_host.argtypes = [P, P, P, P]
+    lib.dm_full_recompute.argtypes = [P, P, P, P, P]
+    lib.dm_set_profile_events.argtypes = [P, P, P]
+    lib.dm_sync.argtypes = [P, P]
+    lib.dm_destroy.argtypes = [P]
+    lib.dm_destroy.restype = None
+    lib.dm_last_error_string.argtypes = [P]
+    lib.dm_last_error_string.restype = ctypes.c_char_p
+    lib.dm_status_string.argtypes = [S]
+    lib.dm_status_string.restype = ctypes.c_char_p
+    lib.dm_version.argtypes = []
+    for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
+              "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events", "dm_sync",
+              "dm_version"):
+        getattr(lib, n).restype = S
+    _lib = lib
+    return lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return load().dm_status_string(int(s)).decode()
+    except ImportError:
+        return str(s)
+
+
+def _check(ctx, status, where):
+    if status != DM_OK:
+        detail = load().dm_last_error_string(ctx).decode() if ctx else ""
+        raise DmError(status, where, detail)
+
+
+# ---------------------------------------------------------------- same-name wrappers
+def make_config(dims, dtype, block=4, apron=1, num_partitions=16, tf_size=256, borders=None,
+                occ_mode=DM_OCC_MINMAX):
+    cfg = dm_config()
+    cfg.dims[:] = [int(d) for d in dims]
+    cfg.dtype = int(dtype)
+    cfg.block = int(block)
+    cfg.apron = int(apron)
+    cfg.num_partitions = int(num_partitions)
+    cfg.tf_size = int(tf_size)
+    cfg.occ_mode = int(occ_mode)
+    keep = None
+    if borders is not None:
+        keep = (ctypes.c_int32 * len(borders))(*[int(v) for v in borders])
+        cfg.borders = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int32))
+    return cfg, keep
+
+
+def dm_create(cfg: dm_config):
+    """Returns the opaque context handle (int); raises DmError on a non-OK status."""
+    h = ctypes.c_void_p()
+    _check(None, load().dm_create(ctypes.byref(h), ctypes.byref(cfg)), "dm_create")
+    return h.value
+
+
+def dm_create_status(cfg: dm_config) -> int:
+    """dm_create returning the raw status (the context, if any, is destroyed)."""
+    h = ctypes.c_void_p()
+    s = load().dm_create(ctypes.byref(h), ctypes.byref(cfg))
+    if s == DM_OK:
+        load().dm_destroy(h)
+    return s
+
+
+def dm_query_sizes(ctx) -> dm_sizes:
+    s = dm_sizes()
+    _check(ctx, load().dm_query_sizes(ctx, ctypes.byref(s)), "dm_query_sizes")
+    return s
+
+
+def dm_bind(ctx, d_mask, d_pdm, d_minmax, d_scratch):
+    _check(ctx, load().dm_bind(ctx, d_mask, d_pdm, d_minmax, d_scratch), "dm_bind")
+
+
+def dm_build_partitions(ctx, d_volume, stream):
+    _check(ctx, load().dm_build_partitions(ctx, d_volume, stream), "dm_build_partitions")
+
+
+def dm_update_tf(ctx, d_tf_rgba, d_out, d_active_mask_out, stream):
+    _check(ctx, load().dm_update_tf(ctx, d_tf_rgba, d_out, d_active_mask_out, stream),
+           "dm_update_tf")
+
+
+def dm_update_tf_host(ctx, h_tf_rgba, h_out, stream):
+    _check(ctx, load().dm_update_tf_host(ctx, h_tf_rgba, h_out, stream), "dm_update_tf_host")
+
+
+def dm_full_recompute(ctx, d_volume, d_tf_rgba, d_out, stream):
+    _check(ctx, load().dm_full_recompute(ctx, d_volume, d_tf_rgba, d_out, stream),
+           "dm_full_recompute")
+
+
+def dm_set_profile_events(ctx, ev_begin, ev_end):
+    _check(ctx, load().dm_set_profile_events(ctx, ev_begin, ev_end), "dm_set_profile_events")
+
+
+def dm_sync(ctx, stream):
+    _check(ctx, load().dm_sync(ctx, stream), "dm_sync")
+
+
+def dm_destroy(ctx):
+    if ctx:
+        load().dm_destroy(ctx)
+
+
+def dm_last_error_string(ctx) -> str:
+    return load().dm_last_error_string(ctx).decode()
+
+
+def dm_status_string(s: int) -> str:
+    return load().dm_status_string(int(s)).decode()
+
+
+def dm_version() -> int:
+    return int(load().dm_version())

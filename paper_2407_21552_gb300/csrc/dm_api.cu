@@ -1,0 +1,361 @@
+// dm_api.cu -- the C ABI of libdm (declared in include/dm.h).
+//
+// Host-side validation, buffer bookkeeping and launch sequencing.  Every step of the
+// method runs in the kernels of dm_footprint.cu, dm_dt.cu and dm_update.cu; this file only
+// checks arguments, lays out the caller's scratch buffer and enqueues work on the caller's
+// stream.  No device memory is allocated here.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/dm.h"
+#include "dm_internal.cuh"
+
+struct dm_ctx {
+    dm_config cfg;
+    dmk::Borders borders;
+    dmk::Geometry geo;
+    dm_sizes sizes;
+    int W;
+    int num_sms;
+    // scratch layout (byte offsets)
+    size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_tf, off_out;
+    void* d_mask;
+    void* d_pdm;
+    void* d_minmax;
+    void* d_scratch;
+    bool built;
+    bool minmax_built;
+    cudaEvent_t ev_begin, ev_end;   // optional, caller-owned (dm_set_profile_events)
+    char err[256];
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+dm_status fail(dm_ctx* c, dm_status s, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+dm_status cuda_fail(dm_ctx* c, cudaError_t e, const char* where)
+{
+    return fail(c, DM_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// Report an earlier asynchronous error without clearing it from a healthy context.
+dm_status check_sticky(dm_ctx* c, const char* where)
+{
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, where);
+    }
+    return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dm_version(void) { return 10000; }
+
+const char* dm_status_string(dm_status s)
+{
+    switch (s) {
+    case DM_OK: return "DM_OK";
+    case DM_ERR_INVALID_ARG: return "DM_ERR_INVALID_ARG";
+    case DM_ERR_UNSUPPORTED: return "DM_ERR_UNSUPPORTED";
+    case DM_ERR_CUDA: return "DM_ERR_CUDA";
+    case DM_ERR_NOT_BOUND: return "DM_ERR_NOT_BOUND";
+    default: return "DM_ERR_UNKNOWN";
+    }
+}
+
+const char* dm_last_error_string(const dm_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+dm_status dm_create(dm_ctx** out, const dm_config* cfg)
+{
+    if (!out || !cfg) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    const dm_config& c = *cfg;
+    for (int i = 0; i < 3; ++i)
+        if (c.dims[i] < 1) return DM_ERR_INVALID_ARG;
+    if (c.dtype != DM_U8 && c.dtype != DM_U16) return DM_ERR_INVALID_ARG;
+    if (c.block < 1 || c.apron < 0) return DM_ERR_INVALID_ARG;
+    if (c.block > DM_MAX_BLOCK || c.apron > c.block) return DM_ERR_UNSUPPORTED;
+    if (c.num_partitions < 1 || c.tf_size < 2) return DM_ERR_INVALID_ARG;
+    if (c.num_partitions > DM_MAX_PARTITIONS || c.tf_size > DM_MAX_TF_SIZE)
+        return DM_ERR_UNSUPPORTED;
+    if (c.num_partitions > c.tf_size) return DM_ERR_INVALID_ARG;
+    if (c.occ_mode != DM_OCC_MINMAX && c.occ_mode != DM_OCC_EXACT) return DM_ERR_INVALID_ARG;
+    const int K = c.num_partitions, N = c.tf_size;
+    if (c.borders) {
+        if (c.borders[0] != 0 || c.borders[K] != N) return DM_ERR_INVALID_ARG;
+        for (int p = 0; p < K; ++p)
+            if (c.borders[p + 1] <= c.borders[p]) return DM_ERR_INVALID_ARG;
+    }
+    dm_ctx* x = new (std::nothrow) dm_ctx();
+    if (!x) return DM_ERR_INVALID_ARG;
+    x->cfg = c;
+    x->cfg.borders = nullptr;
+    for (int p = 0; p <= K; ++p)
+        x->borders.v[p] = c.borders ? c.borders[p] : int32_t((int64_t(p) * N) / K);
+    for (int p = K + 1; p <= dmk::kMaxPartitions; ++p) x->borders.v[p] = N;
+    dmk::Geometry& g = x->geo;
+    g.X = c.dims[0];
+    g.Y = c.dims[1];
+    g.Z = c.dims[2];
+    g.b = c.block;
+    g.a = c.apron;
+    g.bpv = c.dtype;
+    g.gx = (g.X + g.b - 1) / g.b;
+    g.gy = (g.Y + g.b - 1) / g.b;
+    g.gz = (g.Z + g.b - 1) / g.b;
+    g.G = int64_t(g.gx) * g.gy * g.gz;
+    g.plane = int64_t(align_up(size_t(g.G), 64));
+    x->W = (K + 63) / 64;
+    // limits of the kernels' tilings
+    const int nw = (g.gx + 31) / 32;
+    if (size_t(K) * nw * 4 > size_t(dmk::kXpassSmemLimit) ||
+        dmk::line_pass_smem(g.gy) > size_t(dmk::kLineSmemLimit) ||
+        dmk::line_pass_smem(g.gz) > size_t(dmk::kLineSmemLimit) || g.gz > 65535 ||
+        g.gy > 65535) {
+        delete x;
+        return DM_ERR_UNSUPPORTED;
+    }
+    dm_sizes& s = x->sizes;
+    s.mask_bytes = size_t(g.G) * x->W * 8;
+    s.plane_stride = size_t(g.plane);
+    s.pdm_bytes = size_t(K) * s.plane_stride;
+    s.minmax_bytes = size_t(g.G) * 2 * g.bpv;
+    s.out_bytes = size_t(g.G);
+    s.grid[0] = g.gx;
+    s.grid[1] = g.gy;
+    s.grid[2] = g.gz;
+    s.mask_words = x->W;
+    size_t o = 0;
+    x->off_lut = o;   o = align_up(o + size_t(N), 256);
+    x->off_cnt = o;   o = align_up(o + size_t(N + 1) * 4, 256);
+    x->off_act = o;   o = align_up(o + size_t(dmk::kMaxPartitions) * 2, 256);
+    x->off_nact = o;  o = align_up(o + 64, 64);
+    x->off_smask = o; o = align_up(o + 64, 256);
+    x->off_tf = o;    o = align_up(o + size_t(N) * 16, 256);
+    x->off_out = o;   o = align_up(o + size_t(g.G), 256);
+    s.scratch_bytes = o;
+    int dev = 0;
+    x->num_sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            x->num_sms = n;
+    }
+    cudaGetLastError();   // no GPU is not an error at create time
+    x->err[0] = 0;
+    *out = x;
+    return DM_OK;
+}
+
+dm_status dm_query_sizes(const dm_ctx* ctx, dm_sizes* out)
+{
+    if (!ctx || !out) return DM_ERR_INVALID_ARG;
+    *out = ctx->sizes;
+    return DM_OK;
+}
+
+dm_status dm_bind(dm_ctx* ctx, void* d_mask, void* d_pdm, void* d_minmax, void* d_scratch)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if ((d_mask && !aligned(d_mask, 16)) || (d_pdm && !aligned(d_pdm, 16)) ||
+        (d_minmax && !aligned(d_minmax, 16)) || (d_scratch && !aligned(d_scratch, 256)))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_bind: misaligned buffer (mask/pdm/minmax need "
+                    "16 bytes, scratch 256)");
+    if (d_pdm != ctx->d_pdm) ctx->built = false;
+    if (d_minmax != ctx->d_minmax) ctx->minmax_built = false;
+    ctx->d_mask = d_mask;
+    ctx->d_pdm = d_pdm;
+    ctx->d_minmax = d_minmax;
+    ctx->d_scratch = d_scratch;
+    ctx->err[0] = 0;
+    return DM_OK;
+}
+
+dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!d_volume || !aligned(d_volume, size_t(ctx->geo.bpv)))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_build_partitions: null or misaligned volume");
+    if (!ctx->d_mask || !ctx->d_pdm || !ctx->d_scratch)
+        return fail(ctx, DM_ERR_NOT_BOUND, "dm_build_partitions: mask, pdm and scratch must be bound");
+    dm_status st = check_sticky(ctx, "dm_build_partitions (earlier work)");
+    if (st != DM_OK) return st;
+    const int K = ctx->cfg.num_partitions, N = ctx->cfg.tf_size;
+    cudaStream_t s = as_stream(stream);
+    uint8_t* scratch = static_cast<uint8_t*>(ctx->d_scratch);
+    uint8_t* lut = scratch + ctx->off_lut;
+    uint8_t* pdm = static_cast<uint8_t*>(ctx->d_pdm);
+    cudaError_t e = dmk::launch_partition_lut(lut, N, K, ctx->borders, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition table");
+    e = dmk::launch_pom_build(d_volume, ctx->geo, N, K, lut, static_cast<uint64_t*>(ctx->d_mask),
+                              ctx->d_minmax, 200 * 1024, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "POM build");
+    e = dmk::launch_xpass_mask(static_cast<const uint64_t*>(ctx->d_mask), K, ctx->geo, pdm, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM x pass");
+    e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM y pass");
+    e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 2, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM z pass");
+    ctx->built = true;
+    ctx->minmax_built = ctx->d_minmax != nullptr;
+    ctx->err[0] = 0;
+    return DM_OK;
+}
+
+static dm_status check_update(dm_ctx* ctx, const void* tf, const void* out, const char* who)
+{
+    if (!tf || !out || !aligned(tf, 4))
+        return fail(ctx, DM_ERR_INVALID_ARG, "%s: null or misaligned tf / out", who);
+    if (!ctx->d_pdm || !ctx->d_scratch)
+        return fail(ctx, DM_ERR_NOT_BOUND, "%s: pdm and scratch must be bound", who);
+    if (!ctx->built)
+        return fail(ctx, DM_ERR_NOT_BOUND, "%s: dm_build_partitions has not run on the bound pdm", who);
+    return DM_OK;
+}
+
+static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
+                             uint64_t* d_active_mask_out, cudaStream_t s)
+{
+    uint8_t* scratch = static_cast<uint8_t*>(ctx->d_scratch);
+    const int K = ctx->cfg.num_partitions, N = ctx->cfg.tf_size;
+    int32_t* cnt = reinterpret_cast<int32_t*>(scratch + ctx->off_cnt);
+    uint16_t* act = reinterpret_cast<uint16_t*>(scratch + ctx->off_act);
+    int32_t* nact = reinterpret_cast<int32_t*>(scratch + ctx->off_nact);
+    uint64_t* smask = reinterpret_cast<uint64_t*>(scratch + ctx->off_smask);
+    cudaError_t e = dmk::launch_tf_active(d_tf, N, K, ctx->borders, cnt, act, nact, smask,
+                                          d_active_mask_out, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "active set");
+    if (ctx->ev_begin && (e = cudaEventRecord(ctx->ev_begin, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "profile event");
+    e = dmk::launch_combine(static_cast<const uint8_t*>(ctx->d_pdm), ctx->geo.plane, ctx->geo.G,
+                            act, nact, d_out, ctx->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine");
+    if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "profile event");
+    ctx->err[0] = 0;
+    return DM_OK;
+}
+
+dm_status dm_update_tf(dm_ctx* ctx, const float* d_tf_rgba, uint8_t* d_out,
+                       uint64_t* d_active_mask_out, void* stream)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (d_active_mask_out && !aligned(d_active_mask_out, 8))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_update_tf: misaligned active-mask output");
+    dm_status st = check_update(ctx, d_tf_rgba, d_out, "dm_update_tf");
+    if (st != DM_OK) return st;
+    st = check_sticky(ctx, "dm_update_tf (earlier work)");
+    if (st != DM_OK) return st;
+    return update_into(ctx, d_tf_rgba, d_out, d_active_mask_out, as_stream(stream));
+}
+
+dm_status dm_update_tf_host(dm_ctx* ctx, const float* h_tf_rgba, uint8_t* h_out, void* stream)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!h_tf_rgba || !h_out) return fail(ctx, DM_ERR_INVALID_ARG, "dm_update_tf_host: null buffer");
+    dm_status st = check_update(ctx, h_tf_rgba, h_out, "dm_update_tf_host");
+    if (st != DM_OK) return st;
+    st = check_sticky(ctx, "dm_update_tf_host (earlier work)");
+    if (st != DM_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    uint8_t* scratch = static_cast<uint8_t*>(ctx->d_scratch);
+    float* d_tf = reinterpret_cast<float*>(scratch + ctx->off_tf);
+    uint8_t* d_out = scratch + ctx->off_out;
+    const size_t tf_bytes = size_t(ctx->cfg.tf_size) * 16;
+    cudaError_t e = cudaMemcpyAsync(d_tf, h_tf_rgba, tf_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: TF upload");
+    st = update_into(ctx, d_tf, d_out, nullptr, s);
+    if (st != DM_OK) return st;
+    e = cudaMemcpyAsync(h_out, d_out, size_t(ctx->geo.G), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: D' download");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: sync");
+    return DM_OK;
+}
+
+dm_status dm_full_recompute(dm_ctx* ctx, const void* d_volume, const float* d_tf_rgba,
+                            uint8_t* d_out, void* stream)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (!d_tf_rgba || !d_out || !aligned(d_tf_rgba, 4))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_full_recompute: null or misaligned tf / out");
+    if (!ctx->d_scratch)
+        return fail(ctx, DM_ERR_NOT_BOUND, "dm_full_recompute: scratch must be bound");
+    const bool exact = ctx->cfg.occ_mode == DM_OCC_EXACT;
+    if (exact && (!d_volume || !aligned(d_volume, size_t(ctx->geo.bpv))))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_full_recompute: exact mode needs the volume");
+    if (!exact && (!ctx->d_minmax || !ctx->minmax_built))
+        return fail(ctx, DM_ERR_NOT_BOUND,
+                    "dm_full_recompute: min/max mode needs a bound min/max built by dm_build_partitions");
+    dm_status st = check_sticky(ctx, "dm_full_recompute (earlier work)");
+    if (st != DM_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    uint8_t* scratch = static_cast<uint8_t*>(ctx->d_scratch);
+    const int K = ctx->cfg.num_partitions, N = ctx->cfg.tf_size;
+    int32_t* cnt = reinterpret_cast<int32_t*>(scratch + ctx->off_cnt);
+    uint16_t* act = reinterpret_cast<uint16_t*>(scratch + ctx->off_act);
+    int32_t* nact = reinterpret_cast<int32_t*>(scratch + ctx->off_nact);
+    uint64_t* smask = reinterpret_cast<uint64_t*>(scratch + ctx->off_smask);
+    cudaError_t e = dmk::launch_tf_active(d_tf_rgba, N, K, ctx->borders, cnt, act, nact, smask,
+                                          nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "visibility prefix");
+    if (exact) {
+        e = dmk::launch_occ_exact(d_volume, ctx->geo, N, cnt, d_out, 200 * 1024, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "exact occupancy");
+        e = dmk::launch_xpass_occ(d_out, ctx->geo, s);
+    } else {
+        e = dmk::launch_xpass_minmax(ctx->d_minmax, cnt, ctx->geo, d_out, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DT x pass");
+    e = dmk::launch_line_pass(d_out, 1, 0, ctx->geo, 1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DT y pass");
+    e = dmk::launch_line_pass(d_out, 1, 0, ctx->geo, 2, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "DT z pass");
+    ctx->err[0] = 0;
+    return DM_OK;
+}
+
+dm_status dm_set_profile_events(dm_ctx* ctx, void* ev_begin, void* ev_end)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if ((ev_begin == nullptr) != (ev_end == nullptr))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_set_profile_events: set both events or neither");
+    ctx->ev_begin = static_cast<cudaEvent_t>(ev_begin);
+    ctx->ev_end = static_cast<cudaEvent_t>(ev_end);
+    return DM_OK;
+}
+
+dm_status dm_sync(dm_ctx* ctx, void* stream)
+{
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_sync");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_sync (sticky)");
+    if (ctx) ctx->err[0] = 0;
+    return DM_OK;
+}
+
+void dm_destroy(dm_ctx* ctx) { delete ctx; }
+
+}  // extern "C"

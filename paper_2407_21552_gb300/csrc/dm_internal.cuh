@@ -1,0 +1,74 @@
+// dm_internal.cuh -- launchers shared between the C-ABI layer and the kernel files.
+// Internal to libdm: nothing here is part of the public ABI in include/dm.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dmk {
+
+constexpr int kMaxPartitions = 256;
+constexpr int kLineTile = 16;         // columns per line-pass tile (bytes per row)
+constexpr int kMaxLevels = 9;         // sparse-table levels 0..8 cover windows up to 511
+constexpr int kLineSmemLimit = 200 * 1024;
+constexpr int kXpassSmemLimit = 160 * 1024;
+
+// Partition borders as a by-value kernel parameter: v[p] is the lowest intensity of
+// partition p, v[K] = N (§3.1: integer borders rho_min^p .. rho_max^p = v[p+1]-1).
+struct Borders {
+    int32_t v[kMaxPartitions + 1];
+};
+
+// Volume and block-grid geometry (§3.1: non-overlapping b^3 blocks; footprint adds an
+// apron of `a` voxels per side, clipped at the volume).
+struct Geometry {
+    int32_t X, Y, Z;        // voxels
+    int32_t gx, gy, gz;     // blocks: ceil(dim / b)
+    int32_t b, a;           // block edge, apron
+    int32_t bpv;            // bytes per voxel: 1 or 2
+    int64_t G;              // gx * gy * gz
+    int64_t plane;          // bytes between PDM planes (G rounded up to 64)
+};
+
+// ---------------------------------------------------------------- one-time precompute
+cudaError_t launch_partition_lut(uint8_t* lut, int N, int K, const Borders& bd,
+                                 cudaStream_t s);
+
+// POM bit masks [G][W] (+ block footprint min/max pairs when minmax != nullptr).
+cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
+                             const uint8_t* lut, uint64_t* mask, void* minmax,
+                             size_t smem_limit, cudaStream_t s);
+
+// Exact TF occupancy per block (1 byte, 0/1) from a per-voxel visibility test over the
+// footprint; visibility of intensity i is cnt[i+1] > cnt[i].
+cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const int32_t* cnt,
+                             uint8_t* occ, size_t smem_limit, cudaStream_t s);
+
+// ---------------------------------------------------------------- distance transform
+// x pass: 1D distance along x to the nearest occupied block, saturating at 255.
+cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, uint8_t* pdm,
+                              cudaStream_t s);
+cudaError_t launch_xpass_minmax(const void* minmax, const int32_t* cnt, const Geometry& g,
+                                uint8_t* out, cudaStream_t s);
+cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t s);
+
+// y (axis 1) or z (axis 2) pass in place over P maps at `plane` bytes apart:
+// h(i) = min over j of max(|i - j|, g(j)), saturating at 255.
+cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
+                             cudaStream_t s);
+size_t line_pass_smem(int L);
+
+// ---------------------------------------------------------------- per-TF update
+// Visibility prefix count cnt[0..N] (cnt[i] = #{j < i : alpha_j > 0}), active set S as a
+// bit set smask[4] and as an ascending list act[0..*nact).  smask_out may be null.
+cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, int32_t* cnt,
+                             uint16_t* act, int32_t* nact, uint64_t* smask,
+                             uint64_t* smask_out, cudaStream_t s);
+
+// D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
+cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
+                           const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s);
+
+}  // namespace dmk

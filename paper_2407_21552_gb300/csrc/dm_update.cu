@@ -1,0 +1,164 @@
+// dm_update.cu -- the per-TF update: active partitions from the TF, then the combine.
+//
+// §3.1 step 1: S = partitions holding at least one intensity whose TF alpha is non-zero.
+// One CTA turns the N alphas into a visibility prefix count cnt[0..N] (also what the plain
+// min/max recompute needs), then partition p is active iff cnt[hi_p + 1] > cnt[lo_p]; the
+// active indices are compacted in ascending order with warp ballots.  S never leaves the
+// device.
+//
+// §3.1 step 2, Eq. 1: D'(x,y,z) = min over p in S of PDM_p(x,y,z).  A pure streaming
+// kernel: each thread owns 16-byte chunks of the map, reads the same chunk of every active
+// plane (independent 16-byte loads, several in flight) and folds them with __vminu4.  The
+// HBM traffic is (|S| + 1) * G bytes, the algorithmic minimum.  An empty S yields 255.
+#include "dm_internal.cuh"
+
+namespace dmk {
+namespace {
+
+constexpr int kActThreads = 1024;
+constexpr int kCombineThreads = 256;
+
+__global__ void __launch_bounds__(kActThreads)
+k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __restrict__ cnt,
+            uint16_t* __restrict__ act, int32_t* __restrict__ nact, uint64_t* __restrict__ smask,
+            uint64_t* __restrict__ smask_out)
+{
+    __shared__ int32_t s_warp[32];
+    __shared__ int32_t s_actw[8];
+    __shared__ uint32_t s_bits[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // contiguous chunk of intensities per thread
+    const int per = (N + kActThreads - 1) / kActThreads;
+    const int i0 = min(N, tid * per), i1 = min(N, i0 + per);
+    int c = 0;
+    for (int i = i0; i < i1; ++i) c += (__ldg(tf + 4 * int64_t(i) + 3) > 0.0f);
+    // block exclusive scan of c
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = s_warp[lane];
+        int wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int v = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+            if (lane >= d) wi += v;
+        }
+        s_warp[lane] = wi - w;                 // exclusive warp offsets
+    }
+    __syncthreads();
+    int run = s_warp[warp] + incl - c;
+    for (int i = i0; i < i1; ++i) {
+        cnt[i] = run;
+        run += (__ldg(tf + 4 * int64_t(i) + 3) > 0.0f);
+    }
+    if (i1 == N && i0 < i1) cnt[N] = run;   // the thread holding intensity N-1
+    __syncthreads();                          // cnt is visible to the whole block
+    // active partitions, ascending, compacted with ballots (K <= 256 -> warps 0..7)
+    const int p = tid;
+    const bool on = (p < K) && (cnt[bd.v[p + 1]] > cnt[bd.v[p]]);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
+    if (lane == 0 && warp < 8) {
+        s_actw[warp] = __popc(bal);
+        s_bits[warp] = bal;
+    }
+    __syncthreads();
+    if (tid < 256) {
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += s_actw[w];
+        if (on) act[off + __popc(bal & ((1u << lane) - 1))] = uint16_t(p);
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < 8; ++w) tot += s_actw[w];
+            *nact = tot;
+        }
+        if (tid < 4) {
+            uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
+            smask[tid] = v;
+            if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b)
+{
+    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
+                      __vminu4(a.w, b.w));
+}
+
+__global__ void __launch_bounds__(kCombineThreads)
+k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
+          const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
+          uint8_t* __restrict__ out, int vec_ok)
+{
+    __shared__ int64_t s_off[kMaxPartitions];
+    __shared__ int s_n;
+    if (threadIdx.x == 0) s_n = *nact;
+    __syncthreads();
+    const int n = s_n;
+    for (int j = threadIdx.x; j < n; j += kCombineThreads) s_off[j] = int64_t(act[j]) * plane;
+    __syncthreads();
+    const int64_t stride = int64_t(gridDim.x) * kCombineThreads;
+    const int64_t t0 = int64_t(blockIdx.x) * kCombineThreads + threadIdx.x;
+    int64_t done = 0;
+    if (vec_ok) {
+        const int64_t nvec = G >> 4;
+        for (int64_t v = t0; v < nvec; v += stride) {
+            uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+            const uint8_t* src = pdm + (v << 4);
+            int j = 0;
+            for (; j + 8 <= n; j += 8) {
+                uint4 d[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    d[k] = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + k]));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc = vmin4(acc, d[k]);
+            }
+            for (; j + 2 <= n; j += 2) {
+                uint4 d0 = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j]));
+                uint4 d1 = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + 1]));
+                acc = vmin4(acc, vmin4(d0, d1));
+            }
+            if (j < n) acc = vmin4(acc, __ldcs(reinterpret_cast<const uint4*>(src + s_off[j])));
+            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc);
+        }
+        done = nvec << 4;
+    }
+    // bytes not covered by whole aligned chunks
+    for (int64_t i = done + t0; i < G; i += stride) {
+        unsigned acc = 255;
+        for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
+        out[i] = uint8_t(acc);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, int32_t* cnt,
+                             uint16_t* act, int32_t* nact, uint64_t* smask,
+                             uint64_t* smask_out, cudaStream_t s)
+{
+    k_tf_active<<<1, kActThreads, 0, s>>>(tf, N, K, bd, cnt, act, nact, smask, smask_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
+                           const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s)
+{
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (plane % 16 == 0);
+    int64_t work = vec_ok ? (G >> 4) : G;
+    int64_t want = (work + kCombineThreads - 1) / kCombineThreads;
+    int64_t cap = int64_t(num_sms > 0 ? num_sms : 152) * 8;   // 8 resident CTAs per SM
+    int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
+    k_combine<<<blocks, kCombineThreads, 0, s>>>(pdm, plane, G, act, nact, out, vec_ok);
+    return cudaGetLastError();
+}
+
+}  // namespace dmk

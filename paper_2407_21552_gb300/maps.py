@@ -1,0 +1,131 @@
+"""PyTorch-facing wrapper: torch owns the device buffers, libdm does every step.
+
+PartitionedDistanceMaps allocates the buffers that dm_query_sizes() asks for as torch
+uint8 tensors on the device, binds them, and forwards each call to the C ABI on the
+current torch stream.  It performs no computation of its own.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi as A
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return A.DM_U8
+    if t.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return A.DM_U16
+    raise TypeError("volume must be uint8, or int16/uint16 holding unsigned 16-bit intensities")
+
+
+class PartitionedDistanceMaps:
+    """One volume's partitioned distance maps (§3.1) resident on a CUDA device."""
+
+    def __init__(self, dims, dtype: int, block: int = 4, apron: int = 1,
+                 num_partitions: int = 16, tf_size: int = 256, borders=None,
+                 occ_mode: int = A.DM_OCC_MINMAX, device="cuda", with_minmax: bool = True):
+        self.cfg, self._keep = A.make_config(dims, dtype, block, apron, num_partitions, tf_size,
+                                             borders, occ_mode)
+        self.ctx = A.dm_create(self.cfg)
+        self.sizes = A.dm_query_sizes(self.ctx)
+        self.device = torch.device(device)
+        s = self.sizes
+        self.K = int(num_partitions)
+        self.N = int(tf_size)
+        self.grid = tuple(int(v) for v in s.grid)          # (Gx, Gy, Gz)
+        self.G = self.grid[0] * self.grid[1] * self.grid[2]
+        self.plane_stride = int(s.plane_stride)
+        alloc = dict(dtype=torch.uint8, device=self.device)
+        self._mask = torch.empty(max(16, s.mask_bytes), **alloc)
+        self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
+        self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc) if with_minmax else None
+        self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
+        self._bind()
+
+    def _bind(self):
+        A.dm_bind(self.ctx,
+                  self._mask.data_ptr() if self._mask is not None else None,
+                  self._pdm.data_ptr(),
+                  self._minmax.data_ptr() if self._minmax is not None else None,
+                  self._scratch.data_ptr())
+
+    # ------------------------------------------------------------------ the three calls
+    def build_partitions(self, volume: torch.Tensor, stream=None):
+        assert volume.is_cuda and volume.is_contiguous()
+        assert _dtype_code(volume) == self.cfg.dtype
+        A.dm_build_partitions(self.ctx, volume.data_ptr(), _stream_handle(stream))
+
+    def update_tf(self, tf: torch.Tensor, out: torch.Tensor | None = None,
+                  active_mask: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        assert tf.is_cuda and tf.dtype == torch.float32 and tf.is_contiguous()
+        assert tf.numel() == 4 * self.N
+        if out is None:
+            out = torch.empty(self.G, dtype=torch.uint8, device=self.device)
+        am = active_mask.data_ptr() if active_mask is not None else None
+        A.dm_update_tf(self.ctx, tf.data_ptr(), out.data_ptr(), am, _stream_handle(stream))
+        return out
+
+    def update_tf_host(self, tf_host: torch.Tensor, out_host: torch.Tensor, stream=None):
+        """Host in, host out (the call waits); pinned host tensors give async copies."""
+        assert not tf_host.is_cuda and not out_host.is_cuda
+        assert tf_host.dtype == torch.float32 and tf_host.numel() == 4 * self.N
+        assert out_host.dtype == torch.uint8 and out_host.numel() >= self.G
+        A.dm_update_tf_host(self.ctx, tf_host.data_ptr(), out_host.data_ptr(),
+                            _stream_handle(stream))
+        return out_host
+
+    def full_recompute(self, tf: torch.Tensor, out: torch.Tensor | None = None,
+                       volume: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        assert tf.is_cuda and tf.dtype == torch.float32 and tf.is_contiguous()
+        if out is None:
+            out = torch.empty(self.G, dtype=torch.uint8, device=self.device)
+        vp = volume.data_ptr() if volume is not None else None
+        A.dm_full_recompute(self.ctx, vp, tf.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def sync(self, stream=None):
+        A.dm_sync(self.ctx, _stream_handle(stream))
+
+    # ------------------------------------------------------------------ views for tests
+    def pdm_planes(self) -> torch.Tensor:
+        """[K, Gz, Gy, Gx] view of the PDM planes."""
+        gx, gy, gz = self.grid
+        v = self._pdm[: self.K * self.plane_stride].view(self.K, self.plane_stride)
+        return v[:, : self.G].reshape(self.K, gz, gy, gx)
+
+    def mask_words(self) -> torch.Tensor:
+        gx, gy, gz = self.grid
+        W = int(self.sizes.mask_words)
+        return self._mask[: self.G * W * 8].view(torch.int64).view(gz, gy, gx, W)
+
+    def minmax_pairs(self) -> torch.Tensor:
+        """[Gz, Gy, Gx, 2] (min, max); int16 storage for 16-bit volumes."""
+        gx, gy, gz = self.grid
+        if self.cfg.dtype == A.DM_U8:
+            return self._minmax[: 2 * self.G].view(gz, gy, gx, 2)
+        return self._minmax[: 4 * self.G].view(torch.int16).view(gz, gy, gx, 2)
+
+    def release_mask(self):
+        """The POMs are an intermediate (§5): drop their buffer after the precompute."""
+        self._mask = None
+        self._bind()
+
+    def close(self):
+        if self.ctx:
+            A.dm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,143 @@
+"""Host-side checks of libdm without a GPU: the library loads, exports every function that
+include/dm.h declares, validates configurations, reports sizes (the memory formula of §5)
+and refuses calls on unbound or misaligned buffers before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2407_21552_gb300 as pkg
+from paper_2407_21552_gb300 import _abi as A
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    pkg.build()
+    return A.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "dm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dm_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_function(lib):
+    declared = header_functions()
+    assert set(declared) == set(A.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {A.LIB_PATH}").read()
+    for name in declared:
+        assert re.search(rf"\bT {name}\b", out), f"{name} not exported"
+
+
+def test_version_and_status_names():
+    assert A.dm_version() == 10000
+    assert A.dm_status_string(A.DM_OK) == "DM_OK"
+    assert A.dm_status_string(A.DM_ERR_UNSUPPORTED) == "DM_ERR_UNSUPPORTED"
+    assert A.dm_status_string(99) == "DM_ERR_UNKNOWN"
+
+
+def cfg(**kw):
+    base = dict(dims=(128, 128, 128), dtype=A.DM_U8, block=4, apron=1, num_partitions=16,
+                tf_size=256, borders=None, occ_mode=A.DM_OCC_MINMAX)
+    base.update(kw)
+    return A.make_config(**base)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(), A.DM_OK),
+    (dict(dims=(0, 4, 4)), A.DM_ERR_INVALID_ARG),
+    (dict(dtype=3), A.DM_ERR_INVALID_ARG),
+    (dict(block=0), A.DM_ERR_INVALID_ARG),
+    (dict(block=17), A.DM_ERR_UNSUPPORTED),
+    (dict(apron=-1), A.DM_ERR_INVALID_ARG),
+    (dict(apron=5), A.DM_ERR_UNSUPPORTED),
+    (dict(num_partitions=0), A.DM_ERR_INVALID_ARG),
+    (dict(num_partitions=257, tf_size=4096), A.DM_ERR_UNSUPPORTED),
+    (dict(num_partitions=300, tf_size=256), A.DM_ERR_UNSUPPORTED),
+    (dict(num_partitions=20, tf_size=16), A.DM_ERR_INVALID_ARG),
+    (dict(tf_size=1), A.DM_ERR_INVALID_ARG),
+    (dict(tf_size=70000), A.DM_ERR_UNSUPPORTED),
+    (dict(occ_mode=2), A.DM_ERR_INVALID_ARG),
+    (dict(num_partitions=4, borders=[0, 1, 5, 200, 256]), A.DM_OK),
+    (dict(num_partitions=4, borders=[0, 5, 5, 200, 256]), A.DM_ERR_INVALID_ARG),
+    (dict(num_partitions=4, borders=[1, 5, 9, 200, 256]), A.DM_ERR_INVALID_ARG),
+    (dict(num_partitions=4, borders=[0, 5, 9, 200, 255]), A.DM_ERR_INVALID_ARG),
+    (dict(dims=(4, 4, 4 * 2000)), A.DM_ERR_UNSUPPORTED),     # z lines beyond the tiling
+    (dict(dims=(1, 1, 1), block=1, apron=0, num_partitions=1, tf_size=2), A.DM_OK),
+])
+def test_create_validation(kw, status):
+    c, keep = cfg(**kw)
+    assert A.dm_create_status(c) == status
+
+
+@pytest.mark.parametrize("dims,b,K,bpv", [
+    ((512, 512, 460), 4, 16, 1),         # manix-sized grid 128x128x115
+    ((1024, 1024, 1795), 4, 64, 2),      # 256x256x449
+    ((37, 29, 23), 4, 7, 1),             # ragged edges: ceil
+    ((5, 7, 9), 1, 256, 2),
+])
+def test_query_sizes_memory_formula(dims, b, K, bpv):
+    c, keep = cfg(dims=dims, block=b, num_partitions=K, dtype=bpv,
+                  tf_size=4096 if bpv == 2 else 256, apron=min(1, b))
+    ctx = A.dm_create(c)
+    try:
+        s = A.dm_query_sizes(ctx)
+        g = [-(-d // b) for d in dims]
+        G = g[0] * g[1] * g[2]
+        assert list(s.grid) == g
+        assert s.out_bytes == G
+        assert s.plane_stride == -(-G // 64) * 64
+        assert s.pdm_bytes == K * s.plane_stride
+        if G % 64 == 0:
+            assert s.pdm_bytes == K * G          # §5: n * volumesize / b^3 bytes
+        assert s.mask_words == -(-K // 64)
+        assert s.mask_bytes == G * s.mask_words * 8
+        assert s.minmax_bytes == 2 * bpv * G
+        assert s.scratch_bytes >= G + 16 * c.tf_size
+    finally:
+        A.dm_destroy(ctx)
+
+
+def test_unbound_and_misaligned_calls_are_refused_on_the_host():
+    c, keep = cfg()
+    ctx = A.dm_create(c)
+    lib = A.load()
+    try:
+        fake = ctypes.c_void_p(1 << 20)       # never dereferenced: refused before any launch
+        assert lib.dm_build_partitions(ctx, fake, None) == A.DM_ERR_NOT_BOUND
+        assert lib.dm_update_tf(ctx, fake, fake, None, None) == A.DM_ERR_NOT_BOUND
+        assert lib.dm_full_recompute(ctx, fake, fake, fake, None) == A.DM_ERR_NOT_BOUND
+        assert "bound" in A.dm_last_error_string(ctx)
+        assert lib.dm_bind(ctx, ctypes.c_void_p((1 << 20) + 3), None, None, None) == \
+            A.DM_ERR_INVALID_ARG
+        assert "misaligned" in A.dm_last_error_string(ctx)
+        assert lib.dm_bind(ctx, None, None, None, ctypes.c_void_p((1 << 20) + 16)) == \
+            A.DM_ERR_INVALID_ARG
+        # pdm bound but never built: the update refuses
+        assert lib.dm_bind(ctx, fake, fake, fake, fake) == A.DM_OK
+        assert lib.dm_update_tf(ctx, fake, fake, None, None) == A.DM_ERR_NOT_BOUND
+        assert "build" in A.dm_last_error_string(ctx)
+        assert lib.dm_update_tf(ctx, None, fake, None, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_update_tf_host(ctx, None, None, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_build_partitions(ctx, None, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_query_sizes(None, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_create(None, None) == A.DM_ERR_INVALID_ARG
+    finally:
+        A.dm_destroy(ctx)
+    A.dm_destroy(None)
+
+
+def test_package_fails_loudly_without_the_library(tmp_path):
+    with pytest.raises(ImportError):
+        A._lib_backup = A._lib
+        try:
+            A._lib = None
+            A.load(str(tmp_path / "missing.so"))
+        finally:
+            A._lib = A._lib_backup

@@ -1,0 +1,249 @@
+"""GPU path vs the CPU oracle, bit-exact (integer work; §3.2 uint8 maps).
+
+Every call goes through the C ABI (ctypes) of libdm; torch only allocates device memory.
+Covered: the tiny workload (128^3 uint8, K=16, 100 TF edits + special TFs), the CT
+workload (512^3 12-bit, K=32, N=4096), ragged volumes (dims not multiples of b), several
+tiles and partial tiles in every kernel, b in {1,2,3,4,8}, apron 0..2, K up to 256 (four
+mask words), explicit borders (a separate partition for the minimum intensity, §4.2),
+voxels above the TF domain, lines longer than 255 blocks (clamping), degenerate volumes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import tfs as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def _engine(vol_np, b, a, N, K, borders=None, exact=False):
+    from paper_2407_21552_gb300 import DM_U8, DM_U16, DM_OCC_EXACT, DM_OCC_MINMAX
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    Z, Y, X = vol_np.shape
+    dt = DM_U8 if vol_np.dtype == np.uint8 else DM_U16
+    return PartitionedDistanceMaps((X, Y, Z), dt, b, a, K, N, borders=borders,
+                                   occ_mode=DM_OCC_EXACT if exact else DM_OCC_MINMAX)
+
+
+def _to_dev(vol_np):
+    if vol_np.dtype == np.uint8:
+        return torch.from_numpy(vol_np).cuda()
+    return torch.from_numpy(vol_np.view(np.int16)).cuda()
+
+
+def check_build(vol_np, b, a, N, K, borders=None):
+    eng = _engine(vol_np, b, a, N, K, borders)
+    vd = _to_dev(vol_np)
+    eng.build_partitions(vd)
+    eng.sync()
+    mask_o, pdm_o, vmin_o, vmax_o = oracle.build_partitions(vol_np, b, a, N, K, borders)
+    mask_g = eng.mask_words().cpu().numpy().view(np.uint64)
+    assert np.array_equal(mask_g, mask_o), "POM bit masks differ"
+    mm = eng.minmax_pairs().cpu().numpy()
+    if vol_np.dtype == np.uint16:
+        mm = mm.view(np.uint16)
+    assert np.array_equal(mm[..., 0].astype(np.int64), vmin_o.astype(np.int64)), "block min"
+    assert np.array_equal(mm[..., 1].astype(np.int64), vmax_o.astype(np.int64)), "block max"
+    pdm_g = eng.pdm_planes().cpu().numpy()
+    for p in range(K):
+        assert np.array_equal(pdm_g[p], pdm_o[p]), f"PDM plane {p} differs"
+    return eng, vd, (mask_o, pdm_o, vmin_o, vmax_o)
+
+
+def check_updates(eng, vd, vol_np, ref, tfs, b, a, borders=None, full=True, exact_every=0):
+    from paper_2407_21552_gb300 import DM_OCC_EXACT
+    mask_o, pdm_o, vmin_o, vmax_o = ref
+    K = pdm_o.shape[0]
+    W = (K + 63) // 64
+    am = torch.zeros(W, dtype=torch.int64, device="cuda")
+    for k, tf in enumerate(tfs):
+        tfd = torch.from_numpy(tf).cuda()
+        out = eng.update_tf(tfd, active_mask=am)
+        want, smask = oracle.update_tf(pdm_o, tf, borders)
+        got = out.cpu().numpy().reshape(want.shape)
+        assert np.array_equal(got, want), f"D' differs on TF {k}"
+        assert np.array_equal(am.cpu().numpy().view(np.uint64), smask), f"S differs on TF {k}"
+        if full:
+            d = eng.full_recompute(tfd).cpu().numpy().reshape(want.shape)
+            assert np.array_equal(d, oracle.full_recompute_minmax(vmin_o, vmax_o, tf)), \
+                f"min/max full recompute differs on TF {k}"
+        if exact_every and k % exact_every == 0:
+            ex = _engine(vol_np, b, a, vol_tf_size(tf), K, borders, exact=True)
+            ex._minmax = None
+            ex._bind()
+            d = ex.full_recompute(tfd, volume=vd).cpu().numpy().reshape(want.shape)
+            assert np.array_equal(d, oracle.full_recompute_exact(vol_np, b, a, tf)), \
+                f"exact full recompute differs on TF {k}"
+            ex.close()
+    eng.sync()
+
+
+def vol_tf_size(tf):
+    return tf.shape[0]
+
+
+# ------------------------------------------------------------------------ tiny workload
+@pytest.fixture(scope="module")
+def tiny():
+    w = synth.WORKLOADS["tiny"]
+    vol = synth.as_numpy(synth.make_volume("tiny"))
+    eng, vd, ref = check_build(vol, w["block"], w["apron"], w["N"], w["K"])
+    return dict(w=w, vol=vol, eng=eng, vd=vd, ref=ref)
+
+
+def test_tiny_build_parity(tiny):
+    assert tiny["ref"][1].shape == (16, 32, 32, 32)
+
+
+def test_tiny_100_edits_and_special_tfs(tiny):
+    w = tiny["w"]
+    tfs = T.tf_edit_sequence(w["seed"], w["N"], w["edits"])
+    tfs += T.special_tfs(w["N"], T.uniform_borders(w["N"], w["K"]))
+    check_updates(tiny["eng"], tiny["vd"], tiny["vol"], tiny["ref"], tfs, w["block"],
+                  w["apron"], exact_every=10)
+
+
+def test_host_buffer_update_matches(tiny):
+    w = tiny["w"]
+    eng = tiny["eng"]
+    tf = T.tf_edit_sequence(77, w["N"], 1)[0]
+    h_tf = torch.from_numpy(tf).pin_memory()
+    h_out = torch.empty(eng.G, dtype=torch.uint8).pin_memory()
+    eng.update_tf_host(h_tf, h_out)
+    want, _ = oracle.update_tf(tiny["ref"][1], tf)
+    assert np.array_equal(h_out.numpy().reshape(want.shape), want)
+    # pageable host memory works too
+    h_out2 = torch.empty(eng.G, dtype=torch.uint8)
+    eng.update_tf_host(torch.from_numpy(tf.copy()), h_out2)
+    assert np.array_equal(h_out2.numpy().reshape(want.shape), want)
+
+
+def test_repeated_updates_on_other_stream(tiny):
+    w = tiny["w"]
+    eng = tiny["eng"]
+    s = torch.cuda.Stream()
+    tfs = T.tf_edit_sequence(5, w["N"], 8)
+    outs = []
+    with torch.cuda.stream(s):
+        for tf in tfs:
+            outs.append(eng.update_tf(torch.from_numpy(tf).cuda(), stream=s))
+    s.synchronize()
+    for tf, o in zip(tfs, outs):
+        want, _ = oracle.update_tf(tiny["ref"][1], tf)
+        assert np.array_equal(o.cpu().numpy().reshape(want.shape), want)
+
+
+# --------------------------------------------------------------- ragged / odd configs
+def rand_volume(rng, shape, N, dtype, blob=3):
+    v = rng.integers(0, N, size=tuple(max(1, s // blob) for s in shape))
+    v = np.kron(v, np.ones((blob, blob, blob), np.int64))
+    v = np.pad(v, [(0, max(0, s - v.shape[i])) for i, s in enumerate(shape)], mode="edge")
+    v = v[: shape[0], : shape[1], : shape[2]]
+    noise = rng.integers(-N // 16, N // 16 + 1, size=shape)
+    v = np.clip(v + noise * (rng.uniform(size=shape) < 0.2), 0, N - 1)
+    return v.astype(dtype)
+
+
+CASES = [
+    # shape (Z, Y, X), b, a, N, K, dtype, borders
+    ((23, 29, 37), 4, 1, 256, 7, np.uint8, None),
+    ((23, 29, 37), 4, 0, 256, 16, np.uint8, None),
+    ((9, 10, 11), 3, 2, 4096, 32, np.uint16, None),
+    ((17, 33, 65), 2, 1, 300, 65, np.uint16, None),          # two mask words
+    ((13, 21, 40), 4, 1, 4096, 256, np.uint16, None),        # four mask words
+    ((12, 12, 12), 1, 0, 64, 64, np.uint8, None),            # b = 1: exact voxel classes
+    ((12, 12, 12), 1, 1, 64, 5, np.uint8, None),
+    ((40, 24, 72), 8, 3, 256, 16, np.uint8, None),
+    ((1, 1, 1), 4, 1, 256, 16, np.uint8, None),
+    ((1, 7, 130), 4, 1, 256, 3, np.uint8, None),
+    ((66, 3, 2), 1, 1, 256, 1, np.uint8, None),              # K = 1
+    ((16, 64, 256), 4, 1, 256, 4, np.uint8, [0, 1, 86, 171, 256]),  # rho_min partition
+    ((20, 36, 128), 4, 1, 256, 16, np.uint8, None),          # aligned rows, 16-byte paths
+    ((20, 36, 128), 4, 1, 4096, 32, np.uint16, None),
+]
+
+
+@pytest.mark.parametrize("shape,b,a,N,K,dt,borders", CASES)
+def test_ragged_configs(shape, b, a, N, K, dt, borders):
+    rng = np.random.default_rng(sum(shape) * 7 + b * 3 + K)
+    vol = rand_volume(rng, shape, N, dt)
+    if dt == np.uint16 and vol.size > 2:
+        vol.reshape(-1)[::97] = N + 5        # above the TF domain: treated as N - 1
+    eng, vd, ref = check_build(vol, b, a, N, K, borders)
+    bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
+    tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 6) + T.special_tfs(N, bd)
+    check_updates(eng, vd, vol, ref, tfs, b, a, borders, exact_every=3)
+    eng.close()
+
+
+@pytest.mark.parametrize("shape", [(4 * 600, 8, 8), (8, 4 * 300, 8), (8, 8, 4 * 700)])
+def test_long_lines_clamp_at_255(shape):
+    """One occupied corner; lines of 300-700 blocks need the 255 clamp on every axis."""
+    N, K, b, a = 256, 2, 4, 0
+    vol = np.zeros(shape, np.uint8)
+    vol[0, 0, 0] = 200                     # partition 1 occupied in block (0, 0, 0) only
+    eng, vd, ref = check_build(vol, b, a, N, K)
+    pd = ref[1][1]
+    assert pd.max() == 255 and pd.min() == 0
+    tf = T.single_intensity_tf(N, 200)
+    check_updates(eng, vd, vol, ref, [tf, T.zero_tf(N), T.all_visible_tf(N)], b, a,
+                  exact_every=1)
+    eng.close()
+
+
+def test_sparse_and_dense_lines_mix():
+    """Wide grid (several x tiles) with sparse occupancy: long searches in every pass."""
+    rng = np.random.default_rng(99)
+    N, K, b, a = 256, 8, 4, 1
+    vol = np.zeros((64, 96, 640), np.uint8)
+    pts = rng.integers(0, [64, 96, 640], size=(40, 3))
+    for z, y, x in pts:
+        vol[z, y, x] = rng.integers(1, 255)
+    eng, vd, ref = check_build(vol, b, a, N, K)
+    tfs = T.tf_edit_sequence(3, N, 5) + [T.single_intensity_tf(N, int(vol[tuple(pts[0])]))]
+    check_updates(eng, vd, vol, ref, tfs, b, a, exact_every=2)
+    eng.close()
+
+
+# ---------------------------------------------------------------------- CT workload
+@pytest.fixture(scope="module")
+def ct():
+    w = synth.WORKLOADS["ct"]
+    vol_t = synth.make_volume("ct", device="cuda")
+    vol = synth.as_numpy(vol_t)
+    eng, vd, ref = check_build(vol, w["block"], w["apron"], w["N"], w["K"])
+    return dict(w=w, vol=vol, eng=eng, vd=vd, ref=ref)
+
+
+def test_ct_build_parity(ct):
+    assert ct["ref"][1].shape == (32, 128, 128, 128)
+
+
+def test_ct_edits(ct):
+    w = ct["w"]
+    tfs = T.tf_edit_sequence(w["seed"], w["N"], w["edits"])
+    picked = tfs[::25] + T.special_tfs(w["N"], T.uniform_borders(w["N"], w["K"]))
+    check_updates(ct["eng"], ct["vd"], ct["vol"], ct["ref"], picked, w["block"], w["apron"],
+                  full=True, exact_every=20)
+
+
+def test_ct_all_edits_combine(ct):
+    """All 1000 edits of the workload through the combine, against the oracle."""
+    w = ct["w"]
+    pdm_o = ct["ref"][1]
+    eng = ct["eng"]
+    out = torch.empty(eng.G, dtype=torch.uint8, device="cuda")
+    for k, tf in enumerate(T.tf_edit_sequence(w["seed"], w["N"], w["edits"])):
+        if k % 4:
+            continue
+        eng.update_tf(torch.from_numpy(tf).cuda(), out=out)
+        want, _ = oracle.update_tf(pdm_o, tf)
+        assert np.array_equal(out.cpu().numpy().reshape(want.shape), want), k
