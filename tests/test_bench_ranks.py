@@ -1,0 +1,57 @@
+"""bench.py's multi-rank logic on CPU with two gloo ranks: the max-over-ranks reduction of
+the timed values and the barrier.  The path runs replicas (one GPU per rank, no data-path
+collective), so this host logic is all that N > 1 adds."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        bench.barrier(ws)
+        vals = [1.0 + rank, 10.0 - rank, 0.5 * rank]
+        out = bench.reduce_max(vals, ws)
+        q.put((rank, out))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert res[r] == [2.0, 10.0, 0.5]
+
+
+def test_reduce_max_single_rank_is_identity():
+    import bench
+    assert bench.reduce_max([3.0, 1.0], 1) == [3.0, 1.0]
+
+
+@pytest.mark.parametrize("q,expect", [(50, 2.0), (100, 3.0)])
+def test_percentile_helper(q, expect):
+    import bench
+    assert bench.pct([1.0, 2.0, 3.0], q) == expect
