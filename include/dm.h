@@ -151,6 +151,41 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
  */
 dm_status dm_set_profile_events(dm_ctx *ctx, void *ev_begin, void *ev_end);
 
+/*
+ * TF update for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is a deployment variant of dm_update_tf (same results, bit for bit).
+ *
+ * Who needs it: code that is not allowed to call cudaMalloc -- for example a plug-in
+ * inside a host renderer that owns all device allocations and only hands out the buffers
+ * it manages, or a render loop that must not allocate between frames because an
+ * allocation can synchronize the device and stall the frame.  dm_update_tf needs a small
+ * scratch buffer bound to a context; this call needs neither a context nor scratch from
+ * the caller.  Its working memory is a fixed array of DM_NOALLOC_SCRATCH_BYTES inside the
+ * library's own device memory, which every GPU that loads the library keeps until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Inputs: d_pdm, the K PDM planes (uint8, plane p at byte p * plane_stride, each [G] =
+ * num_blocks bytes, as built by dm_build_partitions); borders, host, K+1 lower borders as
+ * in dm_config (NULL = uniform); tf_size N; d_tf_rgba, device float32 [N][4].  Output:
+ * d_out, device uint8 [G], D' = min over active p of PDM_p (255 if none is active).
+ * Errors: DM_ERR_INVALID_ARG for null pointers, plane_stride < num_blocks, bad borders;
+ * DM_ERR_UNSUPPORTED when K > DM_MAX_PARTITIONS or N > DM_NOALLOC_MAX_TF_SIZE (the fixed
+ * array holds one visibility bit per TF entry); DM_ERR_CUDA for a launch failure.  Sizes
+ * are checked on the host before anything is enqueued.
+ *
+ * The first call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call outside any stream capture.  Every call
+ * shares the array and it keeps the last call's contents (each call rewrites all of the
+ * array that it reads); calls whose work overlaps on the GPU, e.g. on two unordered
+ * streams, race on it.  Asynchronous on `stream`.
+ */
+#define DM_NOALLOC_MAX_TF_SIZE 16384
+#define DM_NOALLOC_SCRATCH_BYTES 4096
+dm_status dm_update_tf_noalloc(const uint8_t *d_pdm, size_t plane_stride, int64_t num_blocks,
+                               int32_t num_partitions, const int32_t *borders,
+                               int32_t tf_size, const float *d_tf_rgba, uint8_t *d_out,
+                               void *stream);
+
 /* Wait for `stream` and report any asynchronous CUDA error as DM_ERR_CUDA. */
 dm_status dm_sync(dm_ctx *ctx, void *stream);
 

@@ -22,11 +22,13 @@ DM_OCC_EXACT = 1
 DM_MAX_PARTITIONS = 256
 DM_MAX_TF_SIZE = 65536
 DM_MAX_BLOCK = 16
+DM_NOALLOC_MAX_TF_SIZE = 16384
+DM_NOALLOC_SCRATCH_BYTES = 4096
 
 #: every function declared in include/dm.h
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
-            "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events", "dm_sync",
-            "dm_destroy",
+            "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
+            "dm_update_tf_noalloc", "dm_sync", "dm_destroy",
             "dm_last_error_string", "dm_status_string", "dm_version")
 
 
@@ -72,6 +74,7 @@ def load(path: str = LIB_PATH):
     lib.dm_update_tf_host.argtypes = [P, P, P, P]
     lib.dm_full_recompute.argtypes = [P, P, P, P, P]
     lib.dm_set_profile_events.argtypes = [P, P, P]
+    lib.dm_update_tf_noalloc.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, S, P, S, P, P, P]
     lib.dm_sync.argtypes = [P, P]
     lib.dm_destroy.argtypes = [P]
     lib.dm_destroy.restype = None
@@ -81,8 +84,8 @@ def load(path: str = LIB_PATH):
     lib.dm_status_string.restype = ctypes.c_char_p
     lib.dm_version.argtypes = []
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
-              "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events", "dm_sync",
-              "dm_version"):
+              "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
+              "dm_update_tf_noalloc", "dm_sync", "dm_version"):
         getattr(lib, n).restype = S
     _lib = lib
     return lib
@@ -165,6 +168,19 @@ def dm_full_recompute(ctx, d_volume, d_tf_rgba, d_out, stream):
 
 def dm_set_profile_events(ctx, ev_begin, ev_end):
     _check(ctx, load().dm_set_profile_events(ctx, ev_begin, ev_end), "dm_set_profile_events")
+
+
+def dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, borders, tf_size,
+                         d_tf_rgba, d_out, stream):
+    """Context-free update whose working memory is the library's fixed device array.
+    `borders` is None (uniform) or a sequence of K+1 ints."""
+    keep = None
+    if borders is not None:
+        keep = (ctypes.c_int32 * len(borders))(*[int(v) for v in borders])
+    st = load().dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, keep,
+                                     tf_size, d_tf_rgba, d_out, stream)
+    if st != DM_OK:
+        raise DmError(st, "dm_update_tf_noalloc")
 
 
 def dm_sync(ctx, stream):
