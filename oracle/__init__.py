@@ -50,6 +50,7 @@ def _load():
             "oracle_combine": [P, i32, i64, P, P],
             "oracle_update_tf": [P, i32, i64, P, i32, P, P, P],
             "oracle_full_recompute_minmax": [P, P, P, P, i32, P],
+            "oracle_occ_minmax": [P, P, i64, P, i32, P],
             "oracle_full_recompute_exact": [P, i32, P, i32, i32, P, i32, P],
         }
         for name, args in sig.items():
@@ -206,6 +207,17 @@ def full_recompute_minmax(vmin, vmax, tf):
     _check(_load().oracle_full_recompute_minmax(_p(mn), _p(mx), _p(grid), _p(t), t.shape[0],
                                                 _p(out)), "full_recompute_minmax")
     return out
+
+
+def occ_minmax(vmin, vmax, tf):
+    """0/1 occupancy of the min/max recompute: one visible intensity in [min, max]."""
+    mn = np.ascontiguousarray(vmin, dtype=np.uint16)
+    mx = np.ascontiguousarray(vmax, dtype=np.uint16)
+    t = np.ascontiguousarray(tf, dtype=np.float32)
+    occ = np.empty(mn.shape, dtype=np.uint8)
+    _check(_load().oracle_occ_minmax(_p(mn), _p(mx), int(mn.size), _p(t), t.shape[0], _p(occ)),
+           "occ_minmax")
+    return occ
 
 
 def full_recompute_exact(vol, b, a, tf):

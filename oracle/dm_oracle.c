@@ -296,9 +296,22 @@ int oracle_update_tf(const uint8_t *pdm, int32_t K, int64_t G, const float *tf_r
 }
 
 /*
- * Plain full recompute with block min/max occupancy: a block is occupied when one
- * intensity i in [vmin(blk), vmax(blk)] has alpha(i) > 0; then a fresh distance transform.
+ * TF occupancy of the plain min/max recompute: a block is occupied when one intensity i in
+ * [vmin(blk), vmax(blk)] has alpha(i) > 0.  occ [G] receives 0 / 1.
  */
+int oracle_occ_minmax(const uint16_t *vmin, const uint16_t *vmax, int64_t G,
+                      const float *tf_rgba, int32_t N, uint8_t *occ)
+{
+    if (!vmin || !vmax || !tf_rgba || !occ || G < 0) return -1;
+    for (int64_t i = 0; i < G; ++i) {
+        occ[i] = 0;
+        for (int64_t v = vmin[i]; v <= vmax[i] && v < N; ++v)
+            if (tf_rgba[4 * v + 3] > 0.0f) { occ[i] = 1; break; }
+    }
+    return 0;
+}
+
+/* Plain full recompute with block min/max occupancy, then a fresh distance transform. */
 int oracle_full_recompute_minmax(const uint16_t *vmin, const uint16_t *vmax,
                                  const int32_t grid[3], const float *tf_rgba, int32_t N,
                                  uint8_t *out)
@@ -307,11 +320,7 @@ int oracle_full_recompute_minmax(const uint16_t *vmin, const uint16_t *vmax,
     const int64_t G = (int64_t)grid[0] * grid[1] * grid[2];
     uint8_t *occ = (uint8_t *)malloc((size_t)G);
     if (!occ) return -1;
-    for (int64_t i = 0; i < G; ++i) {
-        occ[i] = 0;
-        for (int64_t v = vmin[i]; v <= vmax[i] && v < N; ++v)
-            if (tf_rgba[4 * v + 3] > 0.0f) { occ[i] = 1; break; }
-    }
+    if (oracle_occ_minmax(vmin, vmax, G, tf_rgba, N, occ)) { free(occ); return -1; }
     int rc = oracle_chamfer_dt(occ, grid, out);
     free(occ);
     return rc;

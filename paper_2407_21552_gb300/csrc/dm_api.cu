@@ -128,8 +128,7 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     g.plane = int64_t(align_up(size_t(g.G), 64));
     x->W = (K + 63) / 64;
     // limits of the kernels' tilings
-    const int nw = (g.gx + 31) / 32;
-    if (size_t(K) * nw * 4 > size_t(dmk::kXpassSmemLimit) ||
+    if (g.gx > 10240 || dmk::xpass_smem(g.gx, K) > size_t(dmk::kXpassSmemLimit) ||
         dmk::line_pass_smem(g.gy) > size_t(dmk::kLineSmemLimit) ||
         dmk::line_pass_smem(g.gz) > size_t(dmk::kLineSmemLimit) || g.gz > 65535 ||
         g.gy > 65535) {
@@ -239,12 +238,11 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
 {
     uint8_t* scratch = static_cast<uint8_t*>(ctx->d_scratch);
     const int K = ctx->cfg.num_partitions, N = ctx->cfg.tf_size;
-    int32_t* cnt = reinterpret_cast<int32_t*>(scratch + ctx->off_cnt);
     uint16_t* act = reinterpret_cast<uint16_t*>(scratch + ctx->off_act);
     int32_t* nact = reinterpret_cast<int32_t*>(scratch + ctx->off_nact);
     uint64_t* smask = reinterpret_cast<uint64_t*>(scratch + ctx->off_smask);
-    cudaError_t e = dmk::launch_tf_active(d_tf, N, K, ctx->borders, cnt, act, nact, smask,
-                                          d_active_mask_out, s);
+    cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->borders, act, nact, smask,
+                                           d_active_mask_out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "active set");
     if (ctx->ev_begin && (e = cudaEventRecord(ctx->ev_begin, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "profile event");

@@ -8,32 +8,35 @@
 // and two passes of the 1D max-min transform h(i) = min_j max(|i-j|, g(j)).  Clamping
 // commutes with every min and max here, so saturating uint8 arithmetic stays exact.
 //
-// x pass: one CTA per block row; warp ballots turn each partition's occupancy along the
-// row into a bit line in shared memory; each output is the distance to the nearest set
-// bit, found with clz/ffs over at most 9 words on either side (>= 256 blocks = 255).
+// x pass: warp ballots turn a row's occupancy into a bit line in shared memory; for every
+// 32-bit word the nearest set bit left of it and right of it are precomputed, so each
+// output is one masked clz/ffs on its own word plus those two lookups.  Four consecutive
+// outputs per thread are stored as one 32-bit word.
 //
 // y / z passes: a CTA stages a tile of 16 neighbouring lines (full line length) in shared
-// memory and builds a doubling table of window minima (level j holds min over 2^j rows,
-// 4 lines per 32-bit word with __vminu4).  h(i) <= t holds exactly when the window of
-// radius t around i has a value <= t, which is monotone in t, so each output is a binary
-// search over t in [1, g(i)] with two table reads per step.  Lines are rewritten in place.
+// memory and builds a doubling table of window minima (level j holds the min over 2^j
+// rows, 4 lines per 32-bit word with __vminu4).  h(i) <= t holds exactly when the window
+// of radius t around i holds a value <= t (monotone in t).  A thread walks a segment of
+// one line: a binary search over t gives h at the segment start; after that h changes by
+// at most 1 per step (h is 1-Lipschitz along the line), so each further output takes at
+// most two window queries.  Results overwrite level 0 and the tile is stored in place.
 #include "dm_internal.cuh"
 
 namespace dmk {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kNone = -30000;          // "no set bit" sentinels for the nearest-bit tables
+constexpr int kFar = 30000;
 
 // ------------------------------------------------------------------------------ x pass
 struct XGeom {
-    int gx, gy, gz;
+    int gx, rows;
     int nw;             // 32-bit words per bit line
-    int64_t G, plane;
+    int64_t plane;
+    int vec4;           // rows are 4-byte aligned: store 4 outputs as one word
 };
 
-struct SrcMask {        // POM bits: partition p is bit p%64 of word p/64
-    const uint64_t* mask;
-};
 struct SrcMinMax8 {     // min/max occupancy: one visible intensity in [min, max]
     const uint16_t* mm;
     const int32_t* cnt;
@@ -46,68 +49,92 @@ struct SrcOcc {         // occupancy bytes (0/1)
     const uint8_t* occ;
 };
 
-__device__ __forceinline__ uint8_t nearest_bit(const uint32_t* __restrict__ bits, int nw, int x)
+// Nearest set bit around x in a bit line: own word by clz/ffs, else the precomputed
+// nearest set bit left (prev) / right (next) of the word; saturates at 255.
+__device__ __forceinline__ unsigned nearest_bit(const uint32_t* __restrict__ bits,
+                                                const int16_t* __restrict__ prev,
+                                                const int16_t* __restrict__ next, int x)
 {
     const int wi = x >> 5, bi = x & 31;
     const uint32_t cur = bits[wi];
-    int dl = 256, dr = 256;
-    uint32_t m = cur & (0xFFFFFFFFu >> (31 - bi));          // bits 0..bi
-    if (m) {
-        dl = bi - (31 - __clz(m));
-    } else {
-        for (int k = wi - 1, s = 0; k >= 0 && s < 9; --k, ++s) {
-            uint32_t w = bits[k];
-            if (w) { dl = x - (k * 32 + 31 - __clz(w)); break; }
-        }
-    }
-    m = cur & (0xFFFFFFFFu << bi);                          // bits bi..31
-    if (m) {
-        dr = __ffs(m) - 1 - bi;
-    } else {
-        for (int k = wi + 1, s = 0; k < nw && s < 9; ++k, ++s) {
-            uint32_t w = bits[k];
-            if (w) { dr = k * 32 + __ffs(w) - 1 - x; break; }
-        }
-    }
-    int d = min(dl, dr);
-    return uint8_t(d > 255 ? 255 : d);
+    const uint32_t ml = cur & (0xFFFFFFFFu >> (31 - bi));   // bits 0..bi
+    const uint32_t mr = cur & (0xFFFFFFFFu << bi);          // bits bi..31
+    const int l = ml ? (wi * 32 + 31 - __clz(ml)) : int(prev[wi]);
+    const int r = mr ? (wi * 32 + __ffs(mr) - 1) : int(next[wi]);
+    const int d = min(x - l, r - x);
+    return unsigned(d > 255 ? 255 : d);
 }
 
-// Occupancy of (row, x) for plane p; templated sources.
-template <int W>
-__device__ __forceinline__ void load_src(const SrcMask& s, int64_t blk, uint64_t (&m)[4])
+// prev[w] / next[w]: nearest set bit strictly left / right of word w of a bit line.
+__device__ __forceinline__ void nearest_tables(const uint32_t* bits, int nw, int16_t* prev,
+                                               int16_t* next)
 {
-#pragma unroll
-    for (int w = 0; w < W; ++w) m[w] = s.mask[blk * W + w];
+    int last = kNone;
+    for (int w = 0; w < nw; ++w) {
+        prev[w] = int16_t(last);
+        const uint32_t b = bits[w];
+        if (b) last = w * 32 + 31 - __clz(b);
+    }
+    int first = kFar;
+    for (int w = nw - 1; w >= 0; --w) {
+        next[w] = int16_t(first);
+        const uint32_t b = bits[w];
+        if (b) first = w * 32 + __ffs(b) - 1;
+    }
 }
 
+// K planes from the POM masks; one CTA per block row, 64 partitions (one mask word) at a
+// time.  Shared memory: bits [cap][nw] uint32, prev / next [cap][nw] int16, cap = min(64, K).
 template <int W>
 __global__ void __launch_bounds__(kThreads)
-k_xpass_mask(SrcMask src, int K, XGeom xg, uint8_t* __restrict__ out)
+k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
 {
-    extern __shared__ uint32_t s_bits[];                     // [K][nw]
+    extern __shared__ uint32_t s_mem[];
+    pdl_wait();
+    const int nw = xg.nw;
+    const int cap = min(64, K);                              // partitions per chunk
+    uint32_t* s_bits = s_mem;
+    int16_t* s_prev = reinterpret_cast<int16_t*>(s_mem + cap * nw);
+    int16_t* s_next = s_prev + cap * nw;
     const int row = blockIdx.x;                              // z * gy + y
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rbase = int64_t(row) * xg.gx;
-    for (int x0 = 0; x0 < xg.gx; x0 += kThreads) {
-        int x = x0 + tid;
-        uint64_t m[4] = {0, 0, 0, 0};
-        if (x < xg.gx) load_src<W>(src, rbase + x, m);
-        const int wi = (x0 >> 5) + warp;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const int pmax = min(64, K - w * 64);
-            for (int q = 0; q < pmax; ++q) {
-                unsigned bal = __ballot_sync(0xFFFFFFFFu, (m[w] >> q) & 1);
-                if (lane == 0 && wi < xg.nw) s_bits[(w * 64 + q) * xg.nw + wi] = bal;
+#pragma unroll 1
+    for (int w = 0; w < W; ++w) {
+        const int np = min(64, K - w * 64);
+        if (w) __syncthreads();                              // previous chunk consumed
+        for (int x0 = 0; x0 < xg.gx; x0 += kThreads) {
+            const int x = x0 + tid;
+            const uint64_t m = x < xg.gx ? mask[(rbase + x) * W + w] : 0;
+            const int wi = (x0 >> 5) + warp;
+            for (int q = 0; q < np; ++q) {
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, (m >> q) & 1);
+                if (lane == 0 && wi < nw) s_bits[q * nw + wi] = bal;
             }
         }
-    }
-    __syncthreads();
-    const int total = K * xg.gx;
-    for (int it = tid; it < total; it += kThreads) {
-        int p = it / xg.gx, x = it - p * xg.gx;
-        out[int64_t(p) * xg.plane + rbase + x] = nearest_bit(s_bits + p * xg.nw, xg.nw, x);
+        __syncthreads();
+        for (int q = tid; q < np; q += kThreads)
+            nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
+        __syncthreads();
+        // outputs: warps over partitions, lanes over groups of 4 consecutive blocks
+        for (int q = warp; q < np; q += kThreads / 32) {
+            const uint32_t* bits = s_bits + q * nw;
+            const int16_t* pv = s_prev + q * nw;
+            const int16_t* nx = s_next + q * nw;
+            uint8_t* dst = out + int64_t(w * 64 + q) * xg.plane + rbase;
+            for (int x = lane * 4; x < xg.gx; x += 128) {
+                if (xg.vec4 && x + 3 < xg.gx) {
+                    unsigned v = nearest_bit(bits, pv, nx, x) |
+                                 (nearest_bit(bits, pv, nx, x + 1) << 8) |
+                                 (nearest_bit(bits, pv, nx, x + 2) << 16) |
+                                 (nearest_bit(bits, pv, nx, x + 3) << 24);
+                    *reinterpret_cast<uint32_t*>(dst + x) = v;
+                } else {
+                    for (int k = 0; k < 4 && x + k < xg.gx; ++k)
+                        dst[x + k] = uint8_t(nearest_bit(bits, pv, nx, x + k));
+                }
+            }
+        }
     }
 }
 
@@ -117,15 +144,15 @@ __device__ __forceinline__ bool occ_of(const Src& s, int64_t blk);
 template <>
 __device__ __forceinline__ bool occ_of<SrcMinMax8>(const SrcMinMax8& s, int64_t blk)
 {
-    uint32_t v = s.mm[blk];
-    uint32_t mn = v & 0xFF, mx = v >> 8;
+    const uint32_t v = s.mm[blk];
+    const uint32_t mn = v & 0xFF, mx = v >> 8;
     return __ldg(s.cnt + mx + 1) > __ldg(s.cnt + mn);
 }
 template <>
 __device__ __forceinline__ bool occ_of<SrcMinMax16>(const SrcMinMax16& s, int64_t blk)
 {
-    uint32_t v = s.mm[blk];
-    uint32_t mn = v & 0xFFFF, mx = v >> 16;
+    const uint32_t v = s.mm[blk];
+    const uint32_t mn = v & 0xFFFF, mx = v >> 16;
     return __ldg(s.cnt + mx + 1) > __ldg(s.cnt + mn);
 }
 template <>
@@ -134,37 +161,56 @@ __device__ __forceinline__ bool occ_of<SrcOcc>(const SrcOcc& s, int64_t blk)
     return s.occ[blk] != 0;
 }
 
-// Single-map x pass (full recompute).  Reads the whole row's occupancy before writing,
-// so `out` may alias the occupancy source.
+// Single-map x pass (full recompute): one warp per block row, 8 rows per CTA.  A warp
+// reads its whole row's occupancy before writing it, so `out` may alias the source.
 template <typename Src>
 __global__ void __launch_bounds__(kThreads)
 k_xpass_single(Src src, XGeom xg, uint8_t* out)
 {
-    extern __shared__ uint32_t s_bits[];                     // [nw]
-    const int row = blockIdx.x;
+    extern __shared__ uint32_t s_mem[];                      // per warp: bits, prev, next
+    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = xg.nw;
+    const int per_warp = nw * 2;                             // words: bits + 2 x int16
+    uint32_t* bits = s_mem + warp * per_warp;
+    int16_t* prev = reinterpret_cast<int16_t*>(bits + nw);
+    int16_t* next = prev + nw;                               // nw int16 + nw int16 = nw words
+    const int row = blockIdx.x * (kThreads / 32) + warp;
+    if (row >= xg.rows) return;                              // warp-uniform
     const int64_t rbase = int64_t(row) * xg.gx;
-    for (int x0 = 0; x0 < xg.gx; x0 += kThreads) {
-        int x = x0 + tid;
-        bool o = x < xg.gx ? occ_of(src, rbase + x) : false;
-        unsigned bal = __ballot_sync(0xFFFFFFFFu, o);
-        const int wi = (x0 >> 5) + warp;
-        if (lane == 0 && wi < xg.nw) s_bits[wi] = bal;
+    for (int x0 = 0; x0 < xg.gx; x0 += 32) {
+        const int x = x0 + lane;
+        const bool o = x < xg.gx ? occ_of(src, rbase + x) : false;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, o);
+        if (lane == 0) bits[x0 >> 5] = bal;
     }
-    __syncthreads();
-    for (int x = tid; x < xg.gx; x += kThreads)
-        out[rbase + x] = nearest_bit(s_bits, xg.nw, x);
+    __syncwarp();
+    if (lane == 0) nearest_tables(bits, nw, prev, next);
+    __syncwarp();
+    uint8_t* dst = out + rbase;
+    for (int x = lane * 4; x < xg.gx; x += 128) {
+        if (xg.vec4 && x + 3 < xg.gx) {
+            unsigned v = nearest_bit(bits, prev, next, x) |
+                         (nearest_bit(bits, prev, next, x + 1) << 8) |
+                         (nearest_bit(bits, prev, next, x + 2) << 16) |
+                         (nearest_bit(bits, prev, next, x + 3) << 24);
+            *reinterpret_cast<uint32_t*>(dst + x) = v;
+        } else {
+            for (int k = 0; k < 4 && x + k < xg.gx; ++k)
+                dst[x + k] = uint8_t(nearest_bit(bits, prev, next, x + k));
+        }
+    }
 }
 
-XGeom xgeom(const Geometry& g, int64_t plane)
+XGeom xgeom(const Geometry& g, int64_t plane, const void* out)
 {
     XGeom x;
     x.gx = g.gx;
-    x.gy = g.gy;
-    x.gz = g.gz;
+    x.rows = g.gy * g.gz;
     x.nw = (g.gx + 31) / 32;
-    x.G = g.G;
     x.plane = plane;
+    x.vec4 = (g.gx % 4 == 0) && (plane % 4 == 0) &&
+             ((reinterpret_cast<uintptr_t>(out) & 3) == 0);
     return x;
 }
 
@@ -176,39 +222,51 @@ struct LineGeom {
     int64_t s;          // element stride along the line
     int64_t os;         // stride of the outer index
     int64_t plane;      // stride between planes
-    int J;              // highest sparse-table level
+    int J;              // highest doubling-table level
+    int seg;            // rows per thread segment
     int vec_ok;         // rows of 16 columns are 16-byte aligned and full
 };
+
+// min of g over rows [r - t, r + t] clipped to the line, from the doubling table
+__device__ __forceinline__ int window_min(const uint8_t* __restrict__ lvl, int L, int r, int t,
+                                          int c)
+{
+    constexpr int TC = kLineTile;
+    const int wl = max(0, r - t), wh = min(L - 1, r + t);
+    const int j = 31 - __clz(wh - wl + 1);
+    const uint8_t* Lj = lvl + j * L * TC;
+    return min(int(Lj[wl * TC + c]), int(Lj[(wh - (1 << j) + 1) * TC + c]));
+}
 
 __global__ void __launch_bounds__(kThreads)
 k_line_pass(uint8_t* buf, LineGeom lg)
 {
     extern __shared__ __align__(16) uint8_t s_lvl[];        // [J+1][L][16]
     constexpr int TC = kLineTile;
+    pdl_wait();
     const int tid = threadIdx.x;
     const int L = lg.L;
     const int x0 = blockIdx.x * TC;
     uint8_t* base = buf + int64_t(blockIdx.z) * lg.plane + int64_t(blockIdx.y) * lg.os + x0;
     const int ncols = min(TC, lg.gx - x0);
 
-    // ---- stage level 0 and note whether the tile can change at all (values >= 2 that
-    //      are not all 255)
+    // ---- stage level 0; note whether the tile can change at all (some value >= 2 and
+    //      not everything 255)
     int any_big = 0, any_not255 = 0;
     if (lg.vec_ok) {
         for (int r = tid; r < L; r += kThreads) {
-            uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(r) * lg.s);
+            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(r) * lg.s);
             reinterpret_cast<uint4*>(s_lvl)[r] = v;
-            unsigned w4[4] = {v.x, v.y, v.z, v.w};
+            const unsigned w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 any_not255 |= (w4[k] != 0xFFFFFFFFu);
-                // a byte >= 2 exists iff some byte has a bit above bit 0 set
-                any_big |= ((w4[k] & 0xFEFEFEFEu) != 0);
+                any_big |= ((w4[k] & 0xFEFEFEFEu) != 0);     // a byte >= 2
             }
         }
     } else {
         for (int i = tid; i < L * TC; i += kThreads) {
-            int r = i / TC, c = i - r * TC;
+            const int r = i / TC, c = i - r * TC;
             uint8_t v = 255;
             if (c < ncols) v = base[int64_t(r) * lg.s + c];
             s_lvl[r * TC + c] = v;
@@ -218,42 +276,60 @@ k_line_pass(uint8_t* buf, LineGeom lg)
     }
     any_big = __syncthreads_or(any_big);
     any_not255 = __syncthreads_or(any_not255);
-    if (!any_big || !any_not255) return;   // all values <= 1 or all 255: h == g
+    if (!any_big || !any_not255) return;   // all values <= 1, or all 255: h == g
 
     // ---- doubling table of window minima, 4 columns per word
     uint32_t* lv = reinterpret_cast<uint32_t*>(s_lvl);
-    const int wpr = TC / 4;                                   // words per row
+    constexpr int wpr = TC / 4;                               // words per row
     for (int j = 1; j <= lg.J; ++j) {
-        const uint32_t* prev = lv + (j - 1) * L * wpr;
+        const uint32_t* prevl = lv + (j - 1) * L * wpr;
         uint32_t* cur = lv + j * L * wpr;
         const int half = 1 << (j - 1);
         for (int i = tid; i < L * wpr; i += kThreads) {
-            int r = i / wpr, q = i - r * wpr;
-            int r2 = min(r + half, L - 1);
-            cur[i] = __vminu4(prev[i], prev[r2 * wpr + q]);
+            const int r = i / wpr, q = i - r * wpr;
+            const int r2 = min(r + half, L - 1);
+            cur[i] = __vminu4(prevl[i], prevl[r2 * wpr + q]);
         }
         __syncthreads();
     }
 
-    // ---- outputs: binary search for the least t with min(window radius t) <= t
-    for (int i = tid; i < L * TC; i += kThreads) {
-        int r = i / TC, c = i - r * TC;
+    // ---- outputs: one thread per (segment, column); results overwrite level 0 (each
+    //      thread reads level 0 only at its own rows; windows of radius >= 1 use j >= 1)
+    const int seg = lg.seg;
+    const int nseg = (L + seg - 1) / seg;
+    for (int item = tid; item < nseg * TC; item += kThreads) {
+        const int c = item % TC, sg = item / TC;
         if (c >= ncols) continue;
-        int gv = s_lvl[r * TC + c];
-        int h = gv;
-        if (gv >= 2) {
-            int lo = 1, hi = gv;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                int wl = max(0, r - mid), wh = min(L - 1, r + mid);
-                int j = 31 - __clz(wh - wl + 1);
-                const uint8_t* Lj = s_lvl + j * L * TC;
-                int m = min(int(Lj[wl * TC + c]), int(Lj[(wh - (1 << j) + 1) * TC + c]));
-                if (m <= mid) hi = mid; else lo = mid + 1;
+        const int r0 = sg * seg, r1 = min(L, r0 + seg);
+        int h = 0;
+        for (int r = r0; r < r1; ++r) {
+            const int gv = s_lvl[r * TC + c];
+            if (gv <= 1) {
+                h = gv;                                      // h == g for g in {0, 1}
+            } else if (r == r0) {
+                int lo = 1, hi = gv;                         // least t with window min <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (window_min(s_lvl, L, r, mid, c) <= mid) hi = mid; else lo = mid + 1;
+                }
+                h = lo;
+            } else {                                         // h(r) in {h-1, h, h+1}
+                if (h - 1 >= 1 && window_min(s_lvl, L, r, h - 1, c) <= h - 1) h = h - 1;
+                else if (window_min(s_lvl, L, r, h, c) > h) h = h + 1;
             }
-            h = lo;
+            s_lvl[r * TC + c] = uint8_t(h);
         }
-        if (h != gv) base[int64_t(r) * lg.s + c] = uint8_t(h);
+    }
+    __syncthreads();
+    // ---- store the tile back in place
+    if (lg.vec_ok) {
+        for (int r = tid; r < L; r += kThreads)
+            *reinterpret_cast<uint4*>(base + int64_t(r) * lg.s) = reinterpret_cast<uint4*>(s_lvl)[r];
+    } else {
+        for (int i = tid; i < L * TC; i += kThreads) {
+            const int r = i / TC, c = i - r * TC;
+            if (c < ncols) base[int64_t(r) * lg.s + c] = s_lvl[r * TC + c];
+        }
     }
 }
 
@@ -266,56 +342,59 @@ size_t line_pass_smem(int L)
     return size_t(J + 1) * size_t(L) * kLineTile;
 }
 
+size_t xpass_smem(int gx, int K)
+{
+    const int nw = (gx + 31) / 32;
+    const size_t mask_pass = size_t(K < 64 ? K : 64) * nw * 8;
+    const size_t single = size_t(kThreads / 32) * nw * 8;
+    return mask_pass > single ? mask_pass : single;
+}
+
 cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, uint8_t* pdm,
                               cudaStream_t s)
 {
-    XGeom xg = xgeom(g, g.plane);
-    size_t smem = size_t(K) * xg.nw * 4;
-    int W = (K + 63) / 64;
-    SrcMask src{mask};
-    const int rows = g.gy * g.gz;
+    XGeom xg = xgeom(g, g.plane, pdm);
+    const size_t smem = size_t(K < 64 ? K : 64) * xg.nw * 8;
+    const int W = (K + 63) / 64;
     cudaError_t e = cudaSuccess;
-#define DM_XPASS_CASE(WW)                                                                   \
-    case WW:                                                                                \
-        e = cudaFuncSetAttribute(k_xpass_mask<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 int(smem));                                                \
-        if (e != cudaSuccess) return e;                                                     \
-        k_xpass_mask<WW><<<rows, kThreads, smem, s>>>(src, K, xg, pdm);                     \
-        break;
     switch (W) {
+#define DM_XPASS_CASE(WW)                                                                    \
+    case WW:                                                                                 \
+        e = ensure_dynamic_smem<k_xpass_mask<WW>>(int(smem));                                \
+        if (e != cudaSuccess) return e;                                                      \
+        return launch_pdl(k_xpass_mask<WW>, dim3(xg.rows), dim3(kThreads), smem, s, mask, K, \
+                          xg, pdm);
         DM_XPASS_CASE(1)
         DM_XPASS_CASE(2)
         DM_XPASS_CASE(3)
         DM_XPASS_CASE(4)
+#undef DM_XPASS_CASE
     default: return cudaErrorInvalidValue;
     }
-#undef DM_XPASS_CASE
-    return cudaGetLastError();
+}
+
+template <typename Src>
+static cudaError_t launch_single(Src src, const Geometry& g, uint8_t* out, cudaStream_t s)
+{
+    XGeom xg = xgeom(g, 0, out);
+    const size_t smem = size_t(kThreads / 32) * xg.nw * 8;
+    cudaError_t e = ensure_dynamic_smem<k_xpass_single<Src>>(int(smem));
+    if (e != cudaSuccess) return e;
+    const int ctas = (xg.rows + kThreads / 32 - 1) / (kThreads / 32);
+    return launch_pdl(k_xpass_single<Src>, dim3(ctas), dim3(kThreads), smem, s, src, xg, out);
 }
 
 cudaError_t launch_xpass_minmax(const void* minmax, const int32_t* cnt, const Geometry& g,
                                 uint8_t* out, cudaStream_t s)
 {
-    XGeom xg = xgeom(g, g.G);
-    size_t smem = size_t(xg.nw) * 4;
-    const int rows = g.gy * g.gz;
-    if (g.bpv == 1) {
-        SrcMinMax8 src{static_cast<const uint16_t*>(minmax), cnt};
-        k_xpass_single<SrcMinMax8><<<rows, kThreads, smem, s>>>(src, xg, out);
-    } else {
-        SrcMinMax16 src{static_cast<const uint32_t*>(minmax), cnt};
-        k_xpass_single<SrcMinMax16><<<rows, kThreads, smem, s>>>(src, xg, out);
-    }
-    return cudaGetLastError();
+    if (g.bpv == 1)
+        return launch_single(SrcMinMax8{static_cast<const uint16_t*>(minmax), cnt}, g, out, s);
+    return launch_single(SrcMinMax16{static_cast<const uint32_t*>(minmax), cnt}, g, out, s);
 }
 
 cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t s)
 {
-    XGeom xg = xgeom(g, g.G);
-    size_t smem = size_t(xg.nw) * 4;
-    SrcOcc src{occ_inout};
-    k_xpass_single<SrcOcc><<<g.gy * g.gz, kThreads, smem, s>>>(src, xg, occ_inout);
-    return cudaGetLastError();
+    return launch_single(SrcOcc{occ_inout}, g, occ_inout, s);
 }
 
 cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
@@ -339,16 +418,17 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
     int J = 0;
     while (J < kMaxLevels - 1 && (2 << J) <= lg.L) ++J;
     lg.J = J;
+    // segments so that the 16 columns x segments of a tile cover about one CTA of threads
+    lg.seg = (lg.L * kLineTile + kThreads - 1) / kThreads;
+    if (lg.seg < 4) lg.seg = 4;
     lg.vec_ok = (g.gx % kLineTile == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
                 (plane % 16 == 0);
-    size_t smem = line_pass_smem(lg.L);
+    const size_t smem = line_pass_smem(lg.L);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_line_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
+    cudaError_t e = ensure_dynamic_smem<k_line_pass>(int(smem));
     if (e != cudaSuccess) return e;
     dim3 grid((g.gx + kLineTile - 1) / kLineTile, lg.n_outer, P);
-    k_line_pass<<<grid, kThreads, smem, s>>>(buf, lg);
-    return cudaGetLastError();
+    return launch_pdl(k_line_pass, grid, dim3(kThreads), smem, s, buf, lg);
 }
 
 }  // namespace dmk

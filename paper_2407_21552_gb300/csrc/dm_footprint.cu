@@ -85,6 +85,7 @@ k_footprint(const T* __restrict__ vol, FpParams prm, const uint8_t* __restrict__
             uint8_t* __restrict__ occ)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    pdl_wait();
     const Geometry& g = prm.g;
     const int tid = threadIdx.x;
     const int tbx = prm.tbx, tby = prm.tby, tw = prm.tile_w, th = prm.tile_h;
@@ -271,13 +272,11 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, const uint8_t
     p.vec_ok = ((reinterpret_cast<uintptr_t>(vol) & 15) == 0) &&
                ((int64_t(g.X) * sz) % 16 == 0) && ((p.tbx * g.b * sz) % 16 == 0) &&
                (int64_t(g.gx) % p.tbx == 0) && (int64_t(g.gx) * g.b == g.X);
-    auto kern = k_footprint<T, W, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
+    cudaError_t e = ensure_dynamic_smem<k_footprint<T, W, MODE>>(int(smem));
     if (e != cudaSuccess) return e;
     dim3 grid((g.gx + p.tbx - 1) / p.tbx, (g.gy + p.tby - 1) / p.tby, g.gz);
-    kern<<<grid, kThreads, smem, s>>>(static_cast<const T*>(vol), p, lut, cnt, mask, minmax, occ);
-    return cudaGetLastError();
+    return launch_pdl(k_footprint<T, W, MODE>, grid, dim3(kThreads), smem, s,
+                      static_cast<const T*>(vol), p, lut, cnt, mask, minmax, occ);
 }
 
 template <typename T>

@@ -2,6 +2,7 @@
 // Internal to libdm: nothing here is part of the public ABI in include/dm.h.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -32,6 +33,55 @@ struct Geometry {
     int64_t plane;          // bytes between PDM planes (G rounded up to 64)
 };
 
+// Programmatic dependent launch (PDL).  A kernel launched with the programmatic stream
+// serialization attribute may start while the previous kernel in the stream still runs;
+// pdl_wait() blocks until that kernel has finished and its writes are visible, and must
+// precede every access to memory the previous kernel touches.  pdl_trigger() lets the
+// next kernel's CTAs launch early.  Both are no-ops for a kernel launched normally.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kern` on `s` with the PDL attribute set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device,
+// calling cudaFuncSetAttribute only when the limit set so far is lower.
+template <auto Kern>
+cudaError_t ensure_dynamic_smem(int bytes)
+{
+    static std::atomic<int> set_to[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && set_to[dev].load(std::memory_order_relaxed) >= bytes)
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) {
+        int cur = set_to[dev].load(std::memory_order_relaxed);
+        while (cur < bytes && !set_to[dev].compare_exchange_weak(cur, bytes)) {
+        }
+    }
+    return e;
+}
+
 // ---------------------------------------------------------------- one-time precompute
 cudaError_t launch_partition_lut(uint8_t* lut, int N, int K, const Borders& bd,
                                  cudaStream_t s);
@@ -59,6 +109,7 @@ cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t
 cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
                              cudaStream_t s);
 size_t line_pass_smem(int L);
+size_t xpass_smem(int gx, int K);
 
 // ---------------------------------------------------------------- per-TF update
 // Visibility prefix count cnt[0..N] (cnt[i] = #{j < i : alpha_j > 0}), active set S as a
@@ -66,6 +117,11 @@ size_t line_pass_smem(int L);
 cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, int32_t* cnt,
                              uint16_t* act, int32_t* nact, uint64_t* smask,
                              uint64_t* smask_out, cudaStream_t s);
+
+// The active set alone (no prefix count), for the update path.
+cudaError_t launch_active_set(const float* tf, int N, int K, const Borders& bd, uint16_t* act,
+                              int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                              cudaStream_t s);
 
 // D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,

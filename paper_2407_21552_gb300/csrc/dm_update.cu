@@ -16,6 +16,7 @@ namespace dmk {
 namespace {
 
 constexpr int kActThreads = 1024;
+constexpr int DM_MAX_TF_WORDS = 65536 / 32;
 constexpr int kCombineThreads = 256;
 
 __global__ void __launch_bounds__(kActThreads)
@@ -26,12 +27,16 @@ k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __r
     __shared__ int32_t s_warp[32];
     __shared__ int32_t s_actw[8];
     __shared__ uint32_t s_bits[8];
+    pdl_trigger();     // the next kernel's CTAs may launch; they wait for this grid
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // contiguous chunk of intensities per thread
+    // contiguous chunk of intensities per thread; visibility kept as bits (chunk <= 64)
     const int per = (N + kActThreads - 1) / kActThreads;
     const int i0 = min(N, tid * per), i1 = min(N, i0 + per);
-    int c = 0;
-    for (int i = i0; i < i1; ++i) c += (__ldg(tf + 4 * int64_t(i) + 3) > 0.0f);
+    uint64_t vbits = 0;
+#pragma unroll 8
+    for (int i = i0; i < i1; ++i)
+        vbits |= uint64_t(__ldg(tf + 4 * int64_t(i) + 3) > 0.0f) << (i - i0);
+    const int c = __popcll(vbits);
     // block exclusive scan of c
     int incl = c;
 #pragma unroll
@@ -55,7 +60,7 @@ k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __r
     int run = s_warp[warp] + incl - c;
     for (int i = i0; i < i1; ++i) {
         cnt[i] = run;
-        run += (__ldg(tf + 4 * int64_t(i) + 3) > 0.0f);
+        run += int((vbits >> (i - i0)) & 1u);
     }
     if (i1 == N && i0 < i1) cnt[N] = run;   // the thread holding intensity N-1
     __syncthreads();                          // cnt is visible to the whole block
@@ -85,6 +90,71 @@ k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __r
     }
 }
 
+// Step 1 of §3.1 for the update path: visibility bits from warp ballots (all loads of a
+// batch issued before any is used), then partition p is active iff a visibility bit in
+// [lo_p, hi_p] is set; compacted ascending.  Lets the combine's CTAs launch at once.
+__global__ void __launch_bounds__(kActThreads)
+k_active_set(const float* __restrict__ tf, int N, int K, Borders bd, uint16_t* __restrict__ act,
+             int32_t* __restrict__ nact, uint64_t* __restrict__ smask,
+             uint64_t* __restrict__ smask_out)
+{
+    pdl_trigger();
+    constexpr int kBatch = 8;
+    __shared__ uint32_t s_vis[DM_MAX_TF_WORDS];
+    __shared__ int32_t s_cnt[8];
+    __shared__ uint32_t s_bits[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int base = 0; base < N; base += kActThreads * kBatch) {
+        float a[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int i = base + k * kActThreads + tid;
+            a[k] = i < N ? __ldg(tf + 4 * int64_t(i) + 3) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int i0 = base + k * kActThreads;          // uniform over the block
+            if (i0 < N) {
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, a[k] > 0.0f);
+                if (lane == 0 && i0 + warp * 32 < N) s_vis[(i0 >> 5) + warp] = bal;
+            }
+        }
+    }
+    __syncthreads();
+    bool on = false;
+    const int p = tid;
+    if (p < K) {
+        const int lo = bd.v[p], hi = bd.v[p + 1] - 1;
+        for (int w = lo >> 5; w <= (hi >> 5) && !on; ++w) {
+            uint32_t m = s_vis[w];
+            if (w == (lo >> 5)) m &= 0xFFFFFFFFu << (lo & 31);
+            if (w == (hi >> 5)) m &= 0xFFFFFFFFu >> (31 - (hi & 31));
+            on = m != 0;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
+    if (lane == 0 && warp < 8) {
+        s_cnt[warp] = __popc(bal);
+        s_bits[warp] = bal;
+    }
+    __syncthreads();
+    if (tid < 256) {
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += s_cnt[w];
+        if (on) act[off + __popc(bal & ((1u << lane) - 1))] = uint16_t(p);
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < 8; ++w) tot += s_cnt[w];
+            *nact = tot;
+        }
+        if (tid < 4) {
+            uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
+            smask[tid] = v;
+            if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
+        }
+    }
+}
+
 __device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b)
 {
     return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
@@ -96,12 +166,15 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
           const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
           uint8_t* __restrict__ out, int vec_ok)
 {
-    __shared__ int64_t s_off[kMaxPartitions];
+    constexpr int kBatch = 8;                          // plane loads issued before any use
+    __shared__ int64_t s_off[kMaxPartitions + kBatch];
     __shared__ int s_n;
+    pdl_wait();        // the active set written by the previous kernel is visible now
     if (threadIdx.x == 0) s_n = *nact;
     __syncthreads();
     const int n = s_n;
-    for (int j = threadIdx.x; j < n; j += kCombineThreads) s_off[j] = int64_t(act[j]) * plane;
+    for (int j = threadIdx.x; j < kMaxPartitions + kBatch; j += kCombineThreads)
+        s_off[j] = j < n ? int64_t(act[j]) * plane : 0;
     __syncthreads();
     const int64_t stride = int64_t(gridDim.x) * kCombineThreads;
     const int64_t t0 = int64_t(blockIdx.x) * kCombineThreads + threadIdx.x;
@@ -111,21 +184,15 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         for (int64_t v = t0; v < nvec; v += stride) {
             uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
             const uint8_t* src = pdm + (v << 4);
-            int j = 0;
-            for (; j + 8 <= n; j += 8) {
-                uint4 d[8];
+            for (int j = 0; j < n; j += kBatch) {
+                uint4 d[kBatch];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    d[k] = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + k]));
+                for (int k = 0; k < kBatch; ++k)
+                    d[k] = (j + k < n) ? __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + k]))
+                                       : make_uint4(~0u, ~0u, ~0u, ~0u);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc = vmin4(acc, d[k]);
+                for (int k = 0; k < kBatch; ++k) acc = vmin4(acc, d[k]);
             }
-            for (; j + 2 <= n; j += 2) {
-                uint4 d0 = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j]));
-                uint4 d1 = __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + 1]));
-                acc = vmin4(acc, vmin4(d0, d1));
-            }
-            if (j < n) acc = vmin4(acc, __ldcs(reinterpret_cast<const uint4*>(src + s_off[j])));
             __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc);
         }
         done = nvec << 4;
@@ -148,6 +215,14 @@ cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_active_set(const float* tf, int N, int K, const Borders& bd, uint16_t* act,
+                              int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                              cudaStream_t s)
+{
+    k_active_set<<<1, kActThreads, 0, s>>>(tf, N, K, bd, act, nact, smask, smask_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
                            const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s)
 {
@@ -157,8 +232,8 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
     int64_t want = (work + kCombineThreads - 1) / kCombineThreads;
     int64_t cap = int64_t(num_sms > 0 ? num_sms : 152) * 8;   // 8 resident CTAs per SM
     int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
-    k_combine<<<blocks, kCombineThreads, 0, s>>>(pdm, plane, G, act, nact, out, vec_ok);
-    return cudaGetLastError();
+    return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), 0, s, pdm, plane, G, act,
+                      nact, out, vec_ok);
 }
 
 }  // namespace dmk

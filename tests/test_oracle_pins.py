@@ -268,6 +268,7 @@ def test_minmax_occupancy_matches_prefix_count(small_case):
         vis = tf[:, 3] > 0
         cnt = np.concatenate([[0], np.cumsum(vis)])
         occ = (cnt[c["vmax"].astype(int) + 1] - cnt[c["vmin"].astype(int)]) > 0
+        assert np.array_equal(oracle.occ_minmax(c["vmin"], c["vmax"], tf), occ)
         assert np.array_equal(oracle.full_recompute_minmax(c["vmin"], c["vmax"], tf),
                               scipy_chessboard(occ))
 
