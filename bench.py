@@ -46,7 +46,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ct", "tiny", "large"], default="ct")
+    ap.add_argument("--workload", choices=["ct", "tiny", "large", "batch", "serving"],
+                    default="ct")
+    ap.add_argument("--serve-seconds", type=float, default=1.5,
+                    help="serving workload: arrival window per rate and server")
+    ap.add_argument("--batch-target-us", type=float, default=2000.0,
+                    help="batch workload: latency target for the block-size choice")
     ap.add_argument("--cpu-edits", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -395,6 +400,210 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(res))
 
 
+# ------------------------------------------------------------ batched instances workload
+def run_batch(args, ws, rank, local):
+    """64 volumes of uneven size (sides U[64, 384], uint8 / 12-bit, K 16 / 32), one TF edit
+    each per step: 64 separate update launches vs one batched launch pair vs a CUDA-graph
+    replay of the batched pair.  The autotuner picks the block size and combine grid."""
+    import ctypes
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U8, DM_U16, _abi as A
+    from paper_2407_21552_gb300.autotune import tune
+    from paper_2407_21552_gb300.build import build as build_lib
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+
+    build_lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    specs = synth.batch_specs()
+    n = len(specs)
+    vols = [synth.volume_of(sp["kind"], sp["dims"], sp["seed"], device=dev) for sp in specs]
+    E = max(8, min(64, args.steps + args.warmup))
+    NMAX = max(sp["N"] for sp in specs)
+    edits = torch.zeros((E, n, NMAX, 4), dtype=torch.float32, device=dev)
+    for i, sp in enumerate(specs):
+        seq = synth.tf_edit_sequence(sp["seed"], sp["N"], E)
+        edits[:, i, : sp["N"]] = torch.from_numpy(np.stack(seq)).to(dev)
+    engines = {}
+
+    def build(b):
+        if b not in engines:
+            engs = []
+            for sp, v in zip(specs, vols):
+                X, Y, Z = sp["dims"]
+                e = PartitionedDistanceMaps((X, Y, Z), DM_U8 if sp["kind"] == "u8" else DM_U16,
+                                            b, 1, sp["K"], sp["N"], device=dev, with_minmax=False)
+                e.build_partitions(v)
+                e.release_mask()
+                engs.append(e)
+            torch.cuda.synchronize(dev)
+            outs = [torch.empty(e.G, dtype=torch.uint8, device=dev) for e in engs]
+            engines[b] = (engs, outs)
+        return engines[b]
+
+    def items_for(b, k):
+        engs, outs = build(b)
+        return [(e.ctx, edits[k, i].data_ptr(), outs[i].data_ptr()) for i, e in enumerate(engs)]
+
+    tr = tune(lambda b: items_for(b, 0), args.batch_target_us, device=dev)
+    engs, outs = build(tr.block)
+    stream = torch.cuda.current_stream(dev)
+    sp_ = ctypes.c_void_p(stream.cuda_stream)
+    # graph of the batched pair reading fixed TF buffers
+    tf_fixed = torch.zeros((n, NMAX, 4), dtype=torch.float32, device=dev)
+    fixed_items = [(e.ctx, tf_fixed[i].data_ptr(), outs[i].data_ptr()) for i, e in enumerate(engs)]
+    A.dm_update_tf_batch(fixed_items, tr.ctas_per_sm, sp_)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        A.dm_update_tf_batch(fixed_items, tr.ctas_per_sm,
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    flush_w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.int64, device=dev)
+
+    def flush():
+        flush_w.zero_()
+        flush_r.max()
+    for k in range(args.warmup):
+        for i, e in enumerate(engs):
+            e.update_tf(edits[k % E, i, : specs[i]["N"]], out=outs[i])
+        A.dm_update_tf_batch(items_for(tr.block, k % E), tr.ctas_per_sm, sp_)
+        tf_fixed.copy_(edits[k % E])
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    clocks = ClockSampler(smi_gpu_id(dev))
+    clocks.start()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    r0.record(stream)
+    for k in range(K):
+        kk = k % E
+        flush()
+        ev[k][0].record(stream)
+        for i, e in enumerate(engs):
+            e.update_tf(edits[kk, i, : specs[i]["N"]], out=outs[i])
+        ev[k][1].record(stream)
+        items_k = items_for(tr.block, kk)            # host-side list, built before timing
+        flush()
+        ev[k][2].record(stream)
+        A.dm_update_tf_batch(items_k, tr.ctas_per_sm, sp_)
+        ev[k][3].record(stream)
+        flush()
+        ev[k][4].record(stream)
+        tf_fixed.copy_(edits[kk])
+        graph.replay()
+        ev[k][5].record(stream)
+    r1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    sep = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    bat = [ev[k][2].elapsed_time(ev[k][3]) for k in range(K)]
+    gra = [ev[k][4].elapsed_time(ev[k][5]) for k in range(K)]
+    vox = sum(int(np.prod(sp["dims"])) for sp in specs)
+    if rank != 0:
+        return
+    res = {
+        "metric": METRIC + " (batched instances)", "value": pct(bat, 50), "unit": "ms",
+        "n_gpus": ws, "steps": K, "warmup": args.warmup, "ms_per_step": r0.elapsed_time(r1) / K,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"batch: {n} volumes, sides U[64,384], uint8/12-bit, K 16/32, "
+                               f"one TF edit each", "voxels": vox,
+                   "l2": "flushed before every timed call (256 MiB write, then 256 MiB read)"},
+        "separate_launches": {"p50_ms": pct(sep, 50), "p99_ms": pct(sep, 99),
+                              "launches": 2 * n},
+        "batched": {"p50_ms": pct(bat, 50), "p99_ms": pct(bat, 99), "launches": 2},
+        "batched_graph": {"p50_ms": pct(gra, 50), "p99_ms": pct(gra, 99),
+                          "note": "includes the device copy of the 64 TFs into the "
+                                  "graph's fixed buffers"},
+        "speedup_batched_vs_separate_p50": pct(sep, 50) / pct(bat, 50),
+        "autotune": {"block": tr.block, "combine_ctas_per_sm": tr.ctas_per_sm,
+                     "target_us": args.batch_target_us,
+                     "table_us": {f"b{b}_c{c}": v for (b, c), v in tr.table.items()}},
+        "gpu_launches": K * (2 * n + 2 + 2),
+        "clocks": clk,
+    }
+    print(json.dumps(res))
+
+
+# -------------------------------------------------------------------- serving workload
+def run_serving(args, ws, rank, local):
+    """32 sessions (12-bit volumes with sides U[256, 1024], K in {16, 32, 64}) admitted
+    under a 150 GB HBM budget; TF edits arrive as a Poisson process over the sessions at
+    200, 1000 and 5000 edits/s.  The partitioned server batches them continuously onto 3
+    streams; the comparison server runs a full recompute per edit in the same loop."""
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U16
+    from paper_2407_21552_gb300.build import build as build_lib
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    from paper_2407_21552_gb300.serving import DeviceExecutor, Scheduler, SessionSpec
+
+    build_lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(5)
+    n_sess, budget = 32, 150 * 10**9
+    engines, specs = [], []
+    for sid in range(n_sess):
+        side = int(rng.integers(256, 1025))
+        K = int(rng.choice([16, 32, 64]))
+        vol = synth.volume_of("u16", (side, side, side), 2000 + sid, device=dev)
+        eng = PartitionedDistanceMaps((side, side, side), DM_U16, 4, 1, K, 4096, device=dev)
+        eng.build_partitions(vol)
+        eng.release_mask()
+        del vol
+        engines.append(eng)
+        s = eng.sizes
+        specs.append(SessionSpec(sid, int(s.pdm_bytes + s.minmax_bytes + s.scratch_bytes
+                                          + 3 * s.out_bytes), dict(engine=eng)))
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    tfs = [torch.from_numpy(t).pin_memory() for t in synth.tf_edit_sequence(6, 4096, 256)]
+    results = {}
+    for rate in (200, 1000, 5000):
+        for mode in ("partitioned", "full"):
+            ex = DeviceExecutor(slots=3, mode=mode, device=dev)
+            sch = Scheduler(ex, budget, slots=3)
+            for sp in specs:
+                sch.open_session(sp)
+            n_req = max(50, int(rate * args.serve_seconds))
+            gaps = rng.exponential(1.0 / rate, size=n_req)
+            arrive = np.cumsum(gaps)
+            sess = rng.integers(0, n_sess, size=n_req)
+            t0 = time.perf_counter()
+            k = 0
+            while k < n_req or sch.has_work():
+                now = time.perf_counter() - t0
+                while k < n_req and arrive[k] <= now:
+                    sch.submit(int(sess[k]), tfs[k % len(tfs)], t_arrival=t0 + arrive[k])
+                    k += 1
+                sch.poll()
+            wall = time.perf_counter() - t0
+            lat = np.array(sch.stats.latencies) * 1e3
+            results[f"{mode}@{rate}"] = {
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
+                "offered_edits_per_s": rate, "batches": sch.stats.batches,
+                "mean_batch": float(np.mean(sch.stats.batch_sizes))}
+    if rank != 0:
+        return
+    sides = [e.grid[0] * 4 for e in engines]
+    res = {"metric": "serving: TF-update latency p50/p99 (ms) and sustained edits/s",
+           "value": results["partitioned@1000"]["p50_ms"], "unit": "ms", "n_gpus": ws,
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": f"serving: {n_sess} sessions, 12-bit volumes with sides "
+                                  f"{min(sides)}..{max(sides)}, K in {{16,32,64}}, 150 GB "
+                                  f"budget, Poisson arrivals, 3 streams",
+                      "resident_gb": sum(sp.device_bytes for sp in specs) / 1e9},
+           "servers": results}
+    print(json.dumps(res))
+
+
 # --------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -438,6 +647,10 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch":
+        run_batch(args, ws, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

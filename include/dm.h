@@ -144,9 +144,38 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
                             uint8_t *d_out, void *stream);
 
 /*
+ * Batched per-TF update over several volumes (§3.1 steps 1 and 2 for each item).  Item i
+ * updates context items[i].ctx with its device TF (float32 [N_i][4]) into its device
+ * output (uint8 [G_i]); results are those of dm_update_tf on each item alone.  Contexts may
+ * differ in size, voxel type, K and N; each must have been built (dm_build_partitions)
+ * with pdm and scratch bound, and a context may appear at most once per call (its scratch
+ * holds the item's active set).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an
+ * active-set kernel with one CTA per item, then one persistent combine over all items);
+ * longer batches are split.  tuning may be NULL (defaults).  Asynchronous on `stream`; the
+ * launch pair has no host-side dependency on the items, so it can be captured in a CUDA
+ * graph.  Errors: DM_ERR_INVALID_ARG (null / repeated context, null buffers),
+ * DM_ERR_NOT_BOUND (a context not built).
+ */
+#define DM_BATCH_MAX_ITEMS 64
+typedef struct dm_batch_item {
+    dm_ctx *ctx;
+    const float *d_tf_rgba;
+    uint8_t *d_out;
+} dm_batch_item;
+
+typedef struct dm_batch_tuning {
+    int32_t combine_ctas_per_sm;   /* persistent combine grid: CTAs per SM (0 = default 2) */
+    int32_t reserved[3];
+} dm_batch_tuning;
+
+dm_status dm_update_tf_batch(const dm_batch_item *items, int32_t n,
+                             const dm_batch_tuning *tuning, void *stream);
+
+/*
  * Instrumentation: when set, dm_update_tf() records `ev_begin` on its stream right before
  * the combine kernel (Eq. 1) is launched and `ev_end` right after it, so a caller can time
- * that kernel alone with cudaEventElapsedTime.  Both are cudaEvent_t created by the caller
+ * that kernel alone with cudaEventElapsedTime (for tf_size <= 8192 the combine kernel also
+ * derives the active set, so the events bracket the whole update).  Both are cudaEvent_t created by the caller
  * (owned by the caller); pass NULL, NULL to stop.  No effect on results.
  */
 dm_status dm_set_profile_events(dm_ctx *ctx, void *ev_begin, void *ev_end);

@@ -24,11 +24,12 @@ DM_MAX_TF_SIZE = 65536
 DM_MAX_BLOCK = 16
 DM_NOALLOC_MAX_TF_SIZE = 16384
 DM_NOALLOC_SCRATCH_BYTES = 4096
+DM_BATCH_MAX_ITEMS = 64
 
 #: every function declared in include/dm.h
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-            "dm_update_tf_noalloc", "dm_sync", "dm_destroy",
+            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_sync", "dm_destroy",
             "dm_last_error_string", "dm_status_string", "dm_version")
 
 
@@ -44,6 +45,15 @@ class dm_sizes(ctypes.Structure):
                 ("plane_stride", ctypes.c_size_t), ("minmax_bytes", ctypes.c_size_t),
                 ("scratch_bytes", ctypes.c_size_t), ("out_bytes", ctypes.c_size_t),
                 ("grid", ctypes.c_int32 * 3), ("mask_words", ctypes.c_int32)]
+
+
+class dm_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("d_tf_rgba", ctypes.c_void_p),
+                ("d_out", ctypes.c_void_p)]
+
+
+class dm_batch_tuning(ctypes.Structure):
+    _fields_ = [("combine_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class DmError(RuntimeError):
@@ -75,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.dm_full_recompute.argtypes = [P, P, P, P, P]
     lib.dm_set_profile_events.argtypes = [P, P, P]
     lib.dm_update_tf_noalloc.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, S, P, S, P, P, P]
+    lib.dm_update_tf_batch.argtypes = [ctypes.POINTER(dm_batch_item), S,
+                                       ctypes.POINTER(dm_batch_tuning), P]
     lib.dm_sync.argtypes = [P, P]
     lib.dm_destroy.argtypes = [P]
     lib.dm_destroy.restype = None
@@ -85,7 +97,7 @@ def load(path: str = LIB_PATH):
     lib.dm_version.argtypes = []
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-              "dm_update_tf_noalloc", "dm_sync", "dm_version"):
+              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_sync", "dm_version"):
         getattr(lib, n).restype = S
     _lib = lib
     return lib
@@ -181,6 +193,24 @@ def dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, border
                                      tf_size, d_tf_rgba, d_out, stream)
     if st != DM_OK:
         raise DmError(st, "dm_update_tf_noalloc")
+
+
+def dm_update_tf_batch(items, tuning=None, stream=None):
+    """items: sequence of (ctx, d_tf_rgba, d_out) device pointers; tuning: ctas per SM of
+    the persistent combine (None = library default)."""
+    n = len(items)
+    arr = (dm_batch_item * max(1, n))()
+    for i, (c, tf, out) in enumerate(items):
+        arr[i].ctx, arr[i].d_tf_rgba, arr[i].d_out = c, tf, out
+    tp = None
+    if tuning is not None:
+        t = dm_batch_tuning()
+        t.combine_ctas_per_sm = int(tuning)
+        tp = ctypes.byref(t)
+    st = load().dm_update_tf_batch(arr, n, tp, stream)
+    if st != DM_OK:
+        detail = load().dm_last_error_string(items[0][0]).decode() if n else ""
+        raise DmError(st, "dm_update_tf_batch", detail)
 
 
 def dm_sync(ctx, stream):

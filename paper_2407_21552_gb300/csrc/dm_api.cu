@@ -241,6 +241,21 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
     uint16_t* act = reinterpret_cast<uint16_t*>(scratch + ctx->off_act);
     int32_t* nact = reinterpret_cast<int32_t*>(scratch + ctx->off_nact);
     uint64_t* smask = reinterpret_cast<uint64_t*>(scratch + ctx->off_smask);
+    if (dmk::update_fused_ok(N)) {          // one launch: every CTA derives S itself
+        if (ctx->ev_begin) {
+            cudaError_t e = cudaEventRecord(ctx->ev_begin, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "profile event");
+        }
+        cudaError_t e = dmk::launch_update_fused(static_cast<const uint8_t*>(ctx->d_pdm),
+                                                 ctx->geo.plane, ctx->geo.G, d_tf, N, K,
+                                                 ctx->borders, act, nact, smask,
+                                                 d_active_mask_out, d_out, ctx->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "update");
+        if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "profile event");
+        ctx->err[0] = 0;
+        return DM_OK;
+    }
     cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->borders, act, nact, smask,
                                            d_active_mask_out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "active set");
@@ -331,6 +346,53 @@ dm_status dm_full_recompute(dm_ctx* ctx, const void* d_volume, const float* d_tf
     e = dmk::launch_line_pass(d_out, 1, 0, ctx->geo, 2, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "DT z pass");
     ctx->err[0] = 0;
+    return DM_OK;
+}
+
+dm_status dm_update_tf_batch(const dm_batch_item* items, int32_t n, const dm_batch_tuning* tuning,
+                             void* stream)
+{
+    if (!items || n < 0) return DM_ERR_INVALID_ARG;
+    if (n == 0) return DM_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        dm_ctx* c = items[i].ctx;
+        if (!c || !items[i].d_tf_rgba || !items[i].d_out ||
+            (reinterpret_cast<uintptr_t>(items[i].d_tf_rgba) & 3))
+            return c ? fail(c, DM_ERR_INVALID_ARG, "dm_update_tf_batch: item %d: null or "
+                            "misaligned buffer", i) : DM_ERR_INVALID_ARG;
+        if (!c->d_pdm || !c->d_scratch || !c->built)
+            return fail(c, DM_ERR_NOT_BOUND, "dm_update_tf_batch: item %d: context not built", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (items[j].ctx == c)
+                return fail(c, DM_ERR_INVALID_ARG, "dm_update_tf_batch: context repeated "
+                            "(items %d and %d)", j, i);
+    }
+    dm_ctx* first = items[0].ctx;
+    dm_status st = check_sticky(first, "dm_update_tf_batch (earlier work)");
+    if (st != DM_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    const int per_sm = tuning ? tuning->combine_ctas_per_sm : 0;
+    dmk::BatchDesc desc[dmk::kMaxBatch];
+    for (int32_t i0 = 0; i0 < n; i0 += dmk::kMaxBatch) {
+        const int m = (n - i0) < dmk::kMaxBatch ? (n - i0) : dmk::kMaxBatch;
+        for (int k = 0; k < m; ++k) {
+            dm_ctx* c = items[i0 + k].ctx;
+            uint8_t* scratch = static_cast<uint8_t*>(c->d_scratch);
+            dmk::BatchDesc& d = desc[k];
+            d.pdm = static_cast<const uint8_t*>(c->d_pdm);
+            d.plane = c->geo.plane;
+            d.G = c->geo.G;
+            d.tf = items[i0 + k].d_tf_rgba;
+            d.out = items[i0 + k].d_out;
+            d.lut = scratch + c->off_lut;
+            d.act = reinterpret_cast<uint16_t*>(scratch + c->off_act);
+            d.nact = reinterpret_cast<int32_t*>(scratch + c->off_nact);
+            d.N = c->cfg.tf_size;
+            d.K = c->cfg.num_partitions;
+        }
+        cudaError_t e = dmk::launch_update_batch(desc, m, per_sm, first->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched update");
+    }
     return DM_OK;
 }
 

@@ -1,0 +1,190 @@
+// dm_batch.cu -- the per-TF update for many volumes at once.
+//
+// Each item is one volume's resident PDMs (§3.1) with its own TF.  Two launches cover up
+// to kMaxBatch items: an active-set kernel with one CTA per item (§3.1 step 1, from the
+// item's partition table built at precompute time), then a persistent combine (Eq. 1) over
+// one flattened list of 4 KiB work units of all items, launched with programmatic
+// dependent launch.  Per-item descriptors are passed by value as kernel parameters, so
+// the pair needs no device-side setup and can be captured in a CUDA graph.
+#include "dm_internal.cuh"
+
+namespace dmk {
+namespace {
+
+constexpr int kActThreads = 1024;
+constexpr int kThreads = 256;                  // combine CTA; one work unit = 256 x 16 B
+
+struct Item {
+    const uint8_t* pdm;
+    int64_t plane;
+    int64_t G;
+    const float* tf;
+    uint8_t* out;
+    const uint8_t* lut;                        // partition of each intensity (precompute)
+    uint16_t* act;                             // active list and count (item's scratch)
+    int32_t* nact;
+    int32_t N, K;
+    int32_t vec;                               // 16-byte units (else bytes)
+};
+
+struct Params {
+    int n;
+    int64_t unit_prefix[kMaxBatch + 1];        // work units before item i (256 lanes each)
+    Item it[kMaxBatch];
+};
+
+__device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b)
+{
+    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
+                      __vminu4(a.w, b.w));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(sa), "l"(gmem)
+                 : "memory");
+}
+
+// §3.1 step 1 for item blockIdx.x: partition lut[i] is active when alpha_i > 0.
+__global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_constant__ Params P)
+{
+    pdl_trigger();
+    __shared__ uint32_t s_S[kMaxPartitions / 32];
+    __shared__ int s_cnt[8];
+    const Item& it = P.it[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kMaxPartitions / 32) s_S[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < it.N; i += kActThreads) {
+        if (__ldg(it.tf + 4 * int64_t(i) + 3) > 0.0f) {
+            const unsigned p = it.lut[i];
+            atomicOr(&s_S[p >> 5], 1u << (p & 31));
+        }
+    }
+    __syncthreads();
+    const bool on = tid < it.K && ((s_S[tid >> 5] >> (tid & 31)) & 1u);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
+    if (lane == 0 && warp < 8) s_cnt[warp] = __popc(bal);
+    __syncthreads();
+    if (tid < 256) {
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += s_cnt[w];
+        if (on) it.act[off + __popc(bal & ((1u << lane) - 1))] = uint16_t(tid);
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < 8; ++w) tot += s_cnt[w];
+            *it.nact = tot;
+        }
+    }
+}
+
+// Eq. 1 over every item's work units; CTA b takes a contiguous range of units.
+__global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constant__ Params P)
+{
+    constexpr int kB = 8;                                     // plane loads per group
+    __shared__ int64_t s_off[kMaxPartitions + kB];
+    __shared__ int s_n;
+    extern __shared__ uint4 s_dyn[];                          // [2][kB][kThreads] staging
+    uint4 (*s_stage)[kB][kThreads] = reinterpret_cast<uint4 (*)[kB][kThreads]>(s_dyn);
+    pdl_wait();                                               // active sets are visible
+    const int tid = threadIdx.x;
+    const int64_t total = P.unit_prefix[P.n];
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t u0 = int64_t(blockIdx.x) * per, u1 = min(total, u0 + per);
+    int item = 0;
+    while (item < P.n && P.unit_prefix[item + 1] <= u0) ++item;
+    int loaded = -1;
+    for (int64_t u = u0; u < u1; ++u) {
+        while (P.unit_prefix[item + 1] <= u) ++item;
+        const Item& it = P.it[item];
+        if (item != loaded) {                                 // this item's active planes
+            __syncthreads();
+            if (tid == 0) s_n = *it.nact;
+            __syncthreads();
+            const int n = s_n;
+            for (int j = tid; j < kMaxPartitions + kB; j += kThreads)
+                s_off[j] = int64_t(it.act[j < n ? j : 0]) * it.plane;
+            __syncthreads();
+            loaded = item;
+        }
+        const int n = s_n;
+        const int64_t lane_unit = (u - P.unit_prefix[item]) * kThreads + tid;
+        if (it.vec) {
+            const int64_t nvec = it.G >> 4;
+            if (lane_unit < nvec) {
+                const uint8_t* src = it.pdm + (lane_unit << 4);
+                uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+                const int nb = (n + kB - 1) / kB;
+                if (nb > 0) {
+                    for (int k = 0; k < kB; ++k) cp_async16(&s_stage[0][k][tid], src + s_off[k]);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                }
+                for (int b = 0; b < nb; ++b) {
+                    if (b + 1 < nb)
+                        for (int k = 0; k < kB; ++k)
+                            cp_async16(&s_stage[(b + 1) & 1][k][tid], src + s_off[(b + 1) * kB + k]);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) acc = vmin4(acc, s_stage[b & 1][k][tid]);
+                }
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                __stcs(reinterpret_cast<uint4*>(it.out + (lane_unit << 4)), acc);
+            }
+            // the last < 16 bytes of a vectorised item: first unit's thread 0
+            if (u == P.unit_prefix[item] && tid == 0) {
+                for (int64_t i = nvec << 4; i < it.G; ++i) {
+                    unsigned a = 255;
+                    for (int j = 0; j < n; ++j) a = min(a, unsigned(it.pdm[s_off[j] + i]));
+                    it.out[i] = uint8_t(a);
+                }
+            }
+        } else if (lane_unit < it.G) {
+            unsigned a = 255;
+            for (int j = 0; j < n; ++j) a = min(a, unsigned(it.pdm[s_off[j] + lane_unit]));
+            it.out[lane_unit] = uint8_t(a);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, int num_sms,
+                                cudaStream_t s)
+{
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    Params P;
+    P.n = n;
+    P.unit_prefix[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const BatchDesc& d = items[i];
+        Item& it = P.it[i];
+        it.pdm = d.pdm;
+        it.plane = d.plane;
+        it.G = d.G;
+        it.tf = d.tf;
+        it.out = d.out;
+        it.lut = d.lut;
+        it.act = d.act;
+        it.nact = d.nact;
+        it.N = d.N;
+        it.K = d.K;
+        it.vec = ((reinterpret_cast<uintptr_t>(d.pdm) & 15) == 0) &&
+                 ((reinterpret_cast<uintptr_t>(d.out) & 15) == 0) && (d.plane % 16 == 0);
+        const int64_t units = it.vec ? (d.G >> 4) : d.G;
+        P.unit_prefix[i + 1] = P.unit_prefix[i] + (units + kThreads - 1) / kThreads + (units == 0);
+    }
+    k_active_batch<<<n, kActThreads, 0, s>>>(P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = P.unit_prefix[n];
+    int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 2);
+    if (ctas > total) ctas = total;
+    const size_t smem = size_t(2) * 8 * kThreads * sizeof(uint4);
+    e = ensure_dynamic_smem<k_combine_batch>(int(smem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_combine_batch, dim3(unsigned(ctas)), dim3(kThreads), smem, s, P);
+}
+
+}  // namespace dmk

@@ -123,8 +123,34 @@ cudaError_t launch_active_set(const float* tf, int N, int K, const Borders& bd, 
                               int32_t* nact, uint64_t* smask, uint64_t* smask_out,
                               cudaStream_t s);
 
+// Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
+bool update_fused_ok(int N);
+cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
+                                int N, int K, const Borders& bd, uint16_t* act, int32_t* nact,
+                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
+                                cudaStream_t s);
+
 // D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
                            const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched update
+constexpr int kMaxBatch = 64;          // items per launch pair (descriptors as parameters)
+
+struct BatchDesc {
+    const uint8_t* pdm;
+    int64_t plane, G;
+    const float* tf;
+    uint8_t* out;
+    const uint8_t* lut;                // the item's partition table (its scratch)
+    uint16_t* act;                     // the item's active list and count (its scratch)
+    int32_t* nact;
+    int32_t N, K;
+};
+
+// Active sets of up to kMaxBatch items (one CTA each), then one persistent combine over
+// all their work units (PDL); `ctas_per_sm` sizes the combine grid (<= 0: 2).
+cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, int num_sms,
+                                cudaStream_t s);
 
 }  // namespace dmk

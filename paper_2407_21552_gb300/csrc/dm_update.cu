@@ -161,6 +161,70 @@ __device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b)
                       __vminu4(a.w, b.w));
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(sa), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// D' for `nvec` 16-byte chunks through cp.async: each thread streams its chunk of every
+// active plane into its own shared-memory slots, kAsyncBatch planes per group with two
+// groups in flight (no registers held by the loads), and folds a group once it landed.
+// `stage` is this thread's [2][kAsyncBatch] slot array (stride `ld` uint4 between slots);
+// s_off is padded as for combine_chunks.
+constexpr int kAsyncBatch = 8;
+
+__device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__ pdm,
+                                                     const int64_t* s_off, int n, int64_t nvec,
+                                                     int64_t t0, int64_t stride, uint4* stage,
+                                                     int ld, uint8_t* __restrict__ out)
+{
+    const int nb = (n + kAsyncBatch - 1) / kAsyncBatch;       // batches per chunk
+    if (nb == 0) {
+        for (int64_t v = t0; v < nvec; v += stride)
+            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), make_uint4(~0u, ~0u, ~0u, ~0u));
+        return;
+    }
+    // flattened sequence of (chunk, batch) steps; step i+1 is issued before step i is used
+    int64_t v = t0;
+    int jb = 0;
+    auto issue = [&](int64_t vv, int b, int slot) {
+        const uint8_t* src = pdm + (vv << 4);
+#pragma unroll
+        for (int k = 0; k < kAsyncBatch; ++k)
+            cp_async16(stage + (slot * kAsyncBatch + k) * ld, src + s_off[b * kAsyncBatch + k]);
+        cp_async_commit();
+    };
+    if (v >= nvec) return;
+    issue(v, 0, 0);
+    int slot = 0;
+    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+    while (true) {
+        // next step
+        int64_t nv = v;
+        int njb = jb + 1;
+        if (njb == nb) { njb = 0; nv = v + stride; }
+        const bool more = nv < nvec;
+        if (more) issue(nv, njb, slot ^ 1); else cp_async_commit();
+        cp_async_wait1();                                     // step (v, jb) landed
+#pragma unroll
+        for (int k = 0; k < kAsyncBatch; ++k) acc = vmin4(acc, stage[(slot * kAsyncBatch + k) * ld]);
+        if (jb == nb - 1) {
+            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc);
+            acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+        if (!more) break;
+        v = nv;
+        jb = njb;
+        slot ^= 1;
+    }
+    cp_async_wait0();
+}
+
 __global__ void __launch_bounds__(kCombineThreads)
 k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
           const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
@@ -169,33 +233,21 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     constexpr int kBatch = 8;                          // plane loads issued before any use
     __shared__ int64_t s_off[kMaxPartitions + kBatch];
     __shared__ int s_n;
+    extern __shared__ uint4 s_stage[];                 // [2][kAsyncBatch][kCombineThreads]
     pdl_wait();        // the active set written by the previous kernel is visible now
     if (threadIdx.x == 0) s_n = *nact;
     __syncthreads();
     const int n = s_n;
     for (int j = threadIdx.x; j < kMaxPartitions + kBatch; j += kCombineThreads)
-        s_off[j] = j < n ? int64_t(act[j]) * plane : 0;
+        s_off[j] = int64_t(act[j < n ? j : 0]) * plane;      // padding: copies of plane 0
     __syncthreads();
     const int64_t stride = int64_t(gridDim.x) * kCombineThreads;
     const int64_t t0 = int64_t(blockIdx.x) * kCombineThreads + threadIdx.x;
     int64_t done = 0;
     if (vec_ok) {
-        const int64_t nvec = G >> 4;
-        for (int64_t v = t0; v < nvec; v += stride) {
-            uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
-            const uint8_t* src = pdm + (v << 4);
-            for (int j = 0; j < n; j += kBatch) {
-                uint4 d[kBatch];
-#pragma unroll
-                for (int k = 0; k < kBatch; ++k)
-                    d[k] = (j + k < n) ? __ldcs(reinterpret_cast<const uint4*>(src + s_off[j + k]))
-                                       : make_uint4(~0u, ~0u, ~0u, ~0u);
-#pragma unroll
-                for (int k = 0; k < kBatch; ++k) acc = vmin4(acc, d[k]);
-            }
-            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc);
-        }
-        done = nvec << 4;
+        combine_chunks_async(pdm, s_off, n, G >> 4, t0, stride, s_stage + threadIdx.x,
+                             kCombineThreads, out);
+        done = (G >> 4) << 4;
     }
     // bytes not covered by whole aligned chunks
     for (int64_t i = done + t0; i < G; i += stride) {
@@ -205,7 +257,123 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     }
 }
 
+// Step 1 and step 2 in one launch (TFs with N <= kFusedMaxN): every CTA derives S from
+// the alpha channel itself (independent loads, ballots into a visibility bit set in shared
+// memory, one scan per partition), so the combine waits on no other kernel.  CTA 0 also
+// publishes S (list, count, bit set) for callers that read it back.
+constexpr int kFusedThreads = 512;
+constexpr int kFusedMaxN = 8192;
+
+__global__ void __launch_bounds__(kFusedThreads)
+k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
+               const float* __restrict__ tf, int N, int K, Borders bd,
+               uint16_t* __restrict__ act, int32_t* __restrict__ nact,
+               uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
+               uint8_t* __restrict__ out, int vec_ok)
+{
+    constexpr int kBatch = 8;
+    constexpr int kPer = kFusedMaxN / kFusedThreads;          // alphas per thread (max)
+    __shared__ uint32_t s_vis[kFusedMaxN / 32];
+    __shared__ int64_t s_off[kMaxPartitions + kBatch];
+    __shared__ int s_cnt[8];
+    __shared__ uint32_t s_bits[8];
+    extern __shared__ uint4 s_stage[];                 // [2][kAsyncBatch][kFusedThreads]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();
+    // ---- visibility bits: thread t holds intensities t + k * blockDim
+    float a[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = k * kFusedThreads + tid;
+        a[k] = i < N ? __ldg(tf + 4 * int64_t(i) + 3) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (k * kFusedThreads < N) {                          // uniform over the block
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, a[k] > 0.0f);
+            const int word = (k * kFusedThreads >> 5) + warp;
+            if (lane == 0 && word * 32 < N) s_vis[word] = bal;
+        }
+    }
+    __syncthreads();
+    // ---- S: partition p active iff a visibility bit in [lo_p, hi_p] is set
+    bool on = false;
+    if (tid < K) {
+        const int lo = bd.v[tid], hi = bd.v[tid + 1] - 1;
+        for (int w = lo >> 5; w <= (hi >> 5) && !on; ++w) {
+            uint32_t m = s_vis[w];
+            if (w == (lo >> 5)) m &= 0xFFFFFFFFu << (lo & 31);
+            if (w == (hi >> 5)) m &= 0xFFFFFFFFu >> (31 - (hi & 31));
+            on = m != 0;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
+    if (lane == 0 && warp < 8) {
+        s_cnt[warp] = __popc(bal);
+        s_bits[warp] = bal;
+    }
+    __syncthreads();
+    int n = 0;
+    for (int w = 0; w < 8; ++w) n += s_cnt[w];
+    if (tid < 256) {
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += s_cnt[w];
+        const int pos = off + __popc(bal & ((1u << lane) - 1));
+        if (on) {
+            s_off[pos] = int64_t(tid) * plane;
+            if (blockIdx.x == 0) act[pos] = uint16_t(tid);
+        }
+        if (blockIdx.x == 0) {
+            if (tid == 0) *nact = n;
+            if (tid < 4) {
+                const uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
+                smask[tid] = v;
+                if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < kBatch && n > 0) s_off[n + tid] = s_off[0];    // padding: copies of an active plane
+    __syncthreads();
+    // ---- Eq. 1 over the active planes
+    const int64_t stride = int64_t(gridDim.x) * kFusedThreads;
+    const int64_t t0 = int64_t(blockIdx.x) * kFusedThreads + tid;
+    int64_t done = 0;
+    if (vec_ok) {
+        combine_chunks_async(pdm, s_off, n, G >> 4, t0, stride, s_stage + tid, kFusedThreads,
+                             out);
+        done = (G >> 4) << 4;
+    }
+    for (int64_t i = done + t0; i < G; i += stride) {
+        unsigned acc = 255;
+        for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
+        out[i] = uint8_t(acc);
+    }
+}
+
 }  // namespace
+
+bool update_fused_ok(int N) { return N <= kFusedMaxN; }
+
+cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
+                                int N, int K, const Borders& bd, uint16_t* act, int32_t* nact,
+                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
+                                cudaStream_t s)
+{
+    if (N > kFusedMaxN) return cudaErrorInvalidValue;
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (plane % 16 == 0);
+    const int64_t work = vec_ok ? (G >> 4) : G;
+    const int64_t want = (work + kFusedThreads - 1) / kFusedThreads;
+    const size_t smem = vec_ok ? size_t(2) * kAsyncBatch * kFusedThreads * sizeof(uint4) : 0;
+    const int64_t cap = int64_t(num_sms > 0 ? num_sms : 152);  // one 512-thread CTA per SM
+    const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
+    cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
+    if (e != cudaSuccess) return e;
+    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, bd, act, nact,
+                                                      smask, smask_out, out, vec_ok);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, int32_t* cnt,
                              uint16_t* act, int32_t* nact, uint64_t* smask,
@@ -230,10 +398,13 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
                        ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (plane % 16 == 0);
     int64_t work = vec_ok ? (G >> 4) : G;
     int64_t want = (work + kCombineThreads - 1) / kCombineThreads;
-    int64_t cap = int64_t(num_sms > 0 ? num_sms : 152) * 8;   // 8 resident CTAs per SM
+    const size_t smem = vec_ok ? size_t(2) * kAsyncBatch * kCombineThreads * sizeof(uint4) : 0;
+    int64_t cap = int64_t(num_sms > 0 ? num_sms : 152) * 3;   // 3 resident CTAs per SM
     int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
-    return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), 0, s, pdm, plane, G, act,
-                      nact, out, vec_ok);
+    cudaError_t e = ensure_dynamic_smem<k_combine>(int(smem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), smem, s, pdm, plane, G,
+                      act, nact, out, vec_ok);
 }
 
 }  // namespace dmk

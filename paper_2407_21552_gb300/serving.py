@@ -1,0 +1,224 @@
+"""Serving loop: TF edits from many sessions, continuously batched onto one GPU.
+
+Each session is one volume whose partitioned distance maps (§3.1) stay resident on the
+device.  Sessions are admitted while their device bytes fit the HBM budget (§5: the
+PDMs take n x volumesize / b^3 bytes); the others wait until a session leaves.  TF edits
+arrive at any time.  Whenever a batch slot is free, the scheduler takes, for every session
+with pending edits and no edit on the device, its oldest one (so every edit gets the map
+of its own TF, and a session's working memory is used by one batch at a time), and hands
+the batch to the executor, which runs it on the slot's stream without waiting; batches of
+different sessions overlap on the device.  A request completes when its batch's
+completion event has fired; its latency is arrival to completion.
+
+The scheduler (`Scheduler`) holds no GPU state and is tested with a fake executor; the
+executor for the GPU (`DeviceExecutor`) does every step through libdm: the host TFs are
+copied to each session's device TF buffer on the slot's stream, then one
+dm_update_tf_batch (or, for the comparison server, one dm_full_recompute per edit).
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import time
+from dataclasses import dataclass, field
+
+
+@dataclass
+class Request:
+    session: int
+    tf: object                 # host TF (pinned float32 [N][4]) or anything the executor takes
+    t_arrival: float
+    rid: int = 0
+    t_submit: float = 0.0
+    t_done: float = 0.0
+
+
+@dataclass
+class SessionSpec:
+    sid: int
+    device_bytes: int          # bytes the session keeps resident while admitted
+    payload: object = None     # executor-specific (volume, config, ...)
+
+
+@dataclass
+class Batch:
+    slot: int
+    requests: list
+    handle: object = None
+
+
+@dataclass
+class Stats:
+    latencies: list = field(default_factory=list)
+    batches: int = 0
+    batch_sizes: list = field(default_factory=list)
+    admitted: list = field(default_factory=list)
+    rejected_waits: int = 0
+
+
+class Scheduler:
+    """Admission by budget, per-session FIFO, at most one edit of a session on the device
+    at a time, a fixed number of batches in flight.  `executor` provides admit(spec), release(sid),
+    launch(slot, requests) -> handle, done(handle) -> bool, and clock() -> seconds."""
+
+    def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 64):
+        self.ex = executor
+        self.budget = int(budget_bytes)
+        self.slots = int(slots)
+        self.max_batch = int(max_batch)
+        self.used = 0
+        self.sessions = {}                     # sid -> spec (admitted)
+        self.waiting = collections.deque()     # specs not admitted yet
+        self.pending = collections.OrderedDict()   # sid -> deque of requests
+        self.inflight = []                     # batches on the device
+        self.busy = set()                      # sessions with an edit on the device
+        self.free_slots = list(range(self.slots))
+        self.stats = Stats()
+        self.completed = []
+        self._rid = 0
+
+    # ------------------------------------------------------------------ sessions
+    def open_session(self, spec: SessionSpec) -> bool:
+        """Admit now if the budget allows, else queue it; returns whether admitted."""
+        if spec.device_bytes > self.budget:
+            raise ValueError(f"session {spec.sid} needs more than the whole budget")
+        if not self.waiting and self.used + spec.device_bytes <= self.budget:
+            self._admit(spec)
+            return True
+        self.waiting.append(spec)
+        self.stats.rejected_waits += 1
+        return False
+
+    def _admit(self, spec):
+        self.ex.admit(spec)
+        self.sessions[spec.sid] = spec
+        self.used += spec.device_bytes
+        self.stats.admitted.append(spec.sid)
+
+    def close_session(self, sid: int):
+        """Leave once no edit of the session is pending or in flight; frees its budget."""
+        if any(r.session == sid for b in self.inflight for r in b.requests):
+            raise RuntimeError("session has edits in flight")
+        self.pending.pop(sid, None)
+        spec = self.sessions.pop(sid)
+        self.ex.release(sid)
+        self.used -= spec.device_bytes
+        while self.waiting and self.used + self.waiting[0].device_bytes <= self.budget:
+            self._admit(self.waiting.popleft())
+
+    # ------------------------------------------------------------------ requests
+    def submit(self, sid: int, tf, t_arrival: float | None = None) -> Request:
+        if sid not in self.sessions:
+            raise KeyError(f"session {sid} is not admitted")
+        r = Request(session=sid, tf=tf,
+                    t_arrival=self.ex.clock() if t_arrival is None else t_arrival,
+                    rid=self._rid)
+        self._rid += 1
+        self.pending.setdefault(sid, collections.deque()).append(r)
+        return r
+
+    def has_work(self) -> bool:
+        return bool(self.inflight) or any(self.pending.values())
+
+    # ------------------------------------------------------------------ progress
+    def poll(self):
+        """Retire finished batches, then launch new ones while slots are free."""
+        still = []
+        for b in self.inflight:
+            if self.ex.done(b.handle):
+                t = self.ex.clock()
+                for r in b.requests:
+                    r.t_done = t
+                    self.stats.latencies.append(t - r.t_arrival)
+                    self.completed.append(r)
+                    self.busy.discard(r.session)
+                self.free_slots.append(b.slot)
+            else:
+                still.append(b)
+        self.inflight = still
+        while self.free_slots:
+            reqs = []
+            for sid, q in self.pending.items():
+                if q and sid not in self.busy:
+                    reqs.append(q.popleft())
+                    if len(reqs) == self.max_batch:
+                        break
+            if not reqs:
+                break
+            slot = self.free_slots.pop(0)
+            t = self.ex.clock()
+            for r in reqs:
+                r.t_submit = t
+            self.busy.update(r.session for r in reqs)
+            b = Batch(slot=slot, requests=reqs)
+            b.handle = self.ex.launch(slot, reqs)
+            self.inflight.append(b)
+            self.stats.batches += 1
+            self.stats.batch_sizes.append(len(reqs))
+            # rotate so that sessions with many pending edits do not starve the others
+            for r in reqs:
+                self.pending.move_to_end(r.session)
+
+    def drain(self, timeout_s: float = 60.0):
+        t0 = time.perf_counter()
+        while self.has_work():
+            self.poll()
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("serving loop did not drain")
+
+
+class DeviceExecutor:
+    """Runs batches through libdm on one device.  payload of a SessionSpec: dict with
+    'engine' (maps.PartitionedDistanceMaps, built) and optionally 'volume'."""
+
+    def __init__(self, slots: int = 2, mode: str = "partitioned", device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.mode = mode                      # "partitioned" or "full"
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.sessions = {}
+        self.results = {}                     # rid -> device D' (kept if keep_results)
+        self.keep_results = False
+
+    def clock(self):
+        return time.perf_counter()
+
+    def admit(self, spec):
+        eng = spec.payload["engine"]
+        torch = self.torch
+        tf_dev = torch.empty((eng.N, 4), dtype=torch.float32, device=self.device)
+        outs = [torch.empty(eng.G, dtype=torch.uint8, device=self.device)
+                for _ in range(len(self.streams))]
+        self.sessions[spec.sid] = dict(engine=eng, tf=[tf_dev.clone() for _ in self.streams],
+                                       out=outs, volume=spec.payload.get("volume"))
+
+    def release(self, sid):
+        self.sessions.pop(sid, None)
+
+    def launch(self, slot, requests):
+        from . import _abi as A
+        torch = self.torch
+        st = self.streams[slot]
+        items = []
+        with torch.cuda.stream(st):
+            for r in requests:
+                s = self.sessions[r.session]
+                s["tf"][slot].copy_(r.tf, non_blocking=True)
+                items.append((s["engine"].ctx, s["tf"][slot].data_ptr(), s["out"][slot].data_ptr()))
+            sh = ctypes.c_void_p(st.cuda_stream)
+            if self.mode == "partitioned":
+                A.dm_update_tf_batch(items, None, sh)
+            else:
+                for r, (ctx, tfp, outp) in zip(requests, items):
+                    v = self.sessions[r.session]["volume"]
+                    A.dm_full_recompute(ctx, v.data_ptr() if v is not None else None, tfp, outp, sh)
+            if self.keep_results:
+                for r in requests:
+                    self.results[r.rid] = self.sessions[r.session]["out"][slot].clone()
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return ev
+
+    def done(self, handle):
+        return handle.query()

@@ -6,8 +6,11 @@ the method's arithmetic.  Workload recipes:
 * tiny  : 128^3 uint8, 4^3 blocks (32^3 grid), K=16, N=256, 100 TF edits (seed 0)
 * ct    : 512^3 12-bit uint16, 4^3 blocks (128^3 grid), K=32, N=4096, 1000 edits (seed 1)
 * large : 1024x1024x1795 12-bit uint16, 4^3 blocks (256x256x449 grid), K=64, N=4096 (seed 2)
+* batch : 64 volumes, sides U[64, 384], alternating uint8 / 12-bit, K alternating 16 / 32,
+          one TF edit each (seed 4)
 """
-from .volumes import tiny_volume, ct_volume, large_volume, as_numpy, volume_sha256  # noqa: F401
+from .volumes import (tiny_volume, ct_volume, large_volume, as_numpy, volume_sha256,  # noqa: F401
+                      volume_of, batch_specs)
 from .tfs import (tf_edit_sequence, zero_tf, all_visible_tf, single_intensity_tf,  # noqa: F401
                   aligned_tf, special_tfs, uniform_borders, tf_from_ramps, Ramp)
 

@@ -201,3 +201,48 @@ def as_numpy(vol: torch.Tensor) -> np.ndarray:
 def volume_sha256(vol: torch.Tensor) -> str:
     import hashlib
     return hashlib.sha256(as_numpy(vol).tobytes()).hexdigest()
+
+
+def volume_of(kind: str, dims, seed: int, device="cpu") -> torch.Tensor:
+    """A volume of arbitrary dims (X, Y, Z) from one of the generators above: 'u8' uses the
+    tiny recipe (noise + ellipsoids), 'u16' a CT-like recipe (air, soft tissue, bone), both
+    with their structure scaled to the volume."""
+    X, Y, Z = (int(d) for d in dims)
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    shape = (Z, Y, X)
+    if kind == "u8":
+        s = gaussian_smooth(torch.rand(shape, generator=g).to(device), 2.0)
+        s = (s - s.min()) / (s.max() - s.min() + 1e-12) * 40.0
+        vol = s
+        m0 = min(shape)
+        for e in range(6):
+            centre = rng.uniform(0, 1, size=3) * np.array(shape)
+            radii = rng.uniform(0.05, 0.25, size=3) * m0
+            m = _ellipsoid_mask(shape, centre, radii, device)
+            vals = (80.0, 150.0, 220.0)[e % 3] + 10.0 * torch.randn(shape, generator=g).to(device)
+            vol = torch.where(m, vals, vol)
+        return vol.round().clamp(0, 255).to(torch.uint8)
+    vol = 20.0 * torch.randn(shape, generator=g).to(device)
+    body = _ellipsoid_mask(shape, (Z / 2, Y / 2, X / 2), (0.45 * Z, 0.38 * Y, 0.42 * X), device)
+    vol = torch.where(body, 1000.0 + 50.0 * torch.randn(shape, generator=g).to(device), vol)
+    for _ in range(3):
+        centre = (np.array(shape) * rng.uniform(0.3, 0.7, size=3))
+        radii = np.array(shape) * rng.uniform(0.05, 0.15, size=3)
+        m = _ellipsoid_mask(shape, centre, radii, device)
+        vol = torch.where(m, rng.uniform(1500, 3000) + 80.0 * torch.randn(shape, generator=g).to(device), vol)
+    vol = gaussian_smooth(vol, 1.5)
+    return vol.round().clamp(0, 4095).to(torch.int16)
+
+
+def batch_specs(seed: int = 4, count: int = 64, lo: int = 64, hi: int = 384):
+    """The batched-instances workload: `count` volumes with every side drawn uniformly in
+    [lo, hi], alternating uint8 (N=256) and 12-bit (N=4096), K alternating 16 / 32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        dims = tuple(int(v) for v in rng.integers(lo, hi + 1, size=3))
+        kind = "u8" if i % 2 == 0 else "u16"
+        out.append(dict(dims=dims, kind=kind, N=256 if kind == "u8" else 4096,
+                        K=16 if (i // 2) % 2 == 0 else 32, seed=1000 + i))
+    return out

@@ -1,0 +1,86 @@
+"""Batched update over volumes of uneven size, voxel type, K and N (one launch pair per
+<= 64 items): every item's D' equals the oracle's, and equals dm_update_tf alone on that
+item; batches longer than one launch pair and repeated-context errors are covered."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import tfs as T
+
+pytestmark = pytest.mark.gpu
+
+
+def _engines(specs):
+    import __graft_entry__ as g
+    g.build()
+    from paper_2407_21552_gb300 import DM_U8, DM_U16
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    out = []
+    for sp in specs:
+        vol = synth.volume_of(sp["kind"], sp["dims"], sp["seed"])
+        X, Y, Z = sp["dims"]
+        eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if sp["kind"] == "u8" else DM_U16,
+                                      sp.get("b", 4), 1, sp["K"], sp["N"])
+        eng.build_partitions(vol.cuda())
+        out.append((sp, vol, eng))
+    torch.cuda.synchronize()
+    return out
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _small_specs(count, seed):
+    sp = synth.batch_specs(seed=seed, count=count, lo=9, hi=70)
+    for i, s in enumerate(sp):
+        if i % 5 == 4:
+            s["b"] = 3                 # grids that are not multiples of 16: byte paths
+    return sp
+
+
+def test_batch_matches_oracle_and_single_updates():
+    from paper_2407_21552_gb300 import _abi as A
+    items = _engines(_small_specs(12, 9))
+    tfs, outs = [], []
+    for i, (sp, vol, eng) in enumerate(items):
+        tf = T.tf_edit_sequence(50 + i, sp["N"], 3)[-1]
+        tfs.append(torch.from_numpy(tf).cuda())
+        outs.append(torch.full((eng.G,), 3, dtype=torch.uint8, device="cuda"))
+    A.dm_update_tf_batch([(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr())
+                          for i, (_, _, eng) in enumerate(items)], None, _stream())
+    torch.cuda.synchronize()
+    for i, (sp, vol, eng) in enumerate(items):
+        vnp = synth.as_numpy(vol)
+        _, pdm_o, _, _ = oracle.build_partitions(vnp, sp.get("b", 4), 1, sp["N"], sp["K"])
+        want, _ = oracle.update_tf(pdm_o, tfs[i].cpu().numpy())
+        assert np.array_equal(outs[i].cpu().numpy().reshape(want.shape), want), i
+        single = eng.update_tf(tfs[i])
+        assert torch.equal(single, outs[i]), i
+
+
+@pytest.mark.parametrize("per_sm", [1, 2, 8])
+def test_batch_longer_than_one_launch_and_tuning(per_sm):
+    from paper_2407_21552_gb300 import _abi as A
+    items = _engines(_small_specs(70, 10))          # > DM_BATCH_MAX_ITEMS: split in two
+    tfs = [torch.from_numpy(T.tf_edit_sequence(7 + i, sp["N"], 1)[0]).cuda()
+           for i, (sp, _, _) in enumerate(items)]
+    outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in items]
+    A.dm_update_tf_batch([(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr())
+                          for i, (_, _, eng) in enumerate(items)], per_sm, _stream())
+    for i, (_, _, eng) in enumerate(items):
+        assert torch.equal(eng.update_tf(tfs[i]), outs[i]), i
+
+
+def test_batch_rejects_repeated_context():
+    from paper_2407_21552_gb300 import _abi as A
+    items = _engines(_small_specs(2, 11))
+    eng = items[0][2]
+    tf = torch.from_numpy(T.zero_tf(items[0][0]["N"])).cuda()
+    out = torch.empty(eng.G, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.DmError):
+        A.dm_update_tf_batch([(eng.ctx, tf.data_ptr(), out.data_ptr())] * 2, None, _stream())

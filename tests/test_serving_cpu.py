@@ -1,0 +1,104 @@
+"""Scheduler of the serving loop, on the CPU with a fake executor: HBM-budget admission,
+one edit per session per batch in arrival order, a fixed number of batches in flight,
+latency from arrival to completion, and sessions leaving only when idle."""
+import pytest
+
+from paper_2407_21552_gb300.serving import Scheduler, SessionSpec
+
+
+class FakeExec:
+    def __init__(self):
+        self.t = 0.0
+        self.admitted, self.released, self.launched = [], [], []
+
+    def clock(self):
+        return self.t
+
+    def admit(self, spec):
+        self.admitted.append(spec.sid)
+
+    def release(self, sid):
+        self.released.append(sid)
+
+    def launch(self, slot, reqs):
+        h = {"slot": slot, "reqs": [(r.session, r.tf) for r in reqs], "done": False}
+        self.launched.append(h)
+        return h
+
+    def done(self, h):
+        return h["done"]
+
+
+def test_budget_admission_and_release():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=100, slots=2)
+    assert s.open_session(SessionSpec(0, 60))
+    assert s.open_session(SessionSpec(1, 30))
+    assert not s.open_session(SessionSpec(2, 30))      # would exceed the budget: waits
+    assert not s.open_session(SessionSpec(3, 5))       # queued behind session 2 (FIFO)
+    assert ex.admitted == [0, 1] and s.used == 90
+    s.close_session(0)                                 # frees 60: 2 and 3 are admitted
+    assert ex.admitted == [0, 1, 2, 3] and s.used == 65 and ex.released == [0]
+    with pytest.raises(ValueError):
+        s.open_session(SessionSpec(9, 101))
+    with pytest.raises(KeyError):
+        s.submit(0, "tf")                              # no longer admitted
+
+
+def test_one_edit_per_session_per_batch_in_order_and_slots():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=2)
+    for sid in range(3):
+        s.open_session(SessionSpec(sid, 1))
+    for k in range(3):
+        s.submit(0, f"a{k}")
+    s.submit(1, "b0")
+    s.poll()
+    # the oldest edit of each session; sessions 0 and 1 are then on the device, so the
+    # second slot stays free although session 0 has more edits
+    assert len(ex.launched) == 1
+    assert ex.launched[0]["reqs"] == [(0, "a0"), (1, "b0")]
+    s.submit(2, "c0")
+    s.poll()                                           # session 2 is idle: second slot
+    assert len(ex.launched) == 2 and ex.launched[1]["reqs"] == [(2, "c0")]
+    s.poll()                                           # no free slot, busy sessions
+    assert len(ex.launched) == 2
+    ex.t = 5.0
+    ex.launched[0]["done"] = True
+    s.poll()                                           # retire batch 0: a1 goes next
+    assert len(ex.launched) == 3 and ex.launched[2]["reqs"] == [(0, "a1")]
+    assert sorted(s.stats.latencies) == [5.0, 5.0]
+    ex.t = 7.0
+    while s.has_work():
+        for h in ex.launched:
+            h["done"] = True
+        s.poll()
+    assert len(s.completed) == 5 and not s.has_work()
+    assert [r.tf for r in s.completed if r.session == 0] == ["a0", "a1", "a2"]
+
+
+def test_session_with_edits_in_flight_cannot_close():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=1)
+    s.open_session(SessionSpec(0, 1))
+    s.submit(0, "x")
+    s.poll()
+    with pytest.raises(RuntimeError):
+        s.close_session(0)
+    ex.launched[0]["done"] = True
+    s.poll()
+    s.close_session(0)
+    assert ex.released == [0]
+
+
+def test_max_batch_and_rotation():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=100, slots=1, max_batch=2)
+    for sid in range(3):
+        s.open_session(SessionSpec(sid, 1))
+        s.submit(sid, f"s{sid}")
+    s.poll()
+    assert ex.launched[0]["reqs"] == [(0, "s0"), (1, "s1")]
+    ex.launched[0]["done"] = True
+    s.poll()
+    assert ex.launched[1]["reqs"] == [(2, "s2")]
