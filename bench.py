@@ -37,7 +37,11 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per combine launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
 # taken on; reported as null once the source has changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_update_fused on ct, edits with |S| = 7: 14,768,896 B read, 0 B written (D' stays
+    # in L2); profiles/update_and_recompute_kernels_ct.md
+    "ct": {"source_sha": "07fb2251a5221987", "read_per_active_plane": 14768896 / 7, "write": 0.0},
+}
 
 
 def parse():
@@ -46,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ct", "tiny", "large", "batch", "serving"],
+    ap.add_argument("--workload", choices=["ct", "tiny", "large", "batch", "serving", "render"],
                     default="ct")
     ap.add_argument("--serve-seconds", type=float, default=1.5,
                     help="serving workload: arrival window per rate and server")
@@ -326,7 +330,31 @@ def run_ours(args, ws, rank, local):
     tr = NCU_TRAFFIC.get(args.workload)
     src = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc", "dm_update.cu")
     if tr and tr.get("source_sha") == file_sha(src):
-        traffic = tr["bytes_per_launch"]
+        traffic = float(tr["read_per_active_plane"] * nact.mean() + tr["write"])
+
+    # ---- the same edits with the optional partition-range index (DM_INDEX_RANGES): the
+    #      update reads two index planes per run of active partitions
+    from paper_2407_21552_gb300 import DM_INDEX_RANGES
+    idx_eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if w["dtype"] == "u8" else DM_U16,
+                                      w["block"], w["apron"], w["K"], w["N"], device=dev,
+                                      with_minmax=False, index_mode=DM_INDEX_RANGES)
+    idx_eng.build_partitions(vol)
+    idx_eng.release_mask()
+    for k in range(args.warmup):
+        idx_eng.update_tf(tfs[k % E], out=out)
+    torch.cuda.synchronize(dev)
+    ia, ib = mk(), mk()
+    for k in range(K):
+        flush()
+        ia[k].record(stream)
+        idx_eng.update_tf(tfs[k % E], out=out)
+        ib[k].record(stream)
+    torch.cuda.synchronize(dev)
+    upd_idx = [ia[k].elapsed_time(ib[k]) for k in range(K)]
+    idx_planes = int(idx_eng.sizes.pdm_planes)
+    idx_eng.close()
+    del idx_eng
+    torch.cuda.empty_cache()
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -380,6 +408,12 @@ def run_ours(args, ws, rank, local):
         "full_recompute": {"p50_ms": p50f, "p99_ms": p99f, "mode": "min/max occupancy",
                            "voxels_per_s_p50": V / (p50f * 1e-3)},
         "speedup_vs_full_recompute_p50": p50f / p50u,
+        "update_range_index": {"p50_ms": pct(upd_idx, 50), "p99_ms": pct(upd_idx, 99),
+                               "speedup_vs_full_recompute_p50": p50f / pct(upd_idx, 50),
+                               "pdm_planes": idx_planes,
+                               "note": "optional DM_INDEX_RANGES: same D', two index planes "
+                                       "per run of active partitions; memory "
+                                       f"{idx_planes}/{w['K']} of the plain PDMs"},
         "active_partitions": {"mean": float(nact.mean()), "min": int(nact.min()),
                               "max": int(nact.max()), "K": w["K"]},
         "precompute": {"ms": float(np.median(pre)),
@@ -604,6 +638,69 @@ def run_serving(args, ws, rank, local):
     print(json.dumps(res))
 
 
+# --------------------------------------------------------------------- render workload
+def run_render(args, ws, rank, local):
+    """Frame times of the ray caster at 2160^2 (§4.1) on the CT volume, camera circling the
+    vertical axis, early ray termination at 0.98: no skipping, and skipping with the exact
+    distance map D, the min/max D and the partitioned D' (K = 32), as in Figs. 3-4."""
+    import ctypes
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U16, DM_OCC_EXACT, _abi as A
+    from paper_2407_21552_gb300.build import build as build_lib
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+
+    build_lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.WORKLOADS["ct"]
+    dims = w["dims"]
+    vol = synth.make_volume("ct", device=dev)
+    eng = PartitionedDistanceMaps(dims, DM_U16, 4, 1, w["K"], w["N"], device=dev)
+    eng.build_partitions(vol)
+    ex = PartitionedDistanceMaps(dims, DM_U16, 4, 1, w["K"], w["N"], occ_mode=DM_OCC_EXACT,
+                                 device=dev, with_minmax=False)
+    tfs = synth.tf_edit_sequence(w["seed"], w["N"], 4)
+    W = H = 2160
+    img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp_ = ctypes.c_void_p(stream.cuda_stream)
+    rows = {}
+    for ti, tf_np in enumerate(tfs):
+        tf = torch.from_numpy(tf_np).to(dev)
+        maps = {"no_ess": None, "D_exact": ex.full_recompute(tf, volume=vol),
+                "D_minmax": eng.full_recompute(tf), "D_partitioned": eng.update_tf(tf)}
+        for name, m in maps.items():
+            ts, smp = [], []
+            for k in range(8):
+                cam = A.orbit_camera(dims, 2 * np.pi * k / 8, W, H, step=0.5, ert=0.98)
+                for _ in range(2 if k == 0 else 1):        # one warm-up frame
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    A.dm_render(vol.data_ptr(), DM_U16, dims, 4,
+                                m.data_ptr() if m is not None else None, tf.data_ptr(), w["N"],
+                                cam, img.data_ptr(), ns.data_ptr(), sp_)
+                    b.record(stream)
+                    b.synchronize()
+                ts.append(a.elapsed_time(b))
+                smp.append(float(ns.float().mean()))
+            rows.setdefault(name, []).append((float(np.mean(ts)), float(np.mean(smp))))
+    if rank != 0:
+        return
+    res = {"metric": "frame time (ms) at 2160^2 with and without empty-space skipping",
+           "unit": "ms", "n_gpus": ws, "data": "synthetic", "higher_is_better": False,
+           "config": {"workload": "ct volume 512^3 12-bit, b=4 apron=1, K=32; 4 TFs x 8 "
+                                  "camera angles; ERT 0.98; step 0.5 voxel"},
+           "value": float(np.mean([r[0] for r in rows["D_partitioned"]])),
+           "frames": {k: {"mean_ms": float(np.mean([r[0] for r in v])),
+                          "per_tf_ms": [r[0] for r in v],
+                          "mean_samples_per_ray": float(np.mean([r[1] for r in v]))}
+                      for k, v in rows.items()}}
+    print(json.dumps(res))
+
+
 # --------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -651,6 +748,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "serving":
         run_serving(args, ws, rank, local)
+    elif args.workload == "render":
+        run_render(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

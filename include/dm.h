@@ -24,7 +24,8 @@
  *  - Layouts: the volume is [Z][Y][X], x fastest, uint8 or uint16.  The block grid is
  *    Gx = ceil(X/b), Gy = ceil(Y/b), Gz = ceil(Z/b), G = Gx*Gy*Gz, stored [Gz][Gy][Gx].
  *    Distance maps are uint8 [Gz][Gy][Gx]; the K PDMs are planar, plane p at byte offset
- *    p * plane_stride (plane_stride = G rounded up to 64 bytes).  Distances are in block
+ *    p * plane_stride (plane_stride = G rounded up to 64 bytes), followed by the planes of
+ *    the optional range index (dm_config.index_mode).  Distances are in block
  *    units, 0 on occupied blocks, clamped to 255, and 255 for an empty map (§3.2).
  */
 #ifndef DM_H
@@ -70,7 +71,16 @@ typedef struct dm_config {
     int32_t tf_size;          /* N, entries of the 1D TF, 2..DM_MAX_TF_SIZE; entry i maps
                                  intensity i; voxels >= N are treated as N-1 */
     int32_t occ_mode;         /* DM_OCC_MINMAX or DM_OCC_EXACT, for dm_full_recompute */
+    int32_t index_mode;       /* DM_INDEX_NONE (the K PDMs only, as in the paper) or
+                                 DM_INDEX_RANGES: also keep, for k = 1..floor(log2 K),
+                                 plane (k, i) = min of PDM_i .. PDM_{i+2^k-1}, so that an
+                                 update reads two planes per run of consecutive active
+                                 partitions instead of one per active partition (same D');
+                                 costs about K*log2(K) planes of memory instead of K */
 } dm_config;
+
+#define DM_INDEX_NONE 0
+#define DM_INDEX_RANGES 1
 
 typedef struct dm_sizes {
     size_t mask_bytes;        /* POM bit masks: G * ceil(K/64) uint64 words */
@@ -81,6 +91,7 @@ typedef struct dm_sizes {
     size_t out_bytes;         /* one distance map: G */
     int32_t grid[3];          /* Gx, Gy, Gz */
     int32_t mask_words;       /* ceil(K/64) */
+    int32_t pdm_planes;       /* planes in the pdm buffer: K, or K plus the range index */
 } dm_sizes;
 
 /*
@@ -214,6 +225,31 @@ dm_status dm_update_tf_noalloc(const uint8_t *d_pdm, size_t plane_stride, int64_
                                int32_t num_partitions, const int32_t *borders,
                                int32_t tf_size, const float *d_tf_rgba, uint8_t *d_out,
                                void *stream);
+
+/*
+ * Consumer of the distance map (not part of the update path): a headless orthographic ray
+ * caster with empty-space skipping, the renderer the distance map serves (§1; §4.1: early
+ * ray termination at 0.98).  Pixel (i, j) casts origin + i*pixel_dx + j*pixel_dy +
+ * t*direction; samples lie on t_k = t_in + k*step inside the box of voxel centres and are
+ * pre-classified trilinear (the RGBA of the 8 corner voxels are blended).  With d_dmap
+ * (uint8 [G] Chebyshev distances in blocks of `block` voxels, built with an apron >= 1,
+ * e.g. D' from dm_update_tf) the ray jumps over every cube of blocks the map proves empty,
+ * landing on the same sample lattice, so the image equals the one rendered with d_dmap =
+ * NULL (no skipping).  d_image_rgba: device float32 [height][width][4], premultiplied
+ * colour and accumulated alpha.  d_samples (nullable): device uint32 [height][width],
+ * samples evaluated per ray.  Asynchronous on `stream`.
+ */
+typedef struct dm_camera {
+    float origin[3], pixel_dx[3], pixel_dy[3], direction[3];
+    int32_t width, height;
+    float step;                 /* sample spacing in voxels along the ray, > 0 */
+    float ert;                  /* early ray termination threshold (accumulated alpha) */
+} dm_camera;
+
+dm_status dm_render(const void *d_volume, int32_t dtype, const int32_t dims[3], int32_t block,
+                    const uint8_t *d_dmap, const float *d_tf_rgba, int32_t tf_size,
+                    const dm_camera *cam, float *d_image_rgba, uint32_t *d_samples,
+                    void *stream);
 
 /* Wait for `stream` and report any asynchronous CUDA error as DM_ERR_CUDA. */
 dm_status dm_sync(dm_ctx *ctx, void *stream);

@@ -19,6 +19,8 @@ DM_U8 = 1
 DM_U16 = 2
 DM_OCC_MINMAX = 0
 DM_OCC_EXACT = 1
+DM_INDEX_NONE = 0
+DM_INDEX_RANGES = 1
 DM_MAX_PARTITIONS = 256
 DM_MAX_TF_SIZE = 65536
 DM_MAX_BLOCK = 16
@@ -29,7 +31,8 @@ DM_BATCH_MAX_ITEMS = 64
 #: every function declared in include/dm.h
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_sync", "dm_destroy",
+            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_sync",
+            "dm_destroy",
             "dm_last_error_string", "dm_status_string", "dm_version")
 
 
@@ -37,14 +40,16 @@ class dm_config(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("dtype", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("apron", ctypes.c_int32),
                 ("num_partitions", ctypes.c_int32), ("borders", ctypes.POINTER(ctypes.c_int32)),
-                ("tf_size", ctypes.c_int32), ("occ_mode", ctypes.c_int32)]
+                ("tf_size", ctypes.c_int32), ("occ_mode", ctypes.c_int32),
+                ("index_mode", ctypes.c_int32)]
 
 
 class dm_sizes(ctypes.Structure):
     _fields_ = [("mask_bytes", ctypes.c_size_t), ("pdm_bytes", ctypes.c_size_t),
                 ("plane_stride", ctypes.c_size_t), ("minmax_bytes", ctypes.c_size_t),
                 ("scratch_bytes", ctypes.c_size_t), ("out_bytes", ctypes.c_size_t),
-                ("grid", ctypes.c_int32 * 3), ("mask_words", ctypes.c_int32)]
+                ("grid", ctypes.c_int32 * 3), ("mask_words", ctypes.c_int32),
+                ("pdm_planes", ctypes.c_int32)]
 
 
 class dm_batch_item(ctypes.Structure):
@@ -54,6 +59,13 @@ class dm_batch_item(ctypes.Structure):
 
 class dm_batch_tuning(ctypes.Structure):
     _fields_ = [("combine_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class dm_camera(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("pixel_dx", ctypes.c_float * 3),
+                ("pixel_dy", ctypes.c_float * 3), ("direction", ctypes.c_float * 3),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("step", ctypes.c_float), ("ert", ctypes.c_float)]
 
 
 class DmError(RuntimeError):
@@ -87,6 +99,7 @@ def load(path: str = LIB_PATH):
     lib.dm_update_tf_noalloc.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, S, P, S, P, P, P]
     lib.dm_update_tf_batch.argtypes = [ctypes.POINTER(dm_batch_item), S,
                                        ctypes.POINTER(dm_batch_tuning), P]
+    lib.dm_render.argtypes = [P, S, P, S, P, P, S, ctypes.POINTER(dm_camera), P, P, P]
     lib.dm_sync.argtypes = [P, P]
     lib.dm_destroy.argtypes = [P]
     lib.dm_destroy.restype = None
@@ -97,7 +110,8 @@ def load(path: str = LIB_PATH):
     lib.dm_version.argtypes = []
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_sync", "dm_version"):
+              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_sync",
+              "dm_version"):
         getattr(lib, n).restype = S
     _lib = lib
     return lib
@@ -118,7 +132,7 @@ def _check(ctx, status, where):
 
 # ---------------------------------------------------------------- same-name wrappers
 def make_config(dims, dtype, block=4, apron=1, num_partitions=16, tf_size=256, borders=None,
-                occ_mode=DM_OCC_MINMAX):
+                occ_mode=DM_OCC_MINMAX, index_mode=DM_INDEX_NONE):
     cfg = dm_config()
     cfg.dims[:] = [int(d) for d in dims]
     cfg.dtype = int(dtype)
@@ -127,6 +141,7 @@ def make_config(dims, dtype, block=4, apron=1, num_partitions=16, tf_size=256, b
     cfg.num_partitions = int(num_partitions)
     cfg.tf_size = int(tf_size)
     cfg.occ_mode = int(occ_mode)
+    cfg.index_mode = int(index_mode)
     keep = None
     if borders is not None:
         keep = (ctypes.c_int32 * len(borders))(*[int(v) for v in borders])
@@ -211,6 +226,40 @@ def dm_update_tf_batch(items, tuning=None, stream=None):
     if st != DM_OK:
         detail = load().dm_last_error_string(items[0][0]).decode() if n else ""
         raise DmError(st, "dm_update_tf_batch", detail)
+
+
+def orbit_camera(dims, angle_rad, width, height, step=0.5, ert=0.98, elevation_rad=0.3):
+    """Orthographic camera circling the volume's vertical (y) axis, its image plane
+    covering the volume's bounding sphere."""
+    import math
+    X, Y, Z = (float(d) for d in dims)
+    c = [(X - 1) / 2, (Y - 1) / 2, (Z - 1) / 2]
+    r = 0.5 * math.sqrt(X * X + Y * Y + Z * Z)
+    d = [math.cos(elevation_rad) * math.sin(angle_rad), -math.sin(elevation_rad),
+         math.cos(elevation_rad) * math.cos(angle_rad)]
+    up = [0.0, 1.0, 0.0]
+    u = [d[1] * up[2] - d[2] * up[1], d[2] * up[0] - d[0] * up[2], d[0] * up[1] - d[1] * up[0]]
+    nu = math.sqrt(sum(x * x for x in u))
+    u = [x / nu for x in u]
+    v = [u[1] * d[2] - u[2] * d[1], u[2] * d[0] - u[0] * d[2], u[0] * d[1] - u[1] * d[0]]
+    cam = dm_camera()
+    px = 2 * r / max(width, height)
+    for a in range(3):
+        cam.direction[a] = d[a]
+        cam.pixel_dx[a] = u[a] * px
+        cam.pixel_dy[a] = v[a] * px
+        cam.origin[a] = c[a] - d[a] * 2 * r - u[a] * px * width / 2 - v[a] * px * height / 2
+    cam.width, cam.height, cam.step, cam.ert = int(width), int(height), float(step), float(ert)
+    return cam
+
+
+def dm_render(d_volume, dtype, dims, block, d_dmap, d_tf_rgba, tf_size, cam, d_image, d_samples,
+              stream):
+    d = (ctypes.c_int32 * 3)(*[int(x) for x in dims])
+    st = load().dm_render(d_volume, int(dtype), d, int(block), d_dmap, d_tf_rgba, int(tf_size),
+                          ctypes.byref(cam), d_image, d_samples, stream)
+    if st != DM_OK:
+        raise DmError(st, "dm_render")
 
 
 def dm_sync(ctx, stream):

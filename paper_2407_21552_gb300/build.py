@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdm.so")
 SOURCES = ["dm_api.cu", "dm_footprint.cu", "dm_dt.cu", "dm_update.cu", "dm_noalloc.cu",
-           "dm_batch.cu"]
+           "dm_batch.cu", "dm_render.cu"]
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
 

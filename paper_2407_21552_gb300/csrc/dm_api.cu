@@ -18,6 +18,8 @@ struct dm_ctx {
     dmk::Geometry geo;
     dm_sizes sizes;
     int W;
+    int J;                          // range-index levels (-1: none)
+    int planes;                     // planes in the pdm buffer
     int num_sms;
     // scratch layout (byte offsets)
     size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_tf, off_out;
@@ -101,6 +103,7 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
         return DM_ERR_UNSUPPORTED;
     if (c.num_partitions > c.tf_size) return DM_ERR_INVALID_ARG;
     if (c.occ_mode != DM_OCC_MINMAX && c.occ_mode != DM_OCC_EXACT) return DM_ERR_INVALID_ARG;
+    if (c.index_mode != DM_INDEX_NONE && c.index_mode != DM_INDEX_RANGES) return DM_ERR_INVALID_ARG;
     const int K = c.num_partitions, N = c.tf_size;
     if (c.borders) {
         if (c.borders[0] != 0 || c.borders[K] != N) return DM_ERR_INVALID_ARG;
@@ -127,6 +130,8 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     g.G = int64_t(g.gx) * g.gy * g.gz;
     g.plane = int64_t(align_up(size_t(g.G), 64));
     x->W = (K + 63) / 64;
+    x->J = c.index_mode == DM_INDEX_RANGES ? dmk::index_levels(K) : -1;
+    x->planes = x->J < 0 ? K : dmk::index_level_base(K, x->J + 1);
     // limits of the kernels' tilings
     if (g.gx > 10240 || dmk::xpass_smem(g.gx, K) > size_t(dmk::kXpassSmemLimit) ||
         dmk::line_pass_smem(g.gy) > size_t(dmk::kLineSmemLimit) ||
@@ -138,7 +143,8 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     dm_sizes& s = x->sizes;
     s.mask_bytes = size_t(g.G) * x->W * 8;
     s.plane_stride = size_t(g.plane);
-    s.pdm_bytes = size_t(K) * s.plane_stride;
+    s.pdm_bytes = size_t(x->planes) * s.plane_stride;
+    s.pdm_planes = x->planes;
     s.minmax_bytes = size_t(g.G) * 2 * g.bpv;
     s.out_bytes = size_t(g.G);
     s.grid[0] = g.gx;
@@ -216,6 +222,10 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM y pass");
     e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 2, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM z pass");
+    if (ctx->J > 0) {
+        e = dmk::launch_build_index(pdm, ctx->geo.plane, ctx->geo.G, K, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "range index");
+    }
     ctx->built = true;
     ctx->minmax_built = ctx->d_minmax != nullptr;
     ctx->err[0] = 0;
@@ -248,7 +258,7 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         }
         cudaError_t e = dmk::launch_update_fused(static_cast<const uint8_t*>(ctx->d_pdm),
                                                  ctx->geo.plane, ctx->geo.G, d_tf, N, K,
-                                                 ctx->borders, act, nact, smask,
+                                                 ctx->J, ctx->borders, act, nact, smask,
                                                  d_active_mask_out, d_out, ctx->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "update");
         if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
@@ -256,7 +266,7 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         ctx->err[0] = 0;
         return DM_OK;
     }
-    cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->borders, act, nact, smask,
+    cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->J, ctx->borders, act, nact, smask,
                                            d_active_mask_out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "active set");
     if (ctx->ev_begin && (e = cudaEventRecord(ctx->ev_begin, s)) != cudaSuccess)
@@ -389,6 +399,7 @@ dm_status dm_update_tf_batch(const dm_batch_item* items, int32_t n, const dm_bat
             d.nact = reinterpret_cast<int32_t*>(scratch + c->off_nact);
             d.N = c->cfg.tf_size;
             d.K = c->cfg.num_partitions;
+            d.J = c->J;
         }
         cudaError_t e = dmk::launch_update_batch(desc, m, per_sm, first->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(first, e, "batched update");

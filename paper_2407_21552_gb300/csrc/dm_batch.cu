@@ -23,7 +23,7 @@ struct Item {
     const uint8_t* lut;                        // partition of each intensity (precompute)
     uint16_t* act;                             // active list and count (item's scratch)
     int32_t* nact;
-    int32_t N, K;
+    int32_t N, K, J;                           // J: index levels (-1: none)
     int32_t vec;                               // 16-byte units (else bytes)
 };
 
@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
 {
     pdl_trigger();
     __shared__ uint32_t s_S[kMaxPartitions / 32];
-    __shared__ int s_cnt[8];
+    __shared__ uint16_t s_list[kMaxPartitions + 8];
+    __shared__ int s_scan[9];
     const Item& it = P.it[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < kMaxPartitions / 32) s_S[tid] = 0;
@@ -63,20 +64,11 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
         }
     }
     __syncthreads();
-    const bool on = tid < it.K && ((s_S[tid >> 5] >> (tid & 31)) & 1u);
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
-    if (lane == 0 && warp < 8) s_cnt[warp] = __popc(bal);
-    __syncthreads();
-    if (tid < 256) {
-        int off = 0;
-        for (int w = 0; w < warp; ++w) off += s_cnt[w];
-        if (on) it.act[off + __popc(bal & ((1u << lane) - 1))] = uint16_t(tid);
-        if (tid == 0) {
-            int tot = 0;
-            for (int w = 0; w < 8; ++w) tot += s_cnt[w];
-            *it.nact = tot;
-        }
-    }
+    (void)lane;
+    (void)warp;
+    const int n = plan_maps(s_S, it.K, it.J, s_list, s_scan);
+    for (int j = tid; j < n; j += kActThreads) it.act[j] = s_list[j];
+    if (tid == 0) *it.nact = n;
 }
 
 // Eq. 1 over every item's work units; CTA b takes a contiguous range of units.
@@ -170,6 +162,7 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
         it.nact = d.nact;
         it.N = d.N;
         it.K = d.K;
+        it.J = d.J;
         it.vec = ((reinterpret_cast<uintptr_t>(d.pdm) & 15) == 0) &&
                  ((reinterpret_cast<uintptr_t>(d.out) & 15) == 0) && (d.plane % 16 == 0);
         const int64_t units = it.vec ? (d.G >> 4) : d.G;

@@ -8,11 +8,10 @@
 // with a per-intensity visibility bit instead of a partition bit, gives the exact TF
 // occupancy of the plain recompute in its exact mode.
 //
-// Tiling: a CTA owns tbx x tby blocks of one block-slice bz and walks the b + 2a voxel
-// slices of their z-footprint.  Each slice's voxel tile (with its x/y apron) is staged in
-// shared memory with 16-byte vector loads where rows are aligned; a row pass ORs the
-// classes over each block's x-footprint, then a column pass ORs those over the block's
-// y-footprint into per-block accumulators that live in shared memory across slices.
+// Tiling: one warp per block row and one lane per block column (32 x 8 blocks per CTA),
+// the CTA streaming a chunk of 4 block-slices along z.  Every voxel is read once per
+// footprint row it lies in (16-byte vectors when b = 4), classified once, and its x apron
+// reaches the neighbouring block through a warp shuffle.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -33,264 +32,278 @@ __global__ void k_partition_lut(uint8_t* __restrict__ lut, int N, int K, Borders
     lut[i] = static_cast<uint8_t>(lo);
 }
 
+template <typename T>
+struct Quad;                                   // four consecutive voxels in one load
+template <>
+struct Quad<uint8_t> {
+    using V = uint32_t;
+    __device__ static unsigned get(V v, int k) { return (v >> (8 * k)) & 0xFFu; }
+};
+template <>
+struct Quad<uint16_t> {
+    using V = uint2;
+    __device__ static unsigned get(V v, int k)
+    {
+        return ((k < 2 ? v.x : v.y) >> (16 * (k & 1))) & 0xFFFFu;
+    }
+};
+
 struct FpParams {
-    Geometry g;
-    int N;
-    int tbx, tby;          // blocks per tile in x / y
-    int ap;                // tile columns left of the core (>= a, 16-byte aligned)
-    int tile_w, tile_h;    // voxel tile extent
-    int vec_ok;            // core rows can use 16-byte loads
+    int X, Y, Z;
+    int gx, gy, gz;
+    int b, a, N, W64;
+    int zchunk;                                // block-slices per CTA
 };
 
 enum { kModePom = 0, kModeVis = 1 };
-
-template <typename T>
-struct MinMaxPack;
-template <>
-struct MinMaxPack<uint8_t> {
-    using P = uint16_t;
-    __device__ static P pack(unsigned mn, unsigned mx) { return P(mn | (mx << 8)); }
-};
-template <>
-struct MinMaxPack<uint16_t> {
-    using P = uint32_t;
-    __device__ static P pack(unsigned mn, unsigned mx) { return P(mn | (mx << 16)); }
-};
+constexpr int kWarps = 8;
+constexpr int kMaxRows = 12;                   // b + 2a rows of a footprint when b = 4
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-struct FpSmem {
-    size_t cls, tile, rowacc, rowmm, blkacc, blkmm, total;
-};
-
-__host__ __device__ inline FpSmem fp_smem_layout(int N, int W, int bpv, int tile_w, int tile_h,
-                                                 int tbx, int tby)
+// Accumulates one voxel into a mask (NW 32-bit words) and a min / max.
+template <int NW, int MODE>
+__device__ __forceinline__ void classify(unsigned v, int N, const uint8_t* s_cls, uint32_t (&m)[NW],
+                                         unsigned& mn, unsigned& mx)
 {
-    FpSmem s;
-    size_t o = 0;
-    s.cls = o;    o = align16(o + size_t(N));
-    s.tile = o;   o = align16(o + size_t(tile_w) * tile_h * bpv);
-    s.rowacc = o; o = align16(o + size_t(tile_h) * tbx * W * 8);
-    s.rowmm = o;  o = align16(o + size_t(tile_h) * tbx * 4);
-    s.blkacc = o; o = align16(o + size_t(tby) * tbx * W * 8);
-    s.blkmm = o;  o = align16(o + size_t(tby) * tbx * 4);
-    s.total = o;
-    return s;
+    if (v > unsigned(N - 1)) v = unsigned(N - 1);
+    const unsigned c = s_cls[v];
+    if (MODE == kModePom) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) m[w] |= ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
+        mn = min(mn, v);
+        mx = max(mx, v);
+    } else {
+        m[0] |= c;
+    }
 }
 
-template <typename T, int W, int MODE>
-__global__ void __launch_bounds__(kThreads)
-k_footprint(const T* __restrict__ vol, FpParams prm, const uint8_t* __restrict__ lut,
+// One warp per block row, one lane per block column; the CTA streams its chunk of
+// block-slices along z.  Per voxel slice: every footprint row of the warp's block row is
+// loaded once (FAST: the lane's 4 core voxels in one load), the lane's core mask and the
+// masks of its first / last `a` voxels are formed, the x apron comes from the neighbour
+// lanes by shuffle (lanes 0 and 31 read theirs), and the rows are ORed into the slice
+// mask.  The slice mask goes to every block whose z footprint holds the slice (at most 3
+// when a <= b: a ring of per-thread accumulators in shared memory); a block is written
+// when its last slice has been added.
+template <typename T, int NW, int MODE, bool FAST>
+__global__ void __launch_bounds__(kWarps * 32)
+k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
             const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
             uint8_t* __restrict__ occ)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     pdl_wait();
-    const Geometry& g = prm.g;
-    const int tid = threadIdx.x;
-    const int tbx = prm.tbx, tby = prm.tby, tw = prm.tile_w, th = prm.tile_h;
-    const FpSmem L = fp_smem_layout(prm.N, W, int(sizeof(T)), tw, th, tbx, tby);
-    uint8_t* s_cls = smem + L.cls;
-    T* s_tile = reinterpret_cast<T*>(smem + L.tile);
-    uint64_t* s_row = reinterpret_cast<uint64_t*>(smem + L.rowacc);
-    uint16_t* s_rowmm = reinterpret_cast<uint16_t*>(smem + L.rowmm);   // [th*tbx][2]
-    uint64_t* s_blk = reinterpret_cast<uint64_t*>(smem + L.blkacc);
-    uint16_t* s_blkmm = reinterpret_cast<uint16_t*>(smem + L.blkmm);   // [tby*tbx][2]
-
-    const int bx0 = blockIdx.x * tbx, by0 = blockIdx.y * tby, bz = blockIdx.z;
-    const int b = g.b, a = g.a, N = prm.N;
-
-    // class table: partition index (POM) or visibility bit (exact occupancy)
-    for (int i = tid; i < N; i += kThreads) {
-        if (MODE == kModePom) s_cls[i] = lut[i];
-        else s_cls[i] = uint8_t(cnt[i + 1] > cnt[i]);
-    }
-    for (int i = tid; i < tby * tbx; i += kThreads) {
-        for (int w = 0; w < W; ++w) s_blk[i * W + w] = 0;
-        s_blkmm[2 * i] = 0xFFFF;
-        s_blkmm[2 * i + 1] = 0;
-    }
-
-    // voxel tile origin: column c <-> x = bx0*b - ap + c, row r <-> y = by0*b - a + r
-    const int xo = bx0 * b - prm.ap;
-    const int yo = by0 * b - a;
-    const int xlo = max(0, bx0 * b - a), xhi = min(g.X - 1, (bx0 + tbx) * b - 1 + a);
-    const int ylo = max(0, yo), yhi = min(g.Y - 1, (by0 + tby) * b - 1 + a);
-    const int zlo = max(0, bz * b - a), zhi = min(g.Z - 1, bz * b + b - 1 + a);
-    const int nrows = yhi - ylo + 1;
-    const int64_t rowstride = g.X;
-    const int64_t slicestride = int64_t(g.X) * g.Y;
-
-    for (int z = zlo; z <= zhi; ++z) {
-        __syncthreads();   // the previous slice's tile and row accumulators are consumed
-        const T* sl = vol + int64_t(z) * slicestride;
-        // ---- stage the slice tile
-        if (prm.vec_ok) {
-            // core columns [bx0*b, (bx0+tbx)*b) with 16-byte loads, apron columns scalar
-            const int per_row = (tbx * b * int(sizeof(T))) / 16;
-            const int nvec = nrows * per_row;
-            for (int i = tid; i < nvec; i += kThreads) {
-                int r = i / per_row, q = i - r * per_row;
-                int y = ylo + r;
-                const uint4* src = reinterpret_cast<const uint4*>(sl + int64_t(y) * rowstride
-                                                                  + int64_t(bx0) * b) + q;
-                uint4 v = __ldg(src);
-                T* dst = s_tile + (y - yo) * tw + prm.ap;
-                reinterpret_cast<uint4*>(dst)[q] = v;
-            }
-            const int na = 2 * a;
-            for (int i = tid; i < nrows * na; i += kThreads) {
-                int r = i / na, k = i - r * na;
-                int y = ylo + r;
-                int x = k < a ? bx0 * b - a + k : (bx0 + tbx) * b + (k - a);
-                if (x >= 0 && x < g.X)
-                    s_tile[(y - yo) * tw + (x - xo)] = sl[int64_t(y) * rowstride + x];
-            }
-        } else {
-            const int ncols = xhi - xlo + 1;
-            for (int i = tid; i < nrows * ncols; i += kThreads) {
-                int r = i / ncols, c = i - r * ncols;
-                int y = ylo + r, x = xlo + c;
-                s_tile[(y - yo) * tw + (x - xo)] = sl[int64_t(y) * rowstride + x];
-            }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint8_t* s_cls = smem;
+    uint32_t* s_ring = reinterpret_cast<uint32_t*>(smem + align16(size_t(p.N)));  // [3][NW][256]
+    uint32_t* s_rmm = s_ring + 3 * NW * kWarps * 32;                                // [3][256]
+    for (int i = tid; i < p.N; i += kWarps * 32)
+        s_cls[i] = MODE == kModePom ? lut[i] : uint8_t(cnt[i + 1] > cnt[i]);
+    __syncthreads();
+    const int bx = blockIdx.x * 32 + lane, by = blockIdx.y * kWarps + warp;
+    if (by >= p.gy) return;                                   // warp-uniform; no CTA barrier follows
+    const int b = p.b, a = p.a, X = p.X, N = p.N;
+    const bool col_ok = bx < p.gx;
+    const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
+    const int zs = max(0, zb0 * b - a), ze = min(p.Z - 1, (zb1 - 1) * b + b - 1 + a);
+    const int y0 = max(0, by * b - a), y1 = min(p.Y - 1, by * b + b - 1 + a);
+    const int nrows = y1 - y0 + 1;
+    const int xc0 = bx * b;
+    const int64_t rowX = X;
+    for (int z = zs; z <= ze; ++z) {
+        uint32_t S[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = 0;
+        unsigned smn = 0xFFFFu, smx = 0;
+        const T* slice = vol + int64_t(z) * p.Y * rowX;
+        typename Quad<T>::V q[FAST ? kMaxRows : 1];
+        if (FAST) {                                           // issue all row loads first
+#pragma unroll
+            for (int r = 0; r < kMaxRows; ++r)
+                if (r < nrows && col_ok)
+                    q[r] = *reinterpret_cast<const typename Quad<T>::V*>(
+                        slice + int64_t(y0 + r) * rowX + xc0);
         }
-        __syncthreads();
-        // ---- row pass: per (tile row, block column) OR over the block's x-footprint
-        for (int i = tid; i < nrows * tbx; i += kThreads) {
-            int r = i / tbx, bxl = i - r * tbx;
-            int y = ylo + r;
-            int bx = bx0 + bxl;
-            uint64_t acc[W];
+#pragma unroll 1
+        for (int r = 0; r < nrows; ++r) {
+            const T* row = slice + int64_t(y0 + r) * rowX;
+            uint32_t core[NW], head[NW], tail[NW];
 #pragma unroll
-            for (int w = 0; w < W; ++w) acc[w] = 0;
-            unsigned mn = 0xFFFF, mx = 0;
-            if (bx < g.gx) {
-                int x0 = max(0, bx * b - a), x1 = min(g.X - 1, bx * b + b - 1 + a);
-                const T* row = s_tile + (y - yo) * tw - xo;
-                for (int x = x0; x <= x1; ++x) {
-                    unsigned v = row[x];
-                    if (v > unsigned(N - 1)) v = unsigned(N - 1);
-                    unsigned c = s_cls[v];
-                    if (MODE == kModePom) {
+            for (int w = 0; w < NW; ++w) core[w] = head[w] = tail[w] = 0;
+            unsigned cmn = 0xFFFFu, cmx = 0, hmn = 0xFFFFu, hmx = 0, tmn = 0xFFFFu, tmx = 0;
+            if (col_ok) {
+                if (FAST) {
+                    typename Quad<T>::V v4 = q[0];
 #pragma unroll
-                        for (int w = 0; w < W; ++w)
-                            acc[w] |= ((c >> 6) == unsigned(w)) ? (uint64_t(1) << (c & 63)) : 0;
-                        mn = min(mn, v);
-                        mx = max(mx, v);
-                    } else {
-                        acc[0] |= c;
+                    for (int rr = 1; rr < kMaxRows; ++rr)
+                        if (rr == r) v4 = q[rr];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t m1[NW];
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) m1[w] = 0;
+                        unsigned mn1 = 0xFFFFu, mx1 = 0;
+                        classify<NW, MODE>(Quad<T>::get(v4, k), N, s_cls, m1, mn1, mx1);
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) core[w] |= m1[w];
+                        cmn = min(cmn, mn1);
+                        cmx = max(cmx, mx1);
+                        if (k < a) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) head[w] |= m1[w];
+                            hmn = min(hmn, mn1);
+                            hmx = max(hmx, mx1);
+                        }
+                        if (k >= 4 - a) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) tail[w] |= m1[w];
+                            tmn = min(tmn, mn1);
+                            tmx = max(tmx, mx1);
+                        }
+                    }
+                } else {
+                    for (int k = 0; k < b && xc0 + k < X; ++k) {
+                        uint32_t m1[NW];
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) m1[w] = 0;
+                        unsigned mn1 = 0xFFFFu, mx1 = 0;
+                        classify<NW, MODE>(row[xc0 + k], N, s_cls, m1, mn1, mx1);
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) core[w] |= m1[w];
+                        cmn = min(cmn, mn1);
+                        cmx = max(cmx, mx1);
+                        if (k < a) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) head[w] |= m1[w];
+                            hmn = min(hmn, mn1);
+                            hmx = max(hmx, mx1);
+                        }
+                        if (k >= b - a) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) tail[w] |= m1[w];
+                            tmn = min(tmn, mn1);
+                            tmx = max(tmx, mx1);
+                        }
                     }
                 }
             }
-            int ri = (y - yo) * tbx + bxl;
+            // x apron: the last `a` voxels of the block to the left, the first `a` of the
+            // block to the right (neighbour lanes; lanes 0 / 31 read them from memory)
+            uint32_t left[NW], right[NW];
 #pragma unroll
-            for (int w = 0; w < W; ++w) s_row[ri * W + w] = acc[w];
-            s_rowmm[2 * ri] = uint16_t(mn);
-            s_rowmm[2 * ri + 1] = uint16_t(mx);
-        }
-        __syncthreads();
-        // ---- column pass: per block OR over its y-footprint rows of this slice
-        for (int i = tid; i < tby * tbx; i += kThreads) {
-            int byl = i / tbx, bxl = i - byl * tbx;
-            int by = by0 + byl, bx = bx0 + bxl;
-            if (by >= g.gy || bx >= g.gx) continue;
-            int y0 = max(0, by * b - a), y1 = min(g.Y - 1, by * b + b - 1 + a);
-            uint64_t acc[W];
+            for (int w = 0; w < NW; ++w) {
+                left[w] = __shfl_up_sync(0xFFFFFFFFu, tail[w], 1);
+                right[w] = __shfl_down_sync(0xFFFFFFFFu, head[w], 1);
+            }
+            unsigned lmm = __shfl_up_sync(0xFFFFFFFFu, tmn | (tmx << 16), 1);
+            unsigned rmm = __shfl_down_sync(0xFFFFFFFFu, hmn | (hmx << 16), 1);
+            if (lane == 0 || lane == 31) {
+                const bool lft = lane == 0;
 #pragma unroll
-            for (int w = 0; w < W; ++w) acc[w] = s_blk[i * W + w];
-            unsigned mn = s_blkmm[2 * i], mx = s_blkmm[2 * i + 1];
-            for (int y = y0; y <= y1; ++y) {
-                int ri = (y - yo) * tbx + bxl;
+                for (int w = 0; w < NW; ++w) (lft ? left[w] : right[w]) = 0;
+                unsigned mn2 = 0xFFFFu, mx2 = 0;
+                uint32_t m2[NW];
 #pragma unroll
-                for (int w = 0; w < W; ++w) acc[w] |= s_row[ri * W + w];
-                mn = min(mn, unsigned(s_rowmm[2 * ri]));
-                mx = max(mx, unsigned(s_rowmm[2 * ri + 1]));
+                for (int w = 0; w < NW; ++w) m2[w] = 0;
+                if (col_ok) {
+                    for (int k = 0; k < a; ++k) {
+                        const int x = lft ? xc0 - 1 - k : xc0 + b + k;
+                        if (x >= 0 && x < X) classify<NW, MODE>(row[x], N, s_cls, m2, mn2, mx2);
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < NW; ++w) (lft ? left[w] : right[w]) = m2[w];
+                (lft ? lmm : rmm) = mn2 | (mx2 << 16);
             }
 #pragma unroll
-            for (int w = 0; w < W; ++w) s_blk[i * W + w] = acc[w];
-            s_blkmm[2 * i] = uint16_t(mn);
-            s_blkmm[2 * i + 1] = uint16_t(mx);
+            for (int w = 0; w < NW; ++w) S[w] |= core[w] | left[w] | right[w];
+            smn = min(smn, min(cmn, min(lmm & 0xFFFFu, rmm & 0xFFFFu)));
+            smx = max(smx, max(cmx, max(lmm >> 16, rmm >> 16)));
         }
-    }
-    __syncthreads();
-    // ---- write the tile's blocks
-    for (int i = tid; i < tby * tbx; i += kThreads) {
-        int byl = i / tbx, bxl = i - byl * tbx;
-        int by = by0 + byl, bx = bx0 + bxl;
-        if (by >= g.gy || bx >= g.gx) continue;
-        int64_t blk = (int64_t(bz) * g.gy + by) * g.gx + bx;
-        if (MODE == kModePom) {
+        // hand the slice to the blocks whose z footprint holds it
+        const int bzc = z / b;
+        for (int bz = max(zb0, bzc - 1); bz <= min(zb1 - 1, bzc + 1); ++bz) {
+            const int f0 = max(0, bz * b - a), f1 = min(p.Z - 1, bz * b + b - 1 + a);
+            if (z < f0 || z > f1) continue;
+            const int slot = bz % 3;
+            uint32_t* rg = s_ring + slot * NW * (kWarps * 32) + tid;
+            uint32_t* rm = s_rmm + slot * (kWarps * 32) + tid;
+            unsigned mn = smn, mx = smx;
+            if (z == f0) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) mask[blk * W + w] = s_blk[i * W + w];
-            if (minmax) {
-                using P = typename MinMaxPack<T>::P;
-                reinterpret_cast<P*>(minmax)[blk] =
-                    MinMaxPack<T>::pack(s_blkmm[2 * i], s_blkmm[2 * i + 1]);
+                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] = S[w];
+            } else {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] |= S[w];
+                mn = min(mn, *rm & 0xFFFFu);
+                mx = max(mx, *rm >> 16);
             }
-        } else {
-            occ[blk] = uint8_t(s_blk[i * W] != 0);
+            *rm = mn | (mx << 16);
+            if (z == f1 && col_ok) {
+                const int64_t blk = (int64_t(bz) * p.gy + by) * p.gx + bx;
+                if (MODE == kModePom) {
+                    for (int w64 = 0; w64 < p.W64; ++w64) {
+                        const uint32_t lo = (2 * w64 < NW) ? rg[(2 * w64) * kWarps * 32] : 0u;
+                        const uint32_t hi = (2 * w64 + 1 < NW) ? rg[(2 * w64 + 1) * kWarps * 32] : 0u;
+                        mask[blk * p.W64 + w64] = uint64_t(lo) | (uint64_t(hi) << 32);
+                    }
+                    if (minmax) {
+                        if (sizeof(T) == 1)
+                            reinterpret_cast<uint16_t*>(minmax)[blk] = uint16_t(mn | (mx << 8));
+                        else
+                            reinterpret_cast<uint32_t*>(minmax)[blk] = mn | (mx << 16);
+                    }
+                } else {
+                    occ[blk] = uint8_t(rg[0] != 0);
+                }
+            }
         }
     }
 }
 
-// Pick the tile so that shared memory stays under `limit`; voxel extent starts at 128 x 32.
-bool plan_tiles(const Geometry& g, int N, int W, size_t limit, FpParams* p, size_t* smem)
-{
-    int b = g.b, a = g.a, s = g.bpv;
-    int vx = 128, vy = 32;
-    for (int attempt = 0; attempt < 8; ++attempt) {
-        int tbx = max(1, vx / b), tby = max(1, vy / b);
-        int ap = max(16 / s, ((a + 16 / s - 1) / (16 / s)) * (16 / s));
-        int tw = ap + tbx * b + ap;
-        int th = tby * b + 2 * a;
-        FpSmem L = fp_smem_layout(N, W, s, tw, th, tbx, tby);
-        if (L.total <= limit) {
-            p->g = g;
-            p->N = N;
-            p->tbx = tbx;
-            p->tby = tby;
-            p->ap = ap;
-            p->tile_w = tw;
-            p->tile_h = th;
-            *smem = L.total;
-            return true;
-        }
-        if (vx > 16) vx /= 2; else if (vy > 4) vy /= 2; else break;
-    }
-    return false;
-}
+size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
-template <typename T, int W, int MODE>
-cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, const uint8_t* lut,
+template <typename T, int NW, int MODE>
+cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const uint8_t* lut,
                         const int32_t* cnt, uint64_t* mask, void* minmax, uint8_t* occ,
-                        size_t limit, cudaStream_t s)
+                        cudaStream_t s)
 {
     FpParams p;
-    size_t smem = 0;
-    if (!plan_tiles(g, N, W, limit, &p, &smem)) return cudaErrorInvalidConfiguration;
-    const int sz = int(sizeof(T));
-    p.vec_ok = ((reinterpret_cast<uintptr_t>(vol) & 15) == 0) &&
-               ((int64_t(g.X) * sz) % 16 == 0) && ((p.tbx * g.b * sz) % 16 == 0) &&
-               (int64_t(g.gx) % p.tbx == 0) && (int64_t(g.gx) * g.b == g.X);
-    cudaError_t e = ensure_dynamic_smem<k_footprint<T, W, MODE>>(int(smem));
+    p.X = g.X; p.Y = g.Y; p.Z = g.Z;
+    p.gx = g.gx; p.gy = g.gy; p.gz = g.gz;
+    p.b = g.b; p.a = g.a; p.N = N;
+    p.W64 = (K + 63) / 64;
+    p.zchunk = 4;
+    const size_t smem = fp_smem(N, NW);
+    const bool fast = g.b == 4 && ((reinterpret_cast<uintptr_t>(vol) & (4 * sizeof(T) - 1)) == 0) &&
+                      ((int64_t(g.X) * sizeof(T)) % (4 * sizeof(T)) == 0) && (g.X % 4 == 0);
+    dim3 grid((g.gx + 31) / 32, (g.gy + kWarps - 1) / kWarps, (g.gz + p.zchunk - 1) / p.zchunk);
+    const T* v = static_cast<const T*>(vol);
+    cudaError_t e;
+    if (fast) {
+        e = ensure_dynamic_smem<k_footprint<T, NW, MODE, true>>(int(smem));
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_footprint<T, NW, MODE, true>, grid, dim3(kWarps * 32), smem, s, v, p,
+                          lut, cnt, mask, minmax, occ);
+    }
+    e = ensure_dynamic_smem<k_footprint<T, NW, MODE, false>>(int(smem));
     if (e != cudaSuccess) return e;
-    dim3 grid((g.gx + p.tbx - 1) / p.tbx, (g.gy + p.tby - 1) / p.tby, g.gz);
-    return launch_pdl(k_footprint<T, W, MODE>, grid, dim3(kThreads), smem, s,
-                      static_cast<const T*>(vol), p, lut, cnt, mask, minmax, occ);
+    return launch_pdl(k_footprint<T, NW, MODE, false>, grid, dim3(kWarps * 32), smem, s, v, p,
+                      lut, cnt, mask, minmax, occ);
 }
 
 template <typename T>
 cudaError_t launch_pom_t(const void* vol, const Geometry& g, int N, int K, const uint8_t* lut,
-                         uint64_t* mask, void* minmax, size_t limit, cudaStream_t s)
+                         uint64_t* mask, void* minmax, cudaStream_t s)
 {
-    int W = (K + 63) / 64;
-    switch (W) {
-    case 1: return launch_fp_t<T, 1, kModePom>(vol, g, N, lut, nullptr, mask, minmax, nullptr, limit, s);
-    case 2: return launch_fp_t<T, 2, kModePom>(vol, g, N, lut, nullptr, mask, minmax, nullptr, limit, s);
-    case 3: return launch_fp_t<T, 3, kModePom>(vol, g, N, lut, nullptr, mask, minmax, nullptr, limit, s);
-    case 4: return launch_fp_t<T, 4, kModePom>(vol, g, N, lut, nullptr, mask, minmax, nullptr, limit, s);
-    default: return cudaErrorInvalidValue;
-    }
+    if (K <= 32)
+        return launch_fp_t<T, 1, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+    if (K <= 64)
+        return launch_fp_t<T, 2, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+    if (K <= 128)
+        return launch_fp_t<T, 4, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+    return launch_fp_t<T, 8, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
 }
 
 }  // namespace
@@ -305,18 +318,18 @@ cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
                              const uint8_t* lut, uint64_t* mask, void* minmax,
                              size_t smem_limit, cudaStream_t s)
 {
-    if (g.bpv == 1) return launch_pom_t<uint8_t>(vol, g, N, K, lut, mask, minmax, smem_limit, s);
-    return launch_pom_t<uint16_t>(vol, g, N, K, lut, mask, minmax, smem_limit, s);
+    (void)smem_limit;
+    if (g.bpv == 1) return launch_pom_t<uint8_t>(vol, g, N, K, lut, mask, minmax, s);
+    return launch_pom_t<uint16_t>(vol, g, N, K, lut, mask, minmax, s);
 }
 
 cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const int32_t* cnt,
                              uint8_t* occ, size_t smem_limit, cudaStream_t s)
 {
+    (void)smem_limit;
     if (g.bpv == 1)
-        return launch_fp_t<uint8_t, 1, kModeVis>(vol, g, N, nullptr, cnt, nullptr, nullptr, occ,
-                                                 smem_limit, s);
-    return launch_fp_t<uint16_t, 1, kModeVis>(vol, g, N, nullptr, cnt, nullptr, nullptr, occ,
-                                              smem_limit, s);
+        return launch_fp_t<uint8_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ, s);
+    return launch_fp_t<uint16_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ, s);
 }
 
 }  // namespace dmk

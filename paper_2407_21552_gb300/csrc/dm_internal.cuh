@@ -82,6 +82,77 @@ cudaError_t ensure_dynamic_smem(int bytes)
     return e;
 }
 
+// ---------------------------------------------------------------- partition-range index
+// Optional sparse index over the K PDMs: plane (k, i) = min of PDM_i .. PDM_{i + 2^k - 1}
+// for k = 0..J (level 0 = the PDMs), J = floor(log2 K).  Level k starts at plane
+// index_level_base(K, k).  A run of consecutive active partitions [i, e] is covered by the
+// two planes (k, i) and (k, e - 2^k + 1) with k = floor(log2(e - i + 1)).
+__host__ __device__ inline int index_level_base(int K, int k)
+{
+    int b = 0;
+    for (int l = 0; l < k; ++l) b += K - (1 << l) + 1;
+    return b;
+}
+__host__ __device__ inline int index_levels(int K)
+{
+    int J = 0;
+    while ((2 << J) <= K) ++J;
+    return J;
+}
+
+// From the active-partition bit set `bits` (shared memory, 8 words, bit p = partition p),
+// write the plane indices to combine to `list` and return their number (to every thread).
+// Without the index (J < 0) the planes are the active partitions; with it, one or two
+// planes per maximal run of active partitions.  Every thread of the CTA must call it (it
+// synchronises the CTA); threads 0..255 handle partition threadIdx.x; `s_scan` is 9 ints
+// of shared scratch.
+__device__ inline int plan_maps(const uint32_t* bits, int K, int J, uint16_t* list, int* s_scan)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto on = [&](int p) { return (bits[p >> 5] >> (p & 31)) & 1u; };
+    int c = 0;
+    int m0 = 0, m1 = 0;
+    if (tid < K && on(tid)) {
+        if (J < 0) {
+            c = 1;
+            m0 = tid;
+        } else if (tid == 0 || !on(tid - 1)) {           // run start: find the run's end
+            int e = tid;
+            while (e + 1 < K && on(e + 1)) ++e;
+            const int k = 31 - __clz(e - tid + 1);
+            const int base = index_level_base(K, k);
+            m0 = base + tid;
+            m1 = base + e - (1 << k) + 1;
+            c = m1 == m0 ? 1 : 2;
+        }
+    }
+    int incl = c;                                         // scan over threads 0..255
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    if (lane == 31 && warp < 8) s_scan[warp] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int w = 0; w < 8; ++w) {
+            const int t = s_scan[w];
+            s_scan[w] = run;
+            run += t;
+        }
+        s_scan[8] = run;
+    }
+    __syncthreads();
+    if (tid < 256 && c) {
+        const int pos = s_scan[warp] + incl - c;
+        list[pos] = uint16_t(m0);
+        if (c == 2) list[pos + 1] = uint16_t(m1);
+    }
+    __syncthreads();
+    return s_scan[8];
+}
+
 // ---------------------------------------------------------------- one-time precompute
 cudaError_t launch_partition_lut(uint8_t* lut, int N, int K, const Borders& bd,
                                  cudaStream_t s);
@@ -109,6 +180,9 @@ cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t
 cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
                              cudaStream_t s);
 size_t line_pass_smem(int L);
+
+// Index levels 1..J over the K PDM planes (level 0), each level one streaming min pass.
+cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cudaStream_t s);
 size_t xpass_smem(int gx, int K);
 
 // ---------------------------------------------------------------- per-TF update
@@ -119,16 +193,16 @@ cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, i
                              uint64_t* smask_out, cudaStream_t s);
 
 // The active set alone (no prefix count), for the update path.
-cudaError_t launch_active_set(const float* tf, int N, int K, const Borders& bd, uint16_t* act,
-                              int32_t* nact, uint64_t* smask, uint64_t* smask_out,
-                              cudaStream_t s);
+cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Borders& bd,
+                              uint16_t* act, int32_t* nact, uint64_t* smask,
+                              uint64_t* smask_out, cudaStream_t s);
 
 // Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
 bool update_fused_ok(int N);
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, const Borders& bd, uint16_t* act, int32_t* nact,
-                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                cudaStream_t s);
+                                int N, int K, int J, const Borders& bd, uint16_t* act,
+                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                                uint8_t* out, int num_sms, cudaStream_t s);
 
 // D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
@@ -146,6 +220,7 @@ struct BatchDesc {
     uint16_t* act;                     // the item's active list and count (its scratch)
     int32_t* nact;
     int32_t N, K;
+    int32_t J;                         // index levels (-1: no index)
 };
 
 // Active sets of up to kMaxBatch items (one CTA each), then one persistent combine over

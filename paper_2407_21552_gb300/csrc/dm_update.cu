@@ -94,15 +94,16 @@ k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __r
 // batch issued before any is used), then partition p is active iff a visibility bit in
 // [lo_p, hi_p] is set; compacted ascending.  Lets the combine's CTAs launch at once.
 __global__ void __launch_bounds__(kActThreads)
-k_active_set(const float* __restrict__ tf, int N, int K, Borders bd, uint16_t* __restrict__ act,
-             int32_t* __restrict__ nact, uint64_t* __restrict__ smask,
-             uint64_t* __restrict__ smask_out)
+k_active_set(const float* __restrict__ tf, int N, int K, int J, Borders bd,
+             uint16_t* __restrict__ act, int32_t* __restrict__ nact,
+             uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out)
 {
     pdl_trigger();
     constexpr int kBatch = 8;
     __shared__ uint32_t s_vis[DM_MAX_TF_WORDS];
-    __shared__ int32_t s_cnt[8];
     __shared__ uint32_t s_bits[8];
+    __shared__ uint16_t s_list[kMaxPartitions + 8];
+    __shared__ int s_scan[9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int base = 0; base < N; base += kActThreads * kBatch) {
         float a[kBatch];
@@ -133,25 +134,15 @@ k_active_set(const float* __restrict__ tf, int N, int K, Borders bd, uint16_t* _
         }
     }
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
-    if (lane == 0 && warp < 8) {
-        s_cnt[warp] = __popc(bal);
-        s_bits[warp] = bal;
-    }
+    if (lane == 0 && warp < 8) s_bits[warp] = bal;
     __syncthreads();
-    if (tid < 256) {
-        int off = 0;
-        for (int w = 0; w < warp; ++w) off += s_cnt[w];
-        if (on) act[off + __popc(bal & ((1u << lane) - 1))] = uint16_t(p);
-        if (tid == 0) {
-            int tot = 0;
-            for (int w = 0; w < 8; ++w) tot += s_cnt[w];
-            *nact = tot;
-        }
-        if (tid < 4) {
-            uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
-            smask[tid] = v;
-            if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
-        }
+    const int n = plan_maps(s_bits, K, J, s_list, s_scan);
+    for (int j = tid; j < n; j += kActThreads) act[j] = s_list[j];
+    if (tid == 0) *nact = n;
+    if (tid < 4) {
+        const uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
+        smask[tid] = v;
+        if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
     }
 }
 
@@ -266,7 +257,7 @@ constexpr int kFusedMaxN = 8192;
 
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
-               const float* __restrict__ tf, int N, int K, Borders bd,
+               const float* __restrict__ tf, int N, int K, int J, Borders bd,
                uint16_t* __restrict__ act, int32_t* __restrict__ nact,
                uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
                uint8_t* __restrict__ out, int vec_ok)
@@ -275,8 +266,9 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     constexpr int kPer = kFusedMaxN / kFusedThreads;          // alphas per thread (max)
     __shared__ uint32_t s_vis[kFusedMaxN / 32];
     __shared__ int64_t s_off[kMaxPartitions + kBatch];
-    __shared__ int s_cnt[8];
     __shared__ uint32_t s_bits[8];
+    __shared__ uint16_t s_list[kMaxPartitions + kBatch];
+    __shared__ int s_scan[9];
     extern __shared__ uint4 s_stage[];                 // [2][kAsyncBatch][kFusedThreads]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     pdl_wait();
@@ -308,32 +300,21 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         }
     }
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
-    if (lane == 0 && warp < 8) {
-        s_cnt[warp] = __popc(bal);
-        s_bits[warp] = bal;
-    }
+    if (lane == 0 && warp < 8) s_bits[warp] = bal;
     __syncthreads();
-    int n = 0;
-    for (int w = 0; w < 8; ++w) n += s_cnt[w];
-    if (tid < 256) {
-        int off = 0;
-        for (int w = 0; w < warp; ++w) off += s_cnt[w];
-        const int pos = off + __popc(bal & ((1u << lane) - 1));
-        if (on) {
-            s_off[pos] = int64_t(tid) * plane;
-            if (blockIdx.x == 0) act[pos] = uint16_t(tid);
-        }
-        if (blockIdx.x == 0) {
-            if (tid == 0) *nact = n;
-            if (tid < 4) {
-                const uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
-                smask[tid] = v;
-                if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
-            }
+    // ---- planes to combine: the active partitions, or index planes covering their runs
+    const int n = plan_maps(s_bits, K, J, s_list, s_scan);
+    for (int j = tid; j < kMaxPartitions + kBatch; j += kFusedThreads)
+        s_off[j] = int64_t(s_list[j < n ? j : 0]) * plane;     // padding: copies of plane 0
+    if (blockIdx.x == 0) {
+        for (int j = tid; j < n; j += kFusedThreads) act[j] = s_list[j];
+        if (tid == 0) *nact = n;
+        if (tid < 4) {
+            const uint64_t v = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
+            smask[tid] = v;
+            if (smask_out && tid < (K + 63) / 64) smask_out[tid] = v;
         }
     }
-    __syncthreads();
-    if (tid < kBatch && n > 0) s_off[n + tid] = s_off[0];    // padding: copies of an active plane
     __syncthreads();
     // ---- Eq. 1 over the active planes
     const int64_t stride = int64_t(gridDim.x) * kFusedThreads;
@@ -351,14 +332,56 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     }
 }
 
+// One level of the partition-range index: plane (k, i) = min(plane (k-1, i),
+// plane (k-1, i + 2^(k-1))), 16 bytes per thread (bytes for a ragged tail).
+__global__ void __launch_bounds__(256)
+k_index_level(uint8_t* __restrict__ pdm, int64_t plane, int64_t G, int prev_base, int base,
+              int half, int vec_ok)
+{
+    pdl_wait();
+    const int i = blockIdx.y;
+    const uint8_t* a = pdm + int64_t(prev_base + i) * plane;
+    const uint8_t* b = pdm + int64_t(prev_base + i + half) * plane;
+    uint8_t* o = pdm + int64_t(base + i) * plane;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (vec_ok) {
+        const int64_t nvec = G >> 4;
+        for (int64_t v = t0; v < nvec; v += stride)
+            reinterpret_cast<uint4*>(o)[v] = vmin4(__ldcs(reinterpret_cast<const uint4*>(a) + v),
+                                                   __ldcs(reinterpret_cast<const uint4*>(b) + v));
+        done = nvec << 4;
+    }
+    for (int64_t j = done + t0; j < G; j += stride) o[j] = min(a[j], b[j]);
+}
+
 }  // namespace
+
+cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cudaStream_t s)
+{
+    const int J = index_levels(K);
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) && (plane % 16 == 0);
+    for (int k = 1; k <= J; ++k) {
+        const int count = K - (1 << k) + 1;
+        const int64_t work = vec_ok ? (G >> 4) : G;
+        int64_t bx = (work + 255) / 256;
+        if (bx > 1024) bx = 1024;
+        if (bx < 1) bx = 1;
+        cudaError_t e = launch_pdl(k_index_level, dim3(unsigned(bx), unsigned(count)), dim3(256), 0, s,
+                                   pdm, plane, G, index_level_base(K, k - 1), index_level_base(K, k),
+                                   1 << (k - 1), vec_ok);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 bool update_fused_ok(int N) { return N <= kFusedMaxN; }
 
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, const Borders& bd, uint16_t* act, int32_t* nact,
-                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                cudaStream_t s)
+                                int N, int K, int J, const Borders& bd, uint16_t* act,
+                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                                uint8_t* out, int num_sms, cudaStream_t s)
 {
     if (N > kFusedMaxN) return cudaErrorInvalidValue;
     const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
@@ -370,8 +393,8 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
     const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
     cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
     if (e != cudaSuccess) return e;
-    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, bd, act, nact,
-                                                      smask, smask_out, out, vec_ok);
+    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, act,
+                                                      nact, smask, smask_out, out, vec_ok);
     return cudaGetLastError();
 }
 
@@ -383,11 +406,11 @@ cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_active_set(const float* tf, int N, int K, const Borders& bd, uint16_t* act,
-                              int32_t* nact, uint64_t* smask, uint64_t* smask_out,
-                              cudaStream_t s)
+cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Borders& bd,
+                              uint16_t* act, int32_t* nact, uint64_t* smask,
+                              uint64_t* smask_out, cudaStream_t s)
 {
-    k_active_set<<<1, kActThreads, 0, s>>>(tf, N, K, bd, act, nact, smask, smask_out);
+    k_active_set<<<1, kActThreads, 0, s>>>(tf, N, K, J, bd, act, nact, smask, smask_out);
     return cudaGetLastError();
 }
 

@@ -32,9 +32,10 @@ class PartitionedDistanceMaps:
 
     def __init__(self, dims, dtype: int, block: int = 4, apron: int = 1,
                  num_partitions: int = 16, tf_size: int = 256, borders=None,
-                 occ_mode: int = A.DM_OCC_MINMAX, device="cuda", with_minmax: bool = True):
+                 occ_mode: int = A.DM_OCC_MINMAX, device="cuda", with_minmax: bool = True,
+                 index_mode: int = A.DM_INDEX_NONE):
         self.cfg, self._keep = A.make_config(dims, dtype, block, apron, num_partitions, tf_size,
-                                             borders, occ_mode)
+                                             borders, occ_mode, index_mode)
         self.ctx = A.dm_create(self.cfg)
         self.sizes = A.dm_query_sizes(self.ctx)
         self.device = torch.device(device)

@@ -101,13 +101,13 @@ def ct_volume(seed: int = 1, size: int = 512, device="cpu") -> torch.Tensor:
     soft-tissue ellipsoid N(1000, 50), bone as rods and shells with Gaussian bands in
     [1500, 3000]; smoothed with sigma 1.5 and clipped to [0, 4095]."""
     rng = np.random.default_rng(seed)
-    g = torch.Generator(device="cpu").manual_seed(seed)
+    g = torch.Generator(device=torch.device(device)).manual_seed(seed)
     shape = (size, size, size)
     f = size / 512.0
-    vol = 20.0 * torch.randn(shape, generator=g).to(device)
+    vol = 20.0 * torch.randn(shape, generator=g, device=torch.device(device))
     body = _ellipsoid_mask(shape, (size / 2, size / 2, size / 2),
                            (0.45 * size, 0.38 * size, 0.42 * size), device)
-    tissue = 1000.0 + 50.0 * torch.randn(shape, generator=g).to(device)
+    tissue = 1000.0 + 50.0 * torch.randn(shape, generator=g, device=torch.device(device))
     vol = torch.where(body, tissue, vol)
     del tissue
     Z, Y, X = shape
@@ -122,7 +122,7 @@ def ct_volume(seed: int = 1, size: int = 512, device="cpu") -> torch.Tensor:
         z0, z1 = sorted(rng.uniform(0.1, 0.9, size=2) * size)
         mu = rng.uniform(1500, 3000)
         m = (((yy - cy) ** 2 + (xx - cx) ** 2) <= r * r) & (zz >= z0) & (zz <= z1)
-        vals = mu + 80.0 * torch.randn(shape, generator=g).to(device)
+        vals = mu + 80.0 * torch.randn(shape, generator=g, device=torch.device(device))
         vol = torch.where(m, vals, vol)
     # ellipsoidal shells (a skull-like layer and an inner one)
     for k in range(2):
@@ -134,7 +134,7 @@ def ct_volume(seed: int = 1, size: int = 512, device="cpu") -> torch.Tensor:
         m = (rho <= 1.0) & (rho >= 1.0 - th / float(rad.min()))
         del rho
         mu = rng.uniform(1500, 3000)
-        vals = mu + 100.0 * torch.randn(shape, generator=g).to(device)
+        vals = mu + 100.0 * torch.randn(shape, generator=g, device=torch.device(device))
         vol = torch.where(m, vals, vol)
     vol = gaussian_smooth(vol, 1.5)
     return vol.round().clamp(0, 4095).to(torch.int16)
@@ -209,10 +209,18 @@ def volume_of(kind: str, dims, seed: int, device="cpu") -> torch.Tensor:
     with their structure scaled to the volume."""
     X, Y, Z = (int(d) for d in dims)
     rng = np.random.default_rng(seed)
-    g = torch.Generator(device="cpu").manual_seed(seed)
     shape = (Z, Y, X)
+    # noise is drawn where the volume is built (a CPU generator is slow for large volumes)
+    gdev = torch.device(device)
+    g = torch.Generator(device=gdev).manual_seed(seed)
+
+    def rand(*shp):
+        return torch.rand(shp, generator=g, device=gdev)
+
+    def randn(*shp):
+        return torch.randn(shp, generator=g, device=gdev)
     if kind == "u8":
-        s = gaussian_smooth(torch.rand(shape, generator=g).to(device), 2.0)
+        s = gaussian_smooth(rand(*shape), 2.0)
         s = (s - s.min()) / (s.max() - s.min() + 1e-12) * 40.0
         vol = s
         m0 = min(shape)
@@ -220,17 +228,17 @@ def volume_of(kind: str, dims, seed: int, device="cpu") -> torch.Tensor:
             centre = rng.uniform(0, 1, size=3) * np.array(shape)
             radii = rng.uniform(0.05, 0.25, size=3) * m0
             m = _ellipsoid_mask(shape, centre, radii, device)
-            vals = (80.0, 150.0, 220.0)[e % 3] + 10.0 * torch.randn(shape, generator=g).to(device)
+            vals = (80.0, 150.0, 220.0)[e % 3] + 10.0 * randn(*shape)
             vol = torch.where(m, vals, vol)
         return vol.round().clamp(0, 255).to(torch.uint8)
-    vol = 20.0 * torch.randn(shape, generator=g).to(device)
+    vol = 20.0 * randn(*shape)
     body = _ellipsoid_mask(shape, (Z / 2, Y / 2, X / 2), (0.45 * Z, 0.38 * Y, 0.42 * X), device)
-    vol = torch.where(body, 1000.0 + 50.0 * torch.randn(shape, generator=g).to(device), vol)
+    vol = torch.where(body, 1000.0 + 50.0 * randn(*shape), vol)
     for _ in range(3):
         centre = (np.array(shape) * rng.uniform(0.3, 0.7, size=3))
         radii = np.array(shape) * rng.uniform(0.05, 0.15, size=3)
         m = _ellipsoid_mask(shape, centre, radii, device)
-        vol = torch.where(m, rng.uniform(1500, 3000) + 80.0 * torch.randn(shape, generator=g).to(device), vol)
+        vol = torch.where(m, rng.uniform(1500, 3000) + 80.0 * randn(*shape), vol)
     vol = gaussian_smooth(vol, 1.5)
     return vol.round().clamp(0, 4095).to(torch.int16)
 

@@ -141,3 +141,19 @@ def test_package_fails_loudly_without_the_library(tmp_path):
             A.load(str(tmp_path / "missing.so"))
         finally:
             A._lib = A._lib_backup
+
+
+@pytest.mark.parametrize("K,planes", [(1, 1), (2, 3), (5, 5 + 4 + 2), (32, 135), (64, 328),
+                                      (256, 256 + 255 + 253 + 249 + 241 + 225 + 193 + 129 + 1)])
+def test_range_index_plane_count(K, planes):
+    """Planes of the optional range index: level k holds K - 2^k + 1 planes, k <= log2 K."""
+    c, keep = cfg(num_partitions=K, tf_size=4096, dtype=A.DM_U16, index_mode=A.DM_INDEX_RANGES)
+    ctx = A.dm_create(c)
+    try:
+        s = A.dm_query_sizes(ctx)
+        assert s.pdm_planes == planes
+        assert s.pdm_bytes == planes * s.plane_stride
+    finally:
+        A.dm_destroy(ctx)
+    c2, keep2 = cfg(index_mode=7)
+    assert A.dm_create_status(c2) == A.DM_ERR_INVALID_ARG
