@@ -155,6 +155,20 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
                             uint8_t *d_out, void *stream);
 
 /*
+ * Checkpoint / resume of a session without recomputing the maps.  dm_config_hash() gives
+ * a 64-bit FNV-1a hash of everything that determines the maps' bytes (dims, voxel type,
+ * block, apron, K, borders, N, index mode) and of the library's layout version.  A caller
+ * that saved the PDM planes (pdm_bytes) and, if used, the min/max (minmax_bytes) of a built
+ * context, and later copies them back into the bound buffers of a context with the same
+ * hash, declares them built with dm_mark_built(ctx, hash); the call fails with
+ * DM_ERR_INVALID_ARG when the hash differs, and with DM_ERR_NOT_BOUND when pdm / scratch
+ * are not bound.  The partition table in scratch is rebuilt on `stream`.  The paper
+ * recomputes the maps at every load (§3.1, one-time initialisation).
+ */
+dm_status dm_config_hash(const dm_ctx *ctx, uint64_t *out);
+dm_status dm_mark_built(dm_ctx *ctx, uint64_t hash, int32_t with_minmax, void *stream);
+
+/*
  * Batched per-TF update over several volumes (§3.1 steps 1 and 2 for each item).  Item i
  * updates context items[i].ctx with its device TF (float32 [N_i][4]) into its device
  * output (uint8 [G_i]); results are those of dm_update_tf on each item alone.  Contexts may

@@ -31,8 +31,8 @@ DM_BATCH_MAX_ITEMS = 64
 #: every function declared in include/dm.h
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_sync",
-            "dm_destroy",
+            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_config_hash",
+            "dm_mark_built", "dm_sync", "dm_destroy",
             "dm_last_error_string", "dm_status_string", "dm_version")
 
 
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
     lib.dm_update_tf_batch.argtypes = [ctypes.POINTER(dm_batch_item), S,
                                        ctypes.POINTER(dm_batch_tuning), P]
     lib.dm_render.argtypes = [P, S, P, S, P, P, S, ctypes.POINTER(dm_camera), P, P, P]
+    lib.dm_config_hash.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.dm_mark_built.argtypes = [P, ctypes.c_uint64, S, P]
     lib.dm_sync.argtypes = [P, P]
     lib.dm_destroy.argtypes = [P]
     lib.dm_destroy.restype = None
@@ -110,8 +112,8 @@ def load(path: str = LIB_PATH):
     lib.dm_version.argtypes = []
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_sync",
-              "dm_version"):
+              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_config_hash",
+              "dm_mark_built", "dm_sync", "dm_version"):
         getattr(lib, n).restype = S
     _lib = lib
     return lib
@@ -260,6 +262,17 @@ def dm_render(d_volume, dtype, dims, block, d_dmap, d_tf_rgba, tf_size, cam, d_i
                           ctypes.byref(cam), d_image, d_samples, stream)
     if st != DM_OK:
         raise DmError(st, "dm_render")
+
+
+def dm_config_hash(ctx) -> int:
+    h = ctypes.c_uint64()
+    _check(ctx, load().dm_config_hash(ctx, ctypes.byref(h)), "dm_config_hash")
+    return int(h.value)
+
+
+def dm_mark_built(ctx, hash_, with_minmax, stream):
+    _check(ctx, load().dm_mark_built(ctx, ctypes.c_uint64(hash_), int(bool(with_minmax)), stream),
+           "dm_mark_built")
 
 
 def dm_sync(ctx, stream):

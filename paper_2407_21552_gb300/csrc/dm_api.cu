@@ -359,6 +359,55 @@ dm_status dm_full_recompute(dm_ctx* ctx, const void* d_volume, const float* d_tf
     return DM_OK;
 }
 
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n)
+{
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static uint64_t ctx_hash(const dm_ctx* c)
+{
+    uint64_t h = 1469598103934665603ull;
+    const int32_t layout_version = 1;
+    h = fnv1a(h, &layout_version, sizeof(layout_version));
+    const int32_t f[] = {c->cfg.dims[0], c->cfg.dims[1], c->cfg.dims[2], c->cfg.dtype,
+                         c->cfg.block, c->cfg.apron, c->cfg.num_partitions, c->cfg.tf_size,
+                         c->cfg.index_mode};
+    h = fnv1a(h, f, sizeof(f));
+    h = fnv1a(h, c->borders.v, sizeof(int32_t) * size_t(c->cfg.num_partitions + 1));
+    return h;
+}
+
+dm_status dm_config_hash(const dm_ctx* ctx, uint64_t* out)
+{
+    if (!ctx || !out) return DM_ERR_INVALID_ARG;
+    *out = ctx_hash(ctx);
+    return DM_OK;
+}
+
+dm_status dm_mark_built(dm_ctx* ctx, uint64_t hash, int32_t with_minmax, void* stream)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (hash != ctx_hash(ctx))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_mark_built: maps were built for another configuration");
+    if (!ctx->d_pdm || !ctx->d_scratch || (with_minmax && !ctx->d_minmax))
+        return fail(ctx, DM_ERR_NOT_BOUND, "dm_mark_built: pdm, scratch (and min/max) must be bound");
+    dm_status st = check_sticky(ctx, "dm_mark_built (earlier work)");
+    if (st != DM_OK) return st;
+    uint8_t* lut = static_cast<uint8_t*>(ctx->d_scratch) + ctx->off_lut;
+    cudaError_t e = dmk::launch_partition_lut(lut, ctx->cfg.tf_size, ctx->cfg.num_partitions,
+                                              ctx->borders, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "partition table");
+    ctx->built = true;
+    ctx->minmax_built = with_minmax != 0;
+    ctx->err[0] = 0;
+    return DM_OK;
+}
+
 dm_status dm_update_tf_batch(const dm_batch_item* items, int32_t n, const dm_batch_tuning* tuning,
                              void* stream)
 {

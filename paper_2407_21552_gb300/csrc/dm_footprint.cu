@@ -17,8 +17,6 @@
 namespace dmk {
 namespace {
 
-constexpr int kThreads = 256;
-
 __global__ void k_partition_lut(uint8_t* __restrict__ lut, int N, int K, Borders bd)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,6 +260,173 @@ k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ l
     }
 }
 
+// Onehot partition / visibility bit of one (already clamped) intensity.
+template <int NW, int MODE>
+__device__ __forceinline__ void onehot(unsigned c, uint32_t (&m)[NW])
+{
+    if (MODE == kModePom) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) m[w] = ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
+    } else {
+        m[0] = c;
+    }
+}
+
+// The footprint kernel for b = 4 and apron 1, with X % 4 == 0 and an aligned volume: a
+// lane's block covers 4 voxels of a row (one vector load), its x footprint adds the last
+// voxel of the left block and the first of the right one (neighbour lanes by shuffle;
+// lanes 0 / 31 load theirs with a predicated load), and the 6 footprint rows of a block
+// row are unrolled.  Min / max are taken on raw intensities and clamped once (clamping is
+// monotone).  Same outputs as k_footprint.
+template <typename T, int NW, int MODE>
+__global__ void __launch_bounds__(kWarps * 32)
+k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
+              const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+              uint8_t* __restrict__ occ)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    pdl_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint8_t* s_cls = smem;
+    uint32_t* s_ring = reinterpret_cast<uint32_t*>(smem + align16(size_t(p.N)));
+    uint32_t* s_rmm = s_ring + 3 * NW * kWarps * 32;
+    for (int i = tid; i < p.N; i += kWarps * 32)
+        s_cls[i] = MODE == kModePom ? lut[i] : uint8_t(cnt[i + 1] > cnt[i]);
+    __syncthreads();
+    const int bx = blockIdx.x * 32 + lane, by = blockIdx.y * kWarps + warp;
+    if (by >= p.gy) return;                                   // warp-uniform; no CTA barrier follows
+    const int X = p.X, Y = p.Y;
+    const unsigned nmax = unsigned(p.N - 1);
+    const bool col_ok = bx < p.gx;
+    const int xc0 = bx * 4;
+    // edge voxel of this lane: left neighbour's last voxel (lane 0), right's first (lane 31)
+    const int xe = lane == 0 ? xc0 - 1 : xc0 + 4;
+    const bool edge_ok = col_ok && (lane == 0 || lane == 31) && xe >= 0 && xe < X;
+    const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
+    const int zs = max(0, zb0 * 4 - 1), ze = min(p.Z - 1, (zb1 - 1) * 4 + 4);
+    const int yb = by * 4 - 1;                                // first footprint row
+    const int64_t rowX = X;
+    for (int z = zs; z <= ze; ++z) {
+        const T* slice = vol + int64_t(z) * Y * rowX;
+        typename Quad<T>::V q[6];
+        unsigned e[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {                         // issue every load first
+            const int y = yb + r;
+            const bool ok = y >= 0 && y < Y;
+            if (ok && col_ok)
+                q[r] = *reinterpret_cast<const typename Quad<T>::V*>(slice + int64_t(y) * rowX + xc0);
+            e[r] = (ok && edge_ok) ? unsigned(slice[int64_t(y) * rowX + xe]) : 0xFFFFFFFFu;
+        }
+        uint32_t S[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S[w] = 0;
+        unsigned smn = 0xFFFFu, smx = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const int y = yb + r;
+            const bool ok = y >= 0 && y < Y;                  // warp-uniform
+            if (!ok) continue;
+            uint32_t core[NW], head[NW], tail[NW], edge[NW];
+            unsigned cmn = 0xFFFFu, cmx = 0, hv = 0, tv = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) core[w] = head[w] = tail[w] = edge[w] = 0;
+            if (col_ok) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned raw = Quad<T>::get(q[r], k);
+                    const unsigned v = min(raw, nmax);
+                    uint32_t m1[NW];
+                    onehot<NW, MODE>(s_cls[v], m1);
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) core[w] |= m1[w];
+                    if (k == 0) {
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) head[w] = m1[w];
+                        hv = v;
+                    }
+                    if (k == 3) {
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) tail[w] = m1[w];
+                        tv = v;
+                    }
+                    cmn = min(cmn, v);
+                    cmx = max(cmx, v);
+                }
+            }
+            unsigned ev = e[r];
+            const bool has_e = ev != 0xFFFFFFFFu;
+            if (has_e) {
+                ev = min(ev, nmax);
+                onehot<NW, MODE>(s_cls[ev], edge);
+            }
+            uint32_t left[NW], right[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                left[w] = __shfl_up_sync(0xFFFFFFFFu, tail[w], 1);
+                right[w] = __shfl_down_sync(0xFFFFFFFFu, head[w], 1);
+            }
+            // neighbours' edge values as (min, max); an absent neighbour is (FFFF, 0)
+            const unsigned tpack = col_ok ? (tv | (tv << 16)) : 0xFFFFu;
+            const unsigned hpack = col_ok ? (hv | (hv << 16)) : 0xFFFFu;
+            unsigned lmm = __shfl_up_sync(0xFFFFFFFFu, tpack, 1);
+            unsigned rmm = __shfl_down_sync(0xFFFFFFFFu, hpack, 1);
+            if (lane == 0) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) left[w] = edge[w];
+                lmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
+            }
+            if (lane == 31) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) right[w] = edge[w];
+                rmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
+            }
+#pragma unroll
+            for (int w = 0; w < NW; ++w) S[w] |= core[w] | left[w] | right[w];
+            smn = min(smn, min(cmn, min(lmm & 0xFFFFu, rmm & 0xFFFFu)));
+            smx = max(smx, max(cmx, max(lmm >> 16, rmm >> 16)));
+        }
+        // hand the slice to the blocks whose z footprint holds it
+        const int bzc = z >> 2;
+        for (int bz = max(zb0, bzc - 1); bz <= min(zb1 - 1, bzc + 1); ++bz) {
+            const int f0 = max(0, bz * 4 - 1), f1 = min(p.Z - 1, bz * 4 + 4);
+            if (z < f0 || z > f1) continue;
+            const int slot = bz % 3;
+            uint32_t* rg = s_ring + slot * NW * (kWarps * 32) + tid;
+            uint32_t* rm = s_rmm + slot * (kWarps * 32) + tid;
+            unsigned mn = smn, mx = smx;
+            if (z == f0) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] = S[w];
+            } else {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] |= S[w];
+                mn = min(mn, *rm & 0xFFFFu);
+                mx = max(mx, *rm >> 16);
+            }
+            *rm = mn | (mx << 16);
+            if (z == f1 && col_ok) {
+                const int64_t blk = (int64_t(bz) * p.gy + by) * p.gx + bx;
+                if (MODE == kModePom) {
+                    for (int w64 = 0; w64 < p.W64; ++w64) {
+                        const uint32_t lo = (2 * w64 < NW) ? rg[(2 * w64) * kWarps * 32] : 0u;
+                        const uint32_t hi = (2 * w64 + 1 < NW) ? rg[(2 * w64 + 1) * kWarps * 32] : 0u;
+                        mask[blk * p.W64 + w64] = uint64_t(lo) | (uint64_t(hi) << 32);
+                    }
+                    if (minmax) {
+                        if (sizeof(T) == 1)
+                            reinterpret_cast<uint16_t*>(minmax)[blk] = uint16_t(mn | (mx << 8));
+                        else
+                            reinterpret_cast<uint32_t*>(minmax)[blk] = mn | (mx << 16);
+                    }
+                } else {
+                    occ[blk] = uint8_t(rg[0] != 0);
+                }
+            }
+        }
+    }
+}
+
 size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
 template <typename T, int NW, int MODE>
@@ -281,6 +446,12 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     dim3 grid((g.gx + 31) / 32, (g.gy + kWarps - 1) / kWarps, (g.gz + p.zchunk - 1) / p.zchunk);
     const T* v = static_cast<const T*>(vol);
     cudaError_t e;
+    if (fast && g.a == 1) {
+        e = ensure_dynamic_smem<k_footprint41<T, NW, MODE>>(int(smem));
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_footprint41<T, NW, MODE>, grid, dim3(kWarps * 32), smem, s, v, p, lut,
+                          cnt, mask, minmax, occ);
+    }
     if (fast) {
         e = ensure_dynamic_smem<k_footprint<T, NW, MODE, true>>(int(smem));
         if (e != cudaSuccess) return e;

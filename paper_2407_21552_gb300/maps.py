@@ -115,6 +115,32 @@ class PartitionedDistanceMaps:
             return self._minmax[: 2 * self.G].view(gz, gy, gx, 2)
         return self._minmax[: 4 * self.G].view(torch.int16).view(gz, gy, gx, 2)
 
+    # ------------------------------------------------------------------ checkpoint / resume
+    def save(self, path: str):
+        """Write the built maps (and min/max) with the configuration hash to `path`."""
+        import numpy as np
+        self.sync()
+        h = A.dm_config_hash(self.ctx)
+        arrays = {"hash": np.array([h], dtype=np.uint64),
+                  "pdm": self._pdm[: self.sizes.pdm_bytes].cpu().numpy()}
+        if self._minmax is not None:
+            arrays["minmax"] = self._minmax[: self.sizes.minmax_bytes].cpu().numpy()
+        np.savez(path, **arrays)
+
+    def load(self, path: str, stream=None):
+        """Restore maps saved by save() from a context with the same configuration."""
+        import numpy as np
+        z = np.load(path)
+        h = int(z["hash"][0])
+        if h != A.dm_config_hash(self.ctx):
+            raise A.DmError(A.DM_ERR_INVALID_ARG, "load", "maps of another configuration")
+        self._pdm[: self.sizes.pdm_bytes].copy_(torch.from_numpy(z["pdm"]))
+        mm = "minmax" in z.files and self._minmax is not None
+        if mm:
+            self._minmax[: self.sizes.minmax_bytes].copy_(torch.from_numpy(z["minmax"]))
+        torch.cuda.current_stream().synchronize()
+        A.dm_mark_built(self.ctx, h, mm, _stream_handle(stream))
+
     def release_mask(self):
         """The POMs are an intermediate (§5): drop their buffer after the precompute."""
         self._mask = None

@@ -157,3 +157,31 @@ def test_range_index_plane_count(K, planes):
         A.dm_destroy(ctx)
     c2, keep2 = cfg(index_mode=7)
     assert A.dm_create_status(c2) == A.DM_ERR_INVALID_ARG
+
+
+def test_config_hash_tracks_everything_that_shapes_the_maps():
+    base = dict()
+    variants = [dict(dims=(128, 128, 127)), dict(block=2), dict(apron=0), dict(num_partitions=8),
+                dict(tf_size=512), dict(num_partitions=4, borders=[0, 1, 5, 200, 256]),
+                dict(index_mode=A.DM_INDEX_RANGES), dict(dtype=A.DM_U16)]
+    hashes = []
+    for kw in [base] + variants:
+        c, keep = cfg(**kw)
+        ctx = A.dm_create(c)
+        hashes.append(A.dm_config_hash(ctx))
+        A.dm_destroy(ctx)
+    assert len(set(hashes)) == len(hashes)
+    c, keep = cfg()
+    ctx = A.dm_create(c)
+    try:
+        assert A.dm_config_hash(ctx) == hashes[0]            # stable
+        # occ_mode does not change the maps: same hash
+        c2, keep2 = cfg(occ_mode=A.DM_OCC_EXACT)
+        ctx2 = A.dm_create(c2)
+        assert A.dm_config_hash(ctx2) == hashes[0]
+        A.dm_destroy(ctx2)
+        lib = A.load()
+        assert lib.dm_mark_built(ctx, hashes[0] ^ 1, 0, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_mark_built(ctx, hashes[0], 0, None) == A.DM_ERR_NOT_BOUND
+    finally:
+        A.dm_destroy(ctx)

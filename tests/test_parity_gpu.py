@@ -168,6 +168,10 @@ CASES = [
     ((16, 64, 256), 4, 1, 256, 4, np.uint8, [0, 1, 86, 171, 256]),  # rho_min partition
     ((20, 36, 128), 4, 1, 256, 16, np.uint8, None),          # aligned rows, 16-byte paths
     ((20, 36, 128), 4, 1, 4096, 32, np.uint16, None),
+    ((12, 20, 264), 4, 1, 256, 16, np.uint8, None),          # 3 x tiles of 32 blocks, ragged
+    ((9, 14, 392), 4, 1, 4096, 64, np.uint16, None),         # two 32-bit mask words per lane
+    ((7, 9, 200), 4, 1, 4096, 200, np.uint16, None),         # eight 32-bit mask words
+    ((13, 11, 132), 4, 1, 300, 33, np.uint16, None),         # K just above one word
 ]
 
 
@@ -247,3 +251,25 @@ def test_ct_all_edits_combine(ct):
         eng.update_tf(torch.from_numpy(tf).cuda(), out=out)
         want, _ = oracle.update_tf(pdm_o, tf)
         assert np.array_equal(out.cpu().numpy().reshape(want.shape), want), k
+
+
+def test_checkpoint_resume_without_recompute(tiny, tmp_path):
+    """Maps saved from a built context and loaded into a fresh one serve the same updates
+    and full recomputes; maps of another configuration are refused."""
+    from paper_2407_21552_gb300 import DM_U8, DmError
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    w = tiny["w"]
+    path = str(tmp_path / "maps.npz")
+    tiny["eng"].save(path)
+    X, Y, Z = w["dims"]
+    fresh = PartitionedDistanceMaps((X, Y, Z), DM_U8, w["block"], w["apron"], w["K"], w["N"])
+    fresh.load(path)
+    for tf in T.tf_edit_sequence(41, w["N"], 3):
+        tfd = torch.from_numpy(tf).cuda()
+        assert torch.equal(fresh.update_tf(tfd), tiny["eng"].update_tf(tfd))
+        assert torch.equal(fresh.full_recompute(tfd), tiny["eng"].full_recompute(tfd))
+    other = PartitionedDistanceMaps((X, Y, Z), DM_U8, w["block"], 0, w["K"], w["N"])
+    with pytest.raises(DmError):
+        other.load(path)
+    fresh.close()
+    other.close()
