@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 NCU_TRAFFIC = {
     # k_update_fused on ct, edits with |S| = 7: 14,768,896 B read, 0 B written (D' stays
     # in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "07fb2251a5221987", "read_per_active_plane": 14768896 / 7, "write": 0.0},
+    "ct": {"source_sha": "2fb83d45b154b107", "read_per_active_plane": 14768896 / 7, "write": 0.0},
 }
 
 

@@ -136,8 +136,9 @@ dm_status dm_update_tf(dm_ctx *ctx, const float *d_tf_rgba, uint8_t *d_out,
 
 /*
  * The same update with HOST buffers: copies h_tf_rgba (float32 [N][4]) to the device,
- * runs dm_update_tf into the context's scratch, copies D' back into h_out (uint8 [G]) and
- * waits for `stream`.  Pinned host memory gives asynchronous copies; pageable works.
+ * runs dm_update_tf and waits for `stream`.  When h_out (uint8 [G]) is pinned host memory
+ * the GPU can address, the update writes D' into it directly; otherwise it writes into the
+ * context's scratch and D' is copied back.  Pageable buffers work too (slower copies).
  */
 dm_status dm_update_tf_host(dm_ctx *ctx, const float *h_tf_rgba, uint8_t *h_out,
                             void *stream);

@@ -308,10 +308,23 @@ dm_status dm_update_tf_host(dm_ctx* ctx, const float* h_tf_rgba, uint8_t* h_out,
     const size_t tf_bytes = size_t(ctx->cfg.tf_size) * 16;
     cudaError_t e = cudaMemcpyAsync(d_tf, h_tf_rgba, tf_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: TF upload");
-    st = update_into(ctx, d_tf, d_out, nullptr, s);
+    // Pinned (page-locked, mapped) host output: the update writes D' into it directly
+    // (over the CPU-GPU link, overlapped with its reads); otherwise through scratch and a
+    // device-to-host copy.
+    cudaPointerAttributes pa;
+    uint8_t* mapped = nullptr;
+    if (cudaPointerGetAttributes(&pa, h_out) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            mapped = static_cast<uint8_t*>(pa.devicePointer);
+    } else {
+        cudaGetLastError();
+    }
+    st = update_into(ctx, d_tf, mapped ? mapped : d_out, nullptr, s);
     if (st != DM_OK) return st;
-    e = cudaMemcpyAsync(h_out, d_out, size_t(ctx->geo.G), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: D' download");
+    if (!mapped) {
+        e = cudaMemcpyAsync(h_out, d_out, size_t(ctx->geo.G), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: D' download");
+    }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "dm_update_tf_host: sync");
     return DM_OK;
