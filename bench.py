@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ct", "tiny", "large", "batch", "serving", "render"],
+    ap.add_argument("--workload",
+                    choices=["ct", "tiny", "large", "mid", "batch", "serving", "render"],
                     default="ct")
     ap.add_argument("--serve-seconds", type=float, default=1.5,
                     help="serving workload: arrival window per rate and server")
@@ -207,12 +208,31 @@ def oracle_sample(vol_np, w, edits, n_edits, n_full=3):
         t0 = time.perf_counter()
         oracle.update_tf(pdm, tf)
         upd.append((time.perf_counter() - t0) * 1e3 * scale)
+    threads = os.cpu_count() or 1
+    tput = oracle_throughput(pdm, edits[:max(1, n_edits)], scale, threads) if n_edits else None
     full = []
     for tf in edits[:n_full]:
         t0 = time.perf_counter()
         oracle.full_recompute_minmax(vmin, vmax, tf)
         full.append((time.perf_counter() - t0) * 1e3 * scale)
-    return dict(pdm=pdm, scale=scale, slab=(X, Y, zs), pre_s=pre_s, upd=upd, full=full)
+    return dict(pdm=pdm, scale=scale, slab=(X, Y, zs), pre_s=pre_s, upd=upd, full=full,
+                tput=tput, threads=threads)
+
+
+def oracle_throughput(pdm, edits, scale, threads):
+    """Whole-volume edits per second of the oracle's update with one edit per host thread
+    at a time (the C call releases the GIL): 2 x `threads` edits over the same slab, each
+    slab edit counted as 1/scale of a whole-volume edit."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    n = 2 * threads
+    batch = [edits[i % len(edits)] for i in range(n)]
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda tf: oracle.update_tf(pdm, tf), batch[:threads]))      # warm-up
+        t0 = time.perf_counter()
+        list(ex.map(lambda tf: oracle.update_tf(pdm, tf), batch))
+        dt = time.perf_counter() - t0
+    return n / (dt * scale)
 
 
 def cpu_baseline_block(s, n_edits):
@@ -223,7 +243,10 @@ def cpu_baseline_block(s, n_edits):
                        f"Eq. 1, single-threaded C; per-edit times scaled by G/G_slab = "
                        f"{s['scale']:.3f}"),
             "full_recompute_p50_ms": pct(s["full"], 50),
-            "nproc": os.cpu_count()}
+            "nproc": os.cpu_count(),
+            "throughput_all_cores": {"edits_per_s": s["tput"], "threads": s["threads"],
+                                     "sample": "one whole-volume-equivalent edit per thread "
+                                               "at a time, same slab and scale"}}
 
 
 # --------------------------------------------------------------------------- our arm

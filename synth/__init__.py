@@ -21,6 +21,9 @@ WORKLOADS = {
                edits=1000, seed=1),
     "large": dict(dims=(1024, 1024, 1795), dtype="u16", block=4, apron=1, K=64, N=4096,
                   edits=1000, seed=2),
+    # the large recipe cut to 448 slices: a profiling size (about 1.5 GB on the device)
+    "mid": dict(dims=(1024, 1024, 448), dtype="u16", block=4, apron=1, K=64, N=4096,
+                edits=1000, seed=2),
 }
 
 
@@ -30,6 +33,6 @@ def make_volume(name: str, device="cpu"):
         return tiny_volume(w["seed"], device=device)
     if name == "ct":
         return ct_volume(w["seed"], device=device)
-    if name == "large":
+    if name in ("large", "mid"):
         return large_volume(w["seed"], dims=w["dims"], device=device)
     raise KeyError(name)

@@ -172,6 +172,7 @@ CASES = [
     ((9, 14, 392), 4, 1, 4096, 64, np.uint16, None),         # two 32-bit mask words per lane
     ((7, 9, 200), 4, 1, 4096, 200, np.uint16, None),         # eight 32-bit mask words
     ((13, 11, 132), 4, 1, 300, 33, np.uint16, None),         # K just above one word
+    ((40, 33, 50), 16, 5, 256, 16, np.uint8, None),          # the largest block size
 ]
 
 
