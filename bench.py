@@ -38,10 +38,26 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
 # taken on; reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # k_update_fused on ct, edits with |S| = 7: 14,768,896 B read, 0 B written (D' stays
-    # in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "2fb83d45b154b107", "read_per_active_plane": 14768896 / 7, "write": 0.0},
+    # k_update_fused on ct (G = 2,097,152), edits with |S| = 7: 14,768,896 B read, 0 B
+    # written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
+    "ct": {"source_sha": "2fb83d45b154b107", "G": 2097152,
+           "read_per_active_plane": 14768896 / 7, "write": 0.0},
+    # k_update_fused on the 1024x1024x448 cut of the large recipe (G = 7,340,032), an edit
+    # with |S| = 31: 227,641,344 B read, 7,651,584 B written; scaled to the large grid by
+    # G (the traffic is |S| * G + G + a fixed 0.1 MB); profiles/update_kernel_mid.md
+    "large": {"source_sha": "2fb83d45b154b107", "G": 7340032,
+              "read_per_active_plane": 227641344 / 31, "write": 7651584.0},
 }
+
+
+def ncu_traffic(workload, G, mean_active):
+    """DRAM bytes per update launch from the committed ncu capture, scaled to this grid and
+    to the mean number of active planes; None once the kernel source has changed."""
+    tr = NCU_TRAFFIC.get(workload)
+    src = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc", "dm_update.cu")
+    if not tr or tr.get("source_sha") != file_sha(src):
+        return None
+    return float((tr["read_per_active_plane"] * mean_active + tr["write"]) * G / tr["G"])
 
 
 def parse():
@@ -60,6 +76,9 @@ def parse():
     ap.add_argument("--cpu-edits", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large-leg", action="store_true",
+                    help="skip the large-workload roofline leg of the default ct run")
+    ap.add_argument("--large-steps", type=int, default=40)
     return ap.parse_args()
 
 
@@ -349,11 +368,7 @@ def run_ours(args, ws, rank, local):
     bytes_comb = (nact + 1) * G                                   # per launch, algorithmic
     achieved = float(bytes_comb.sum() / (np.sum(comb) * 1e-3)) / 1e9   # GB/s
     peak, peak_src = measured_peak()
-    traffic = None
-    tr = NCU_TRAFFIC.get(args.workload)
-    src = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc", "dm_update.cu")
-    if tr and tr.get("source_sha") == file_sha(src):
-        traffic = float(tr["read_per_active_plane"] * nact.mean() + tr["write"])
+    traffic = ncu_traffic(args.workload, G, float(nact.mean()))
 
     # ---- the same edits with the optional partition-range index (DM_INDEX_RANGES): the
     #      update reads two index planes per run of active partitions
@@ -409,15 +424,26 @@ def run_ours(args, ws, rank, local):
         s = oracle_sample(synth.as_numpy(vol), w, edits, args.cpu_edits)
         cpu = cpu_baseline_block(s, args.cpu_edits)
 
+    large = None
+    grid_xyz = list(eng.grid)
+    if ws == 1 and args.workload == "ct" and not args.no_large_leg:
+        eng.close()
+        del eng, vol, tfs, out, out_full
+        torch.cuda.empty_cache()
+        large = large_leg(dev, flush, args.large_steps, args.warmup, peak)
+
     if rank != 0:
         return
-    launches_per_step = 2 + 4 + 2
+    # our kernels per step: the update (1, or 2 when N > 8192), the full recompute (4) and
+    # the profiled update
+    upd_launches = 1 if w["N"] <= 8192 else 2
+    launches_per_step = upd_launches + 4 + upd_launches
     res = {
         "metric": METRIC, "value": p50u, "unit": "ms", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": region_max / K, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": workload_name(args.workload, w), "volume_xyz": [X, Y, Z],
-                   "grid_xyz": list(eng.grid), "G": G, "edits": E,
+                   "grid_xyz": grid_xyz, "G": G, "edits": E,
                    "l2": "flushed before every timed call (256 MiB device write, then a "
                          "256 MiB read)",
                    "volume_sha256": vol_sha, "parallelism": f"replicas x{ws}"},
@@ -442,19 +468,102 @@ def run_ours(args, ws, rank, local):
         "precompute": {"ms": float(np.median(pre)),
                        "algorithmic_gb": (s_bytes * V + w["K"] * G) / 1e9,
                        "gbs": (s_bytes * V + w["K"] * G) / (np.median(pre) * 1e-3) / 1e9},
-        "roofline": {"kernel": "k_combine (Eq. 1)", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)" if upd_launches == 1
+                     else "k_combine (Eq. 1)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": float(bytes_comb.mean()),
                      "mean_launch_us": float(np.mean(comb) * 1e3)},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "large_workload": large,
         "gpu_launches": K * launches_per_step,
         "clocks": clk,
         "paper_context": "paper: up to 30x faster DM update (RTX 4090, OpenGL/GLSL, Table 1); "
                          "not re-run here (no graphics stack)",
     }
     print(json.dumps(res))
+
+
+def large_leg(dev, flush, steps, warmup, peak):
+    """The 1024x1024x1795 workload (K = 64, 449 block slices) inside the default run, after
+    the ct engine is freed: here the maps stream from HBM (about 1.3 GB per edit), so the
+    update kernel's roofline fraction is a bandwidth figure rather than a launch-latency
+    one.  Same protocol as the ct leg: L2 flushed before every timed call; the update, the
+    min/max full recompute, and the update again with events around its kernel."""
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U16, dm_set_profile_events
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    w = synth.WORKLOADS["large"]
+    X, Y, Z = w["dims"]
+    stream = torch.cuda.current_stream(dev)
+    vol = synth.make_volume("large", device=dev)
+    eng = PartitionedDistanceMaps((X, Y, Z), DM_U16, w["block"], w["apron"], w["K"], w["N"],
+                                  device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    flush()
+    p0, p1 = ev(), ev()
+    p0.record(stream)
+    eng.build_partitions(vol)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    pre_ms = p0.elapsed_time(p1)
+    del vol
+    torch.cuda.empty_cache()
+    G = eng.G
+    edits = synth.tf_edit_sequence(w["seed"], w["N"], steps + warmup)
+    tfs = torch.from_numpy(np.stack(edits)).to(dev)
+    out = torch.empty(G, dtype=torch.uint8, device=dev)
+    out_full = torch.empty(G, dtype=torch.uint8, device=dev)
+    am = torch.zeros((steps, (w["K"] + 63) // 64), dtype=torch.int64, device=dev)
+    for k in range(warmup):
+        eng.update_tf(tfs[steps + k], out=out)
+        eng.full_recompute(tfs[steps + k], out=out_full)
+    torch.cuda.synchronize(dev)
+    ua, ub, fa, fb, ca, cb = ([ev() for _ in range(steps)] for _ in range(6))
+    for e in ca + cb:
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    for k in range(steps):
+        flush()
+        ua[k].record(stream)
+        eng.update_tf(tfs[k], out=out, active_mask=am[k])
+        ub[k].record(stream)
+        flush()
+        fa[k].record(stream)
+        eng.full_recompute(tfs[k], out=out_full)
+        fb[k].record(stream)
+        flush()
+        dm_set_profile_events(eng.ctx, ca[k].cuda_event, cb[k].cuda_event)
+        eng.update_tf(tfs[k], out=out)
+        dm_set_profile_events(eng.ctx, None, None)
+    torch.cuda.synchronize(dev)
+    upd = [ua[k].elapsed_time(ub[k]) for k in range(steps)]
+    full = [fa[k].elapsed_time(fb[k]) for k in range(steps)]
+    comb = [ca[k].elapsed_time(cb[k]) for k in range(steps)]
+    masks = am.cpu().numpy().view(np.uint64)
+    nact = np.array([sum(bin(int(x)).count("1") for x in row) for row in masks])
+    bytes_comb = (nact + 1) * G
+    achieved = float(bytes_comb.sum() / (np.sum(comb) * 1e-3)) / 1e9
+    eng.close()
+    del eng, tfs, out, out_full
+    torch.cuda.empty_cache()
+    return {"workload": workload_name("large", w), "G": G, "edits_timed": steps,
+            "update": {"p50_ms": pct(upd, 50), "p99_ms": pct(upd, 99)},
+            "full_recompute": {"p50_ms": pct(full, 50), "p99_ms": pct(full, 99),
+                               "mode": "min/max occupancy"},
+            "speedup_vs_full_recompute_p50": pct(full, 50) / pct(upd, 50),
+            "active_partitions": {"mean": float(nact.mean()), "min": int(nact.min()),
+                                  "max": int(nact.max()), "K": w["K"]},
+            "precompute_ms": pre_ms,
+            "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak,
+                         "traffic": ncu_traffic("large", G, float(nact.mean())),
+                         "algorithmic_bytes_per_launch": float(bytes_comb.mean()),
+                         "mean_launch_us": float(np.mean(comb) * 1e3)},
+            "gpu_launches": steps * 6}
 
 
 # ------------------------------------------------------------ batched instances workload
