@@ -173,6 +173,9 @@ CASES = [
     ((7, 9, 200), 4, 1, 4096, 200, np.uint16, None),         # eight 32-bit mask words
     ((13, 11, 132), 4, 1, 300, 33, np.uint16, None),         # K just above one word
     ((40, 33, 50), 16, 5, 256, 16, np.uint8, None),          # the largest block size
+    ((10, 12, 40), 4, 1, 8192, 64, np.uint16, None),         # largest TF of the one-launch update
+    ((10, 12, 40), 4, 1, 8193, 64, np.uint16, None),         # N > 8192: active set + combine
+    ((11, 9, 36), 2, 1, 65536, 256, np.uint16, None),        # the largest TF and K
 ]
 
 
@@ -180,7 +183,7 @@ CASES = [
 def test_ragged_configs(shape, b, a, N, K, dt, borders):
     rng = np.random.default_rng(sum(shape) * 7 + b * 3 + K)
     vol = rand_volume(rng, shape, N, dt)
-    if dt == np.uint16 and vol.size > 2:
+    if dt == np.uint16 and vol.size > 2 and N + 5 <= 0xFFFF:
         vol.reshape(-1)[::97] = N + 5        # above the TF domain: treated as N - 1
     eng, vd, ref = check_build(vol, b, a, N, K, borders)
     bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
