@@ -13,13 +13,15 @@
 // output is one masked clz/ffs on its own word plus those two lookups.  Four consecutive
 // outputs per thread are stored as one 32-bit word.
 //
-// y / z passes: a CTA stages a tile of 16 neighbouring lines (full line length) in shared
-// memory and builds a doubling table of window minima (level j holds the min over 2^j
-// rows, 4 lines per 32-bit word with __vminu4).  h(i) <= t holds exactly when the window
+// y / z passes: a CTA stages a tile of 16 or 32 neighbouring lines (full line length) in
+// shared memory and builds a doubling table of window minima (level j holds the min over
+// 2^j rows, 16 lines per vector with __vminu4).  h(i) <= t holds exactly when the window
 // of radius t around i holds a value <= t (monotone in t).  A thread walks a segment of
 // one line: a binary search over t gives h at the segment start; after that h changes by
-// at most 1 per step (h is 1-Lipschitz along the line), so each further output takes at
-// most two window queries.  Results overwrite level 0 and the tile is stored in place.
+// at most 1 per step (h is 1-Lipschitz along the line), so each further output takes one
+// window query (radius h - 1) and, when h does not drop, the two rows at distance h read
+// from level 0, which stays the input.  Outputs go straight to global memory in place
+// (the tile was staged before any store).
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -228,21 +230,30 @@ struct LineGeom {
 };
 
 // min of g over rows [r - t, r + t] clipped to the line, from the doubling table
+template <int TC>
 __device__ __forceinline__ int window_min(const uint8_t* __restrict__ lvl, int L, int r, int t,
                                           int c)
 {
-    constexpr int TC = kLineTile;
     const int wl = max(0, r - t), wh = min(L - 1, r + t);
     const int j = 31 - __clz(wh - wl + 1);
     const uint8_t* Lj = lvl + j * L * TC;
     return min(int(Lj[wl * TC + c]), int(Lj[(wh - (1 << j) + 1) * TC + c]));
 }
 
+__device__ __forceinline__ uint4 vmin16(uint4 a, uint4 b)
+{
+    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
+                      __vminu4(a.w, b.w));
+}
+
+// One tile = TC adjacent columns x one whole line.  Level 0 of the table keeps g; every
+// output goes straight to global memory (in place: the tile was staged before any store).
+template <int TC>
 __global__ void __launch_bounds__(kThreads)
 k_line_pass(uint8_t* buf, LineGeom lg)
 {
-    extern __shared__ __align__(16) uint8_t s_lvl[];        // [J+1][L][16]
-    constexpr int TC = kLineTile;
+    extern __shared__ __align__(16) uint8_t s_lvl[];        // [J+1][L][TC]
+    constexpr int V = TC / 16;                               // 16-byte vectors per row
     pdl_wait();
     const int tid = threadIdx.x;
     const int L = lg.L;
@@ -254,9 +265,10 @@ k_line_pass(uint8_t* buf, LineGeom lg)
     //      not everything 255)
     int any_big = 0, any_not255 = 0;
     if (lg.vec_ok) {
-        for (int r = tid; r < L; r += kThreads) {
-            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(r) * lg.s);
-            reinterpret_cast<uint4*>(s_lvl)[r] = v;
+        for (int i = tid; i < L * V; i += kThreads) {
+            const int r = i / V, q = i - r * V;
+            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(r) * lg.s + 16 * q);
+            reinterpret_cast<uint4*>(s_lvl)[i] = v;
             const unsigned w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -278,29 +290,31 @@ k_line_pass(uint8_t* buf, LineGeom lg)
     any_not255 = __syncthreads_or(any_not255);
     if (!any_big || !any_not255) return;   // all values <= 1, or all 255: h == g
 
-    // ---- doubling table of window minima, 4 columns per word
-    uint32_t* lv = reinterpret_cast<uint32_t*>(s_lvl);
-    constexpr int wpr = TC / 4;                               // words per row
+    // ---- doubling table of window minima, 16 columns per vector
+    uint4* lv = reinterpret_cast<uint4*>(s_lvl);
     for (int j = 1; j <= lg.J; ++j) {
-        const uint32_t* prevl = lv + (j - 1) * L * wpr;
-        uint32_t* cur = lv + j * L * wpr;
+        const uint4* prevl = lv + (j - 1) * L * V;
+        uint4* cur = lv + j * L * V;
         const int half = 1 << (j - 1);
-        for (int i = tid; i < L * wpr; i += kThreads) {
-            const int r = i / wpr, q = i - r * wpr;
+        for (int i = tid; i < L * V; i += kThreads) {
+            const int r = i / V, q = i - r * V;
             const int r2 = min(r + half, L - 1);
-            cur[i] = __vminu4(prevl[i], prevl[r2 * wpr + q]);
+            cur[i] = vmin16(prevl[i], prevl[r2 * V + q]);
         }
         __syncthreads();
     }
 
-    // ---- outputs: one thread per (segment, column); results overwrite level 0 (each
-    //      thread reads level 0 only at its own rows; windows of radius >= 1 use j >= 1)
+    // ---- outputs: one thread per (segment, column), rows in order.  At a segment start h
+    //      comes from a binary search; after that h moves by at most 1 per row (the
+    //      transform is 1-Lipschitz), and the window of radius h is the window of radius
+    //      h - 1 plus the two rows at distance h, read from level 0.
     const int seg = lg.seg;
     const int nseg = (L + seg - 1) / seg;
     for (int item = tid; item < nseg * TC; item += kThreads) {
         const int c = item % TC, sg = item / TC;
         if (c >= ncols) continue;
         const int r0 = sg * seg, r1 = min(L, r0 + seg);
+        uint8_t* col = base + c;
         int h = 0;
         for (int r = r0; r < r1; ++r) {
             const int gv = s_lvl[r * TC + c];
@@ -310,37 +324,39 @@ k_line_pass(uint8_t* buf, LineGeom lg)
                 int lo = 1, hi = gv;                         // least t with window min <= t
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (window_min(s_lvl, L, r, mid, c) <= mid) hi = mid; else lo = mid + 1;
+                    if (window_min<TC>(s_lvl, L, r, mid, c) <= mid) hi = mid; else lo = mid + 1;
                 }
                 h = lo;
             } else {                                         // h(r) in {h-1, h, h+1}
-                if (h - 1 >= 1 && window_min(s_lvl, L, r, h - 1, c) <= h - 1) h = h - 1;
-                else if (window_min(s_lvl, L, r, h, c) > h) h = h + 1;
+                int m;                                       // min over radius h - 1
+                if (h >= 2) {
+                    m = window_min<TC>(s_lvl, L, r, h - 1, c);
+                } else {
+                    m = h == 1 ? gv : 255;                   // radius 0, or the empty window
+                }
+                if (h >= 2 && m <= h - 1) {
+                    h = h - 1;
+                } else {
+                    if (r - h >= 0) m = min(m, int(s_lvl[(r - h) * TC + c]));
+                    if (r + h < L) m = min(m, int(s_lvl[(r + h) * TC + c]));
+                    if (m > h) h = h + 1;
+                }
             }
-            s_lvl[r * TC + c] = uint8_t(h);
-        }
-    }
-    __syncthreads();
-    // ---- store the tile back in place
-    if (lg.vec_ok) {
-        for (int r = tid; r < L; r += kThreads)
-            *reinterpret_cast<uint4*>(base + int64_t(r) * lg.s) = reinterpret_cast<uint4*>(s_lvl)[r];
-    } else {
-        for (int i = tid; i < L * TC; i += kThreads) {
-            const int r = i / TC, c = i - r * TC;
-            if (c < ncols) base[int64_t(r) * lg.s + c] = s_lvl[r * TC + c];
+            col[int64_t(r) * lg.s] = uint8_t(h);
         }
     }
 }
 
 }  // namespace
 
-size_t line_pass_smem(int L)
+static size_t line_pass_smem_tc(int L, int TC)
 {
     int J = 0;
     while (J < kMaxLevels - 1 && (2 << J) <= L) ++J;
-    return size_t(J + 1) * size_t(L) * kLineTile;
+    return size_t(J + 1) * size_t(L) * TC;
 }
+
+size_t line_pass_smem(int L) { return line_pass_smem_tc(L, kLineTile); }
 
 size_t xpass_smem(int gx, int K)
 {
@@ -418,17 +434,27 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
     int J = 0;
     while (J < kMaxLevels - 1 && (2 << J) <= lg.L) ++J;
     lg.J = J;
-    // segments so that the 16 columns x segments of a tile cover about one CTA of threads
-    lg.seg = (lg.L * kLineTile + kThreads - 1) / kThreads;
+    // Batched passes take 32-column tiles (a warp owns one segment and stores 32 bytes
+    // per row) while the table still lets 3 CTAs share an SM; one-map passes (the full
+    // recompute, latency-bound) and long lines keep 16 columns.  Segments are sized so
+    // that columns x segments cover about one CTA of threads.
+    const bool wide = P > 1 && line_pass_smem_tc(lg.L, 2 * kLineTile) <= size_t(kLineWideSmem);
+    const int TC = wide ? 2 * kLineTile : kLineTile;
+    lg.seg = (lg.L * TC + kThreads - 1) / kThreads;
     if (lg.seg < 4) lg.seg = 4;
-    lg.vec_ok = (g.gx % kLineTile == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
+    lg.vec_ok = (g.gx % TC == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
                 (plane % 16 == 0);
-    const size_t smem = line_pass_smem(lg.L);
+    const size_t smem = line_pass_smem_tc(lg.L, TC);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_dynamic_smem<k_line_pass>(int(smem));
+    dim3 grid((g.gx + TC - 1) / TC, lg.n_outer, P);
+    if (wide) {
+        cudaError_t e = ensure_dynamic_smem<k_line_pass<2 * kLineTile>>(int(smem));
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_line_pass<2 * kLineTile>, grid, dim3(kThreads), smem, s, buf, lg);
+    }
+    cudaError_t e = ensure_dynamic_smem<k_line_pass<kLineTile>>(int(smem));
     if (e != cudaSuccess) return e;
-    dim3 grid((g.gx + kLineTile - 1) / kLineTile, lg.n_outer, P);
-    return launch_pdl(k_line_pass, grid, dim3(kThreads), smem, s, buf, lg);
+    return launch_pdl(k_line_pass<kLineTile>, grid, dim3(kThreads), smem, s, buf, lg);
 }
 
 }  // namespace dmk

@@ -14,6 +14,7 @@ constexpr int kMaxPartitions = 256;
 constexpr int kLineTile = 16;         // columns per line-pass tile (bytes per row)
 constexpr int kMaxLevels = 9;         // sparse-table levels 0..8 cover windows up to 511
 constexpr int kLineSmemLimit = 200 * 1024;
+constexpr int kLineWideSmem = 72 * 1024;   // 32-column line tiles up to this table size
 constexpr int kXpassSmemLimit = 160 * 1024;
 
 // Partition borders as a by-value kernel parameter: v[p] is the lowest intensity of
