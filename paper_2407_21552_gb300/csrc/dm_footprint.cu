@@ -9,9 +9,10 @@
 // occupancy of the plain recompute in its exact mode.
 //
 // Tiling: one warp per block row and one lane per block column (32 x 8 blocks per CTA),
-// the CTA streaming a chunk of 4 block-slices along z.  Every voxel is read once per
-// footprint row it lies in (16-byte vectors when b = 4), classified once, and its x apron
-// reaches the neighbouring block through a warp shuffle.
+// the CTA streaming a chunk of 4 block-slices along z.  The general kernel reads a voxel
+// once per footprint row it lies in; the b = 4 / apron-1 kernel classifies each voxel row
+// about once and trades apron rows between warps in shared memory.  The x apron reaches
+// the neighbouring block through a warp shuffle.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -56,6 +57,7 @@ struct FpParams {
 enum { kModePom = 0, kModeVis = 1 };
 constexpr int kWarps = 8;
 constexpr int kMaxRows = 12;                   // b + 2a rows of a footprint when b = 4
+constexpr size_t kFpTabLimit = 64 * 1024;     // one-hot mask table in shared memory
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
@@ -272,135 +274,216 @@ __device__ __forceinline__ void onehot(unsigned c, uint32_t (&m)[NW])
     }
 }
 
-// The footprint kernel for b = 4 and apron 1, with X % 4 == 0 and an aligned volume: a
-// lane's block covers 4 voxels of a row (one vector load), its x footprint adds the last
-// voxel of the left block and the first of the right one (neighbour lanes by shuffle;
-// lanes 0 / 31 load theirs with a predicated load), and the 6 footprint rows of a block
-// row are unrolled.  Min / max are taken on raw intensities and clamped once (clamping is
-// monotone).  Same outputs as k_footprint.
-template <typename T, int NW, int MODE>
+// One-hot partition mask of an intensity: from the mask table (TAB) or the class table.
+template <int NW, int MODE, bool TAB>
+__device__ __forceinline__ void lookup_mask(const unsigned char* s_tab, unsigned v, uint32_t (&m)[NW])
+{
+    if (TAB) {
+        const uint32_t* t = reinterpret_cast<const uint32_t*>(s_tab) + size_t(v) * NW;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) m[w] = t[w];
+    } else {
+        onehot<NW, MODE>(s_tab[v], m);
+    }
+}
+
+// Footprint mask and min / max of one voxel row for the b = 4, apron-1 kernel: the lane's
+// 4 voxels, the last voxel of the left block and the first of the right one (shuffles;
+// lanes 0 / 31 take the edge voxel they loaded).  `ok` (the row lies in the volume) is
+// warp-uniform.  An empty row gives mask 0 and (min, max) = (FFFF, 0).
+template <typename T, int NW, int MODE, bool TAB>
+__device__ __forceinline__ void row_footprint(const typename Quad<T>::V& q, unsigned ev, bool ok,
+                                              bool col_ok, int lane, unsigned nmax,
+                                              const unsigned char* s_tab, uint32_t (&R)[NW],
+                                              unsigned& rmn, unsigned& rmx)
+{
+#pragma unroll
+    for (int w = 0; w < NW; ++w) R[w] = 0;
+    rmn = 0xFFFFu;
+    rmx = 0;
+    if (!ok) return;
+    uint32_t core[NW], head[NW], tail[NW], edge[NW];
+    unsigned cmn = 0xFFFFu, cmx = 0, hv = 0, tv = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) core[w] = head[w] = tail[w] = edge[w] = 0;
+    if (col_ok) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned v = min(Quad<T>::get(q, k), nmax);
+            uint32_t m1[NW];
+            lookup_mask<NW, MODE, TAB>(s_tab, v, m1);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) core[w] |= m1[w];
+            if (k == 0) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) head[w] = m1[w];
+                hv = v;
+            }
+            if (k == 3) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) tail[w] = m1[w];
+                tv = v;
+            }
+            cmn = min(cmn, v);
+            cmx = max(cmx, v);
+        }
+    }
+    const bool has_e = ev != 0xFFFFFFFFu;
+    if (has_e) {
+        ev = min(ev, nmax);
+        lookup_mask<NW, MODE, TAB>(s_tab, ev, edge);
+    }
+    uint32_t left[NW], right[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        left[w] = __shfl_up_sync(0xFFFFFFFFu, tail[w], 1);
+        right[w] = __shfl_down_sync(0xFFFFFFFFu, head[w], 1);
+    }
+    const unsigned tpack = col_ok ? (tv | (tv << 16)) : 0xFFFFu;
+    const unsigned hpack = col_ok ? (hv | (hv << 16)) : 0xFFFFu;
+    unsigned lmm = __shfl_up_sync(0xFFFFFFFFu, tpack, 1);
+    unsigned rmm = __shfl_down_sync(0xFFFFFFFFu, hpack, 1);
+    if (lane == 0) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) left[w] = edge[w];
+        lmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) right[w] = edge[w];
+        rmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) R[w] = core[w] | left[w] | right[w];
+    rmn = min(cmn, min(lmm & 0xFFFFu, rmm & 0xFFFFu));
+    rmx = max(cmx, max(lmm >> 16, rmm >> 16));
+}
+
+// The footprint kernel for b = 4 and apron 1, with X % 4 == 0 and an aligned volume.  A
+// lane's block covers 4 voxels of a row (one vector load) and its x apron comes from the
+// neighbouring lanes (row_footprint).  Every voxel row is classified about once: a warp
+// classifies the 4 core rows of its block row and takes its two apron rows from the
+// neighbouring warps' first and last core rows through shared memory (one CTA barrier per
+// voxel slice, double-buffered); the CTA's first and last warps classify the CTA's outer
+// apron rows themselves.  Min / max are taken on clamped intensities.  TAB: one-hot masks
+// read from a shared-memory table (K <= 64).  Same outputs as k_footprint.
+template <typename T, int NW, int MODE, bool TAB>
 __global__ void __launch_bounds__(kWarps * 32)
 k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
-              const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
-              uint8_t* __restrict__ occ)
+               const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+               uint8_t* __restrict__ occ)
 {
+    constexpr int TW = kWarps * 32;
     extern __shared__ __align__(16) unsigned char smem[];
     pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint8_t* s_cls = smem;
-    uint32_t* s_ring = reinterpret_cast<uint32_t*>(smem + align16(size_t(p.N)));
-    uint32_t* s_rmm = s_ring + 3 * NW * kWarps * 32;
-    for (int i = tid; i < p.N; i += kWarps * 32)
-        s_cls[i] = MODE == kModePom ? lut[i] : uint8_t(cnt[i + 1] > cnt[i]);
+    unsigned char* s_tab = smem;
+    const size_t tab_bytes = TAB ? size_t(p.N) * NW * 4 : size_t(p.N);
+    uint32_t* s_ring = reinterpret_cast<uint32_t*>(smem + align16(tab_bytes));
+    uint32_t* s_rmm = s_ring + 3 * NW * TW;
+    uint32_t* s_xr = s_rmm + 3 * TW;                        // [2][2][kWarps][NW][32]
+    uint32_t* s_xmm = s_xr + 2 * 2 * kWarps * NW * 32;      // [2][2][kWarps][32]
+    for (int i = tid; i < p.N; i += TW) {
+        if (TAB) {
+            const unsigned c = lut[i];
+            uint32_t* t = reinterpret_cast<uint32_t*>(s_tab) + size_t(i) * NW;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) t[w] = ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
+        } else {
+            s_tab[i] = MODE == kModePom ? lut[i] : uint8_t(cnt[i + 1] > cnt[i]);
+        }
+    }
     __syncthreads();
     const int bx = blockIdx.x * 32 + lane, by = blockIdx.y * kWarps + warp;
-    if (by >= p.gy) return;                                   // warp-uniform; no CTA barrier follows
+    const bool by_ok = by < p.gy;           // warp-uniform; every warp joins the barriers
     const int X = p.X, Y = p.Y;
     const unsigned nmax = unsigned(p.N - 1);
     const bool col_ok = bx < p.gx;
     const int xc0 = bx * 4;
-    // edge voxel of this lane: left neighbour's last voxel (lane 0), right's first (lane 31)
     const int xe = lane == 0 ? xc0 - 1 : xc0 + 4;
     const bool edge_ok = col_ok && (lane == 0 || lane == 31) && xe >= 0 && xe < X;
     const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
     const int zs = max(0, zb0 * 4 - 1), ze = min(p.Z - 1, (zb1 - 1) * 4 + 4);
-    const int yb = by * 4 - 1;                                // first footprint row
+    const int y0 = by * 4;                                  // first core row
+    // the extra row: the CTA's top apron row (warp 0) or bottom apron row (last warp)
+    const bool has_x = warp == 0 || warp == kWarps - 1;
+    const int yx = warp == 0 ? y0 - 1 : y0 + 4;
     const int64_t rowX = X;
     for (int z = zs; z <= ze; ++z) {
         const T* slice = vol + int64_t(z) * Y * rowX;
-        typename Quad<T>::V q[6];
-        unsigned e[6];
+        typename Quad<T>::V q[5];
+        unsigned e[5];
+        bool okr[5];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {                         // issue every load first
-            const int y = yb + r;
-            const bool ok = y >= 0 && y < Y;
-            if (ok && col_ok)
-                q[r] = *reinterpret_cast<const typename Quad<T>::V*>(slice + int64_t(y) * rowX + xc0);
-            e[r] = (ok && edge_ok) ? unsigned(slice[int64_t(y) * rowX + xe]) : 0xFFFFFFFFu;
+        for (int t = 0; t < 5; ++t) {                         // issue every load first
+            const int y = t < 4 ? y0 + t : yx;
+            okr[t] = (t < 4 || has_x) && y >= 0 && y < Y;     // warp-uniform
+            q[t] = typename Quad<T>::V{};
+            if (okr[t] && col_ok)
+                q[t] = *reinterpret_cast<const typename Quad<T>::V*>(slice + int64_t(y) * rowX + xc0);
+            e[t] = (okr[t] && edge_ok) ? unsigned(slice[int64_t(y) * rowX + xe]) : 0xFFFFFFFFu;
         }
+        uint32_t R[5][NW];
+        unsigned rmn[5], rmx[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+            row_footprint<T, NW, MODE, TAB>(q[t], e[t], okr[t], col_ok, lane, nmax, s_tab, R[t],
+                                            rmn[t], rmx[t]);
+        // publish the first and last core rows for the neighbouring warps
+        const int buf = z & 1;
+        uint32_t* xf = s_xr + ((buf * 2 + 0) * kWarps + warp) * NW * 32 + lane;
+        uint32_t* xl = s_xr + ((buf * 2 + 1) * kWarps + warp) * NW * 32 + lane;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            xf[w * 32] = R[0][w];
+            xl[w * 32] = R[3][w];
+        }
+        s_xmm[((buf * 2 + 0) * kWarps + warp) * 32 + lane] = rmn[0] | (rmx[0] << 16);
+        s_xmm[((buf * 2 + 1) * kWarps + warp) * 32 + lane] = rmn[3] | (rmx[3] << 16);
+        __syncthreads();
         uint32_t S[NW];
+        unsigned smn = min(min(rmn[0], rmn[1]), min(rmn[2], rmn[3]));
+        unsigned smx = max(max(rmx[0], rmx[1]), max(rmx[2], rmx[3]));
 #pragma unroll
-        for (int w = 0; w < NW; ++w) S[w] = 0;
-        unsigned smn = 0xFFFFu, smx = 0;
+        for (int w = 0; w < NW; ++w) S[w] = R[0][w] | R[1][w] | R[2][w] | R[3][w];
+        if (warp > 0) {                                       // row y0 - 1: warp above's last
+            const uint32_t* nl = s_xr + ((buf * 2 + 1) * kWarps + warp - 1) * NW * 32 + lane;
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-            const int y = yb + r;
-            const bool ok = y >= 0 && y < Y;                  // warp-uniform
-            if (!ok) continue;
-            uint32_t core[NW], head[NW], tail[NW], edge[NW];
-            unsigned cmn = 0xFFFFu, cmx = 0, hv = 0, tv = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) core[w] = head[w] = tail[w] = edge[w] = 0;
-            if (col_ok) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned raw = Quad<T>::get(q[r], k);
-                    const unsigned v = min(raw, nmax);
-                    uint32_t m1[NW];
-                    onehot<NW, MODE>(s_cls[v], m1);
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) core[w] |= m1[w];
-                    if (k == 0) {
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) head[w] = m1[w];
-                        hv = v;
-                    }
-                    if (k == 3) {
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) tail[w] = m1[w];
-                        tv = v;
-                    }
-                    cmn = min(cmn, v);
-                    cmx = max(cmx, v);
-                }
-            }
-            unsigned ev = e[r];
-            const bool has_e = ev != 0xFFFFFFFFu;
-            if (has_e) {
-                ev = min(ev, nmax);
-                onehot<NW, MODE>(s_cls[ev], edge);
-            }
-            uint32_t left[NW], right[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                left[w] = __shfl_up_sync(0xFFFFFFFFu, tail[w], 1);
-                right[w] = __shfl_down_sync(0xFFFFFFFFu, head[w], 1);
-            }
-            // neighbours' edge values as (min, max); an absent neighbour is (FFFF, 0)
-            const unsigned tpack = col_ok ? (tv | (tv << 16)) : 0xFFFFu;
-            const unsigned hpack = col_ok ? (hv | (hv << 16)) : 0xFFFFu;
-            unsigned lmm = __shfl_up_sync(0xFFFFFFFFu, tpack, 1);
-            unsigned rmm = __shfl_down_sync(0xFFFFFFFFu, hpack, 1);
-            if (lane == 0) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) left[w] = edge[w];
-                lmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
-            }
-            if (lane == 31) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) right[w] = edge[w];
-                rmm = has_e ? (ev | (ev << 16)) : 0xFFFFu;
-            }
-#pragma unroll
-            for (int w = 0; w < NW; ++w) S[w] |= core[w] | left[w] | right[w];
-            smn = min(smn, min(cmn, min(lmm & 0xFFFFu, rmm & 0xFFFFu)));
-            smx = max(smx, max(cmx, max(lmm >> 16, rmm >> 16)));
+            for (int w = 0; w < NW; ++w) S[w] |= nl[w * 32];
+            const unsigned mm = s_xmm[((buf * 2 + 1) * kWarps + warp - 1) * 32 + lane];
+            smn = min(smn, mm & 0xFFFFu);
+            smx = max(smx, mm >> 16);
         }
+        if (warp < kWarps - 1) {                              // row y0 + 4: warp below's first
+            const uint32_t* nf = s_xr + ((buf * 2 + 0) * kWarps + warp + 1) * NW * 32 + lane;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) S[w] |= nf[w * 32];
+            const unsigned mm = s_xmm[((buf * 2 + 0) * kWarps + warp + 1) * 32 + lane];
+            smn = min(smn, mm & 0xFFFFu);
+            smx = max(smx, mm >> 16);
+        }
+        if (has_x) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) S[w] |= R[4][w];
+            smn = min(smn, rmn[4]);
+            smx = max(smx, rmx[4]);
+        }
+        if (!by_ok) continue;
         // hand the slice to the blocks whose z footprint holds it
         const int bzc = z >> 2;
         for (int bz = max(zb0, bzc - 1); bz <= min(zb1 - 1, bzc + 1); ++bz) {
             const int f0 = max(0, bz * 4 - 1), f1 = min(p.Z - 1, bz * 4 + 4);
             if (z < f0 || z > f1) continue;
             const int slot = bz % 3;
-            uint32_t* rg = s_ring + slot * NW * (kWarps * 32) + tid;
-            uint32_t* rm = s_rmm + slot * (kWarps * 32) + tid;
+            uint32_t* rg = s_ring + slot * NW * TW + tid;
+            uint32_t* rm = s_rmm + slot * TW + tid;
             unsigned mn = smn, mx = smx;
             if (z == f0) {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] = S[w];
+                for (int w = 0; w < NW; ++w) rg[w * TW] = S[w];
             } else {
 #pragma unroll
-                for (int w = 0; w < NW; ++w) rg[w * kWarps * 32] |= S[w];
+                for (int w = 0; w < NW; ++w) rg[w * TW] |= S[w];
                 mn = min(mn, *rm & 0xFFFFu);
                 mx = max(mx, *rm >> 16);
             }
@@ -409,8 +492,8 @@ k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__
                 const int64_t blk = (int64_t(bz) * p.gy + by) * p.gx + bx;
                 if (MODE == kModePom) {
                     for (int w64 = 0; w64 < p.W64; ++w64) {
-                        const uint32_t lo = (2 * w64 < NW) ? rg[(2 * w64) * kWarps * 32] : 0u;
-                        const uint32_t hi = (2 * w64 + 1 < NW) ? rg[(2 * w64 + 1) * kWarps * 32] : 0u;
+                        const uint32_t lo = (2 * w64 < NW) ? rg[(2 * w64) * TW] : 0u;
+                        const uint32_t hi = (2 * w64 + 1 < NW) ? rg[(2 * w64 + 1) * TW] : 0u;
                         mask[blk * p.W64 + w64] = uint64_t(lo) | (uint64_t(hi) << 32);
                     }
                     if (minmax) {
@@ -447,10 +530,21 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     const T* v = static_cast<const T*>(vol);
     cudaError_t e;
     if (fast && g.a == 1) {
-        e = ensure_dynamic_smem<k_footprint41<T, NW, MODE>>(int(smem));
+        const size_t xsm = size_t(2) * 2 * kWarps * (NW + 1) * 32 * 4;   // row exchange
+        if constexpr (MODE == kModePom && NW <= 2) {
+            if (size_t(N) * NW * 4 <= kFpTabLimit) {
+                const size_t sm = align16(size_t(N) * NW * 4) + size_t(3) * (NW + 1) * kWarps * 32 * 4 + xsm;
+                e = ensure_dynamic_smem<k_footprint41<T, NW, MODE, true>>(int(sm));
+                if (e != cudaSuccess) return e;
+                return launch_pdl(k_footprint41<T, NW, MODE, true>, grid, dim3(kWarps * 32), sm, s,
+                                  v, p, lut, cnt, mask, minmax, occ);
+            }
+        }
+        const size_t sm = smem + xsm;
+        e = ensure_dynamic_smem<k_footprint41<T, NW, MODE, false>>(int(sm));
         if (e != cudaSuccess) return e;
-        return launch_pdl(k_footprint41<T, NW, MODE>, grid, dim3(kWarps * 32), smem, s, v, p, lut,
-                          cnt, mask, minmax, occ);
+        return launch_pdl(k_footprint41<T, NW, MODE, false>, grid, dim3(kWarps * 32), sm, s, v, p,
+                          lut, cnt, mask, minmax, occ);
     }
     if (fast) {
         e = ensure_dynamic_smem<k_footprint<T, NW, MODE, true>>(int(smem));
