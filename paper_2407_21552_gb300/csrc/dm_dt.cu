@@ -9,9 +9,12 @@
 // commutes with every min and max here, so saturating uint8 arithmetic stays exact.
 //
 // x pass: warp ballots turn a row's occupancy into a bit line in shared memory; for every
-// 32-bit word the nearest set bit left of it and right of it are precomputed, so each
-// output is one masked clz/ffs on its own word plus those two lookups.  Four consecutive
-// outputs per thread are stored as one 32-bit word.
+// 32-bit word the nearest set bit left of it and right of it are precomputed.  The K-map
+// pass gives each thread 16 consecutive blocks of one bit line: their left and right
+// neighbours' nearest bits come from the rest of the word or those tables, two 16-step
+// scans give the 16 distances, and one 16-byte store writes them.  The one-map pass (full
+// recompute) takes one masked clz/ffs plus the two lookups per output, four outputs per
+// 32-bit store.
 //
 // y / z passes: a CTA stages a tile of 16 or 32 neighbouring lines (full line length) in
 // shared memory and builds a doubling table of window minima (level j holds the min over
@@ -37,6 +40,7 @@ struct XGeom {
     int nw;             // 32-bit words per bit line
     int64_t plane;
     int vec4;           // rows are 4-byte aligned: store 4 outputs as one word
+    int vec16;          // rows are 16-byte aligned: store 16 outputs as one vector
 };
 
 struct SrcMinMax8 {     // min/max occupancy: one visible intensity in [min, max]
@@ -87,6 +91,9 @@ __device__ __forceinline__ void nearest_tables(const uint32_t* bits, int nw, int
 
 // K planes from the POM masks; one CTA per block row, 64 partitions (one mask word) at a
 // time.  Shared memory: bits [cap][nw] uint32, prev / next [cap][nw] int16, cap = min(64, K).
+// Outputs: one thread per (partition, 16 consecutive blocks); the nearest set bit left and
+// right of its 16 blocks comes from the rest of the word or the prev / next tables, then
+// two 16-step scans give every distance, stored as one 16-byte vector.
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
@@ -101,40 +108,58 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
     const int row = blockIdx.x;                              // z * gy + y
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rbase = int64_t(row) * xg.gx;
+    const int nh = 2 * nw;                                   // 16-block items per bit line
 #pragma unroll 1
     for (int w = 0; w < W; ++w) {
         const int np = min(64, K - w * 64);
         if (w) __syncthreads();                              // previous chunk consumed
         for (int x0 = 0; x0 < xg.gx; x0 += kThreads) {
+            if (x0 + warp * 32 >= xg.gx) continue;           // warp-uniform: no blocks here
             const int x = x0 + tid;
             const uint64_t m = x < xg.gx ? mask[(rbase + x) * W + w] : 0;
             const int wi = (x0 >> 5) + warp;
             for (int q = 0; q < np; ++q) {
                 const unsigned bal = __ballot_sync(0xFFFFFFFFu, (m >> q) & 1);
-                if (lane == 0 && wi < nw) s_bits[q * nw + wi] = bal;
+                if (lane == 0) s_bits[q * nw + wi] = bal;
             }
         }
         __syncthreads();
         for (int q = tid; q < np; q += kThreads)
             nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
         __syncthreads();
-        // outputs: warps over partitions, lanes over groups of 4 consecutive blocks
-        for (int q = warp; q < np; q += kThreads / 32) {
-            const uint32_t* bits = s_bits + q * nw;
-            const int16_t* pv = s_prev + q * nw;
-            const int16_t* nx = s_next + q * nw;
-            uint8_t* dst = out + int64_t(w * 64 + q) * xg.plane + rbase;
-            for (int x = lane * 4; x < xg.gx; x += 128) {
-                if (xg.vec4 && x + 3 < xg.gx) {
-                    unsigned v = nearest_bit(bits, pv, nx, x) |
-                                 (nearest_bit(bits, pv, nx, x + 1) << 8) |
-                                 (nearest_bit(bits, pv, nx, x + 2) << 16) |
-                                 (nearest_bit(bits, pv, nx, x + 3) << 24);
-                    *reinterpret_cast<uint32_t*>(dst + x) = v;
-                } else {
-                    for (int k = 0; k < 4 && x + k < xg.gx; ++k)
-                        dst[x + k] = uint8_t(nearest_bit(bits, pv, nx, x + k));
-                }
+        for (int it = tid; it < np * nh; it += kThreads) {
+            const int q = it / nh, hw = it - q * nh;
+            const int wi = hw >> 1, half = hw & 1;
+            const int xb = wi * 32 + half * 16;              // first block of the item
+            if (xb >= xg.gx) continue;
+            const uint32_t b = s_bits[q * nw + wi];
+            const unsigned below = half ? (b & 0xFFFFu) : 0u;    // bits left of the 16 blocks
+            const unsigned above = half ? 0u : (b >> 16);        // bits right of them
+            int last = below ? (wi * 32 + 31 - __clz(below)) : int(s_prev[q * nw + wi]);
+            int nxt = above ? (wi * 32 + 16 + __ffs(above) - 1) : int(s_next[q * nw + wi]);
+            const unsigned hb = (b >> (16 * half)) & 0xFFFFu;
+            int dl[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if ((hb >> i) & 1u) last = xb + i;
+                dl[i] = xb + i - last;
+            }
+            unsigned pk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int i = 15; i >= 0; --i) {
+                if ((hb >> i) & 1u) nxt = xb + i;
+                const int d = min(min(dl[i], nxt - (xb + i)), 255);
+                pk[i >> 2] |= unsigned(d) << (8 * (i & 3));
+            }
+            uint8_t* dst = out + int64_t(w * 64 + q) * xg.plane + rbase + xb;
+            if (xg.vec16 && xb + 16 <= xg.gx) {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            } else if (xg.vec4 && xb + 16 <= xg.gx) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) reinterpret_cast<uint32_t*>(dst)[k] = pk[k];
+            } else {
+                for (int i = 0; i < 16 && xb + i < xg.gx; ++i)
+                    dst[i] = uint8_t(pk[i >> 2] >> (8 * (i & 3)));
             }
         }
     }
@@ -213,6 +238,8 @@ XGeom xgeom(const Geometry& g, int64_t plane, const void* out)
     x.plane = plane;
     x.vec4 = (g.gx % 4 == 0) && (plane % 4 == 0) &&
              ((reinterpret_cast<uintptr_t>(out) & 3) == 0);
+    x.vec16 = (g.gx % 16 == 0) && (plane % 16 == 0) &&
+              ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     return x;
 }
 
