@@ -277,3 +277,34 @@ def test_checkpoint_resume_without_recompute(tiny, tmp_path):
         other.load(path)
     fresh.close()
     other.close()
+
+
+# ------------------------------------------------------- seeded random configurations
+def random_config(seed):
+    """A random configuration: dims 1..70 (1..40 when b <= 2), b in 1..16, apron 0..b,
+    uint8 / 12-bit / 16-bit, N from 2 to 65536, K from 1 to min(N, 256), and explicit
+    random borders for about a third of them."""
+    rng = np.random.default_rng(9000 + seed)
+    b = int(rng.choice([1, 2, 3, 4, 4, 4, 5, 7, 8, 16]))
+    a = int(rng.integers(0, b + 1)) if rng.random() < 0.2 else int(rng.integers(0, min(b, 2) + 1))
+    u16 = rng.random() < 0.5
+    N = int(rng.choice([256, 300, 1024, 4096, 4096, 65536])) if u16 else int(rng.choice([2, 16, 100, 256]))
+    K = int(rng.integers(1, min(N, 16) + 1)) if rng.random() < 0.5 else int(rng.integers(1, min(N, 256) + 1))
+    hi = 40 if b <= 2 else 70
+    shape = tuple(int(rng.integers(1, hi + 1)) for _ in range(3))
+    borders = None
+    if K > 1 and rng.random() < 0.35:
+        inner = np.sort(rng.choice(np.arange(1, N), K - 1, replace=False))
+        borders = [0] + [int(v) for v in inner] + [N]
+    return shape, b, a, N, K, (np.uint16 if u16 else np.uint8), borders, rng
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_configs(seed):
+    shape, b, a, N, K, dt, borders, rng = random_config(seed)
+    vol = rand_volume(rng, shape, N, dt, blob=int(rng.integers(1, 5)))
+    eng, vd, ref = check_build(vol, b, a, N, K, borders)
+    bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
+    tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 4) + T.special_tfs(N, bd)
+    check_updates(eng, vd, vol, ref, tfs, b, a, borders, exact_every=5)
+    eng.close()
