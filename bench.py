@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -40,12 +41,12 @@ L2_FLUSH_BYTES = 256 << 20
 NCU_TRAFFIC = {
     # k_update_fused on ct (G = 2,097,152), edits with |S| = 7: 14,768,896 B read, 0 B
     # written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "2fb83d45b154b107", "G": 2097152,
+    "ct": {"source_sha": "9d8d3d8722cfcdfe", "G": 2097152,
            "read_per_active_plane": 14768896 / 7, "write": 0.0},
     # k_update_fused on the 1024x1024x448 cut of the large recipe (G = 7,340,032), an edit
     # with |S| = 31: 227,641,344 B read, 7,651,584 B written; scaled to the large grid by
     # G (the traffic is |S| * G + G + a fixed 0.1 MB); profiles/update_kernel_mid.md
-    "large": {"source_sha": "2fb83d45b154b107", "G": 7340032,
+    "large": {"source_sha": "9d8d3d8722cfcdfe", "G": 7340032,
               "read_per_active_plane": 227641344 / 31, "write": 7651584.0},
 }
 
@@ -55,7 +56,7 @@ def ncu_traffic(workload, G, mean_active):
     to the mean number of active planes; None once the kernel source has changed."""
     tr = NCU_TRAFFIC.get(workload)
     src = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc", "dm_update.cu")
-    if not tr or tr.get("source_sha") != file_sha(src):
+    if not tr or tr.get("source_sha") != code_sha(src):
         return None
     return float((tr["read_per_active_plane"] * mean_active + tr["write"]) * G / tr["G"])
 
@@ -102,8 +103,14 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
-def file_sha(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+def code_sha(path):
+    """Hash of a source file's code with comments and whitespace removed, so that the
+    recorded ncu traffic stays tied to the kernel and not to its comments."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = " ".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 class ClockSampler:

@@ -166,7 +166,8 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // active plane into its own shared-memory slots, kAsyncBatch planes per group with two
 // groups in flight (no registers held by the loads), and folds a group once it landed.
 // `stage` is this thread's [2][kAsyncBatch] slot array (stride `ld` uint4 between slots);
-// s_off is padded as for combine_chunks.
+// s_off holds the n plane offsets followed by kAsyncBatch copies of the first one, so a
+// last, partial batch reads plane 0 again (same bytes, no effect on the min).
 constexpr int kAsyncBatch = 8;
 
 __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__ pdm,
