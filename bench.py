@@ -264,11 +264,13 @@ def oracle_throughput(pdm, edits, scale, threads):
 def cpu_baseline_block(s, n_edits):
     X, Y, zs = s["slab"]
     return {"value": pct(s["upd"], 50), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": (f"z-slab {X}x{Y}x{zs} of the same volume (precompute untimed, "
-                       f"{s['pre_s']:.1f} s), {n_edits} TF edits through the oracle's step 1 + "
+            "sample": (f"z-slab {X}x{Y}x{zs} of the same volume (its precompute took "
+                       f"{s['pre_s']:.1f} s, outside the per-edit times), {n_edits} TF edits "
+                       f"through the oracle's step 1 + "
                        f"Eq. 1, single-threaded C; per-edit times scaled by G/G_slab = "
                        f"{s['scale']:.3f}"),
             "full_recompute_p50_ms": pct(s["full"], 50),
+            "precompute_ms": s["pre_s"] * 1e3 * s["scale"],
             "nproc": os.cpu_count(),
             "throughput_all_cores": {"edits_per_s": s["tput"], "threads": s["threads"],
                                      "sample": "one whole-volume-equivalent edit per thread "
