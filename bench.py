@@ -649,6 +649,7 @@ def run_batch(args, ws, rank, local):
     torch.cuda.synchronize(dev)
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    am = torch.zeros((K, n, 4), dtype=torch.int64, device=dev)     # S of every item and step
     clocks = ClockSampler(smi_gpu_id(dev))
     clocks.start()
     r0 = torch.cuda.Event(enable_timing=True)
@@ -660,7 +661,7 @@ def run_batch(args, ws, rank, local):
         flush()
         ev[k][0].record(stream)
         for i, e in enumerate(engs):
-            e.update_tf(edits[kk, i, : specs[i]["N"]], out=outs[i])
+            e.update_tf(edits[kk, i, : specs[i]["N"]], out=outs[i], active_mask=am[k, i])
         ev[k][1].record(stream)
         items_k = items_for(tr.block, kk)            # host-side list, built before timing
         flush()
@@ -679,6 +680,15 @@ def run_batch(args, ws, rank, local):
     bat = [ev[k][2].elapsed_time(ev[k][3]) for k in range(K)]
     gra = [ev[k][4].elapsed_time(ev[k][5]) for k in range(K)]
     vox = sum(int(np.prod(sp["dims"])) for sp in specs)
+    # algorithmic bytes of a step: sum over items of (|S_i| + 1) * G_i (the same edits go
+    # through the separate and the batched updates)
+    Gs = np.array([e.G for e in engs], dtype=np.float64)
+    masks = am.cpu().numpy().view(np.uint64)
+    nact = np.array([[sum(bin(int(x)).count("1") for x in masks[k, i]) for i in range(n)]
+                     for k in range(K)], dtype=np.float64)
+    step_bytes = ((nact + 1) * Gs).sum(axis=1)
+    bat_gbs = step_bytes / (np.array(bat) * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
     if rank != 0:
         return
     res = {
@@ -690,16 +700,23 @@ def run_batch(args, ws, rank, local):
                                f"one TF edit each", "voxels": vox,
                    "l2": "flushed before every timed call (256 MiB write, then 256 MiB read)"},
         "separate_launches": {"p50_ms": pct(sep, 50), "p99_ms": pct(sep, 99),
-                              "launches": 2 * n},
+                              "launches": n},
         "batched": {"p50_ms": pct(bat, 50), "p99_ms": pct(bat, 99), "launches": 2},
         "batched_graph": {"p50_ms": pct(gra, 50), "p99_ms": pct(gra, 99),
                           "note": "includes the device copy of the 64 TFs into the "
                                   "graph's fixed buffers"},
         "speedup_batched_vs_separate_p50": pct(sep, 50) / pct(bat, 50),
+        "roofline": {"kernel": "k_active_batch + k_combine_batch (launch pair)", "bound": "hbm",
+                     "achieved": float(step_bytes.sum() / (np.sum(bat) * 1e-3) / 1e9),
+                     "achieved_p50_step": float(np.median(bat_gbs)), "peak": peak,
+                     "unit": "GB/s", "frac": float(step_bytes.sum() / (np.sum(bat) * 1e-3) / 1e9) / peak,
+                     "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_step": float(step_bytes.mean()),
+                     "mean_active_partitions": float(nact.mean())},
         "autotune": {"block": tr.block, "combine_ctas_per_sm": tr.ctas_per_sm,
                      "target_us": args.batch_target_us,
                      "table_us": {f"b{b}_c{c}": v for (b, c), v in tr.table.items()}},
-        "gpu_launches": K * (2 * n + 2 + 2),
+        "gpu_launches": K * (n + 2 + 2),
         "clocks": clk,
     }
     print(json.dumps(res))

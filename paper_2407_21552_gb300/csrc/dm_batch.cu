@@ -2,10 +2,12 @@
 //
 // Each item is one volume's resident PDMs (§3.1) with its own TF.  Two launches cover up
 // to kMaxBatch items: an active-set kernel with one CTA per item (§3.1 step 1, from the
-// item's partition table built at precompute time), then a persistent combine (Eq. 1) over
-// one flattened list of 4 KiB work units of all items, launched with programmatic
-// dependent launch.  Per-item descriptors are passed by value as kernel parameters, so
-// the pair needs no device-side setup and can be captured in a CUDA graph.
+// item's partition table built at precompute time; all loads of a batch issued before any
+// is used), then a persistent combine (Eq. 1) over one flattened list of 4 KiB work units
+// of all items, launched with programmatic dependent launch.  The bytes past an item's
+// last whole 16-byte chunk are folded by one warp per item, its lanes over the planes.
+// Per-item descriptors are passed by value as kernel parameters, so the pair needs no
+// device-side setup and can be captured in a CUDA graph.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -57,11 +59,19 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < kMaxPartitions / 32) s_S[tid] = 0;
     __syncthreads();
-    for (int i = tid; i < it.N; i += kActThreads) {
-        if (__ldg(it.tf + 4 * int64_t(i) + 3) > 0.0f) {
-            const unsigned p = it.lut[i];
-            atomicOr(&s_S[p >> 5], 1u << (p & 31));
+    constexpr int kLB = 8;                                    // loads issued before any use
+    for (int base = 0; base < it.N; base += kActThreads * kLB) {
+        float a[kLB];
+        uint8_t c[kLB];
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) {
+            const int i = base + k * kActThreads + tid;
+            a[k] = i < it.N ? __ldg(it.tf + 4 * int64_t(i) + 3) : 0.0f;
+            c[k] = i < it.N ? it.lut[i] : uint8_t(0);
         }
+#pragma unroll
+        for (int k = 0; k < kLB; ++k)
+            if (a[k] > 0.0f) atomicOr(&s_S[c[k] >> 5], 1u << (c[k] & 31));
     }
     __syncthreads();
     (void)lane;
@@ -69,6 +79,32 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
     const int n = plan_maps(s_S, it.K, it.J, s_list, s_scan);
     for (int j = tid; j < n; j += kActThreads) it.act[j] = s_list[j];
     if (tid == 0) *it.nact = n;
+}
+
+// Bytes past the last whole 16-byte chunk of an item (fewer than 16): one warp, the lanes
+// over the item's active planes, then a warp min per byte.
+__device__ __forceinline__ void item_tail(const Item& it, int lane)
+{
+    const int64_t g0 = (it.G >> 4) << 4;
+    const int rem = int(it.G - g0);
+    if (rem == 0) return;                                     // warp-uniform
+    const int n = *it.nact;
+    unsigned m[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) m[r] = 255;
+    for (int j = lane; j < n; j += 32) {
+        const uint8_t* src = it.pdm + int64_t(it.act[j]) * it.plane + g0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (r < rem) m[r] = min(m[r], unsigned(src[r]));
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        if (r < rem) {
+            const unsigned v = __reduce_min_sync(0xFFFFFFFFu, m[r]);
+            if (lane == 0) it.out[g0 + r] = uint8_t(v);
+        }
+    }
 }
 
 // Eq. 1 over every item's work units; CTA b takes a contiguous range of units.
@@ -81,6 +117,10 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
     uint4 (*s_stage)[kB][kThreads] = reinterpret_cast<uint4 (*)[kB][kThreads]>(s_dyn);
     pdl_wait();                                               // active sets are visible
     const int tid = threadIdx.x;
+    // bytes past the last whole chunk of each vectorised item: one warp per item
+    for (int i = int(blockIdx.x) * (kThreads / 32) + (tid >> 5); i < P.n;
+         i += int(gridDim.x) * (kThreads / 32))
+        if (P.it[i].vec) item_tail(P.it[i], tid & 31);
     const int64_t total = P.unit_prefix[P.n];
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t u0 = int64_t(blockIdx.x) * per, u1 = min(total, u0 + per);
@@ -123,14 +163,6 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
                 }
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
                 __stcs(reinterpret_cast<uint4*>(it.out + (lane_unit << 4)), acc);
-            }
-            // the last < 16 bytes of a vectorised item: first unit's thread 0
-            if (u == P.unit_prefix[item] && tid == 0) {
-                for (int64_t i = nvec << 4; i < it.G; ++i) {
-                    unsigned a = 255;
-                    for (int j = 0; j < n; ++j) a = min(a, unsigned(it.pdm[s_off[j] + i]));
-                    it.out[i] = uint8_t(a);
-                }
             }
         } else if (lane_unit < it.G) {
             unsigned a = 255;
