@@ -8,7 +8,8 @@ with pending edits and no edit on the device, its oldest one (so every edit gets
 of its own TF, and a session's working memory is used by one batch at a time), and hands
 the batch to the executor, which runs it on the slot's stream without waiting; batches of
 different sessions overlap on the device.  A request completes when its batch's
-completion event has fired; its latency is arrival to completion.
+completion event has fired; its latency is arrival to completion.  An edit can be withdrawn
+until it joins a batch; a session still waiting for admission can be withdrawn too.
 
 The scheduler (`Scheduler`) holds no GPU state and is tested with a fake executor; the
 executor for the GPU (`DeviceExecutor`) does every step through libdm: the host TFs are
@@ -31,6 +32,7 @@ class Request:
     rid: int = 0
     t_submit: float = 0.0
     t_done: float = 0.0
+    cancelled: bool = False
 
 
 @dataclass
@@ -54,6 +56,7 @@ class Stats:
     batch_sizes: list = field(default_factory=list)
     admitted: list = field(default_factory=list)
     rejected_waits: int = 0
+    cancelled: int = 0
 
 
 class Scheduler:
@@ -116,6 +119,41 @@ class Scheduler:
         self._rid += 1
         self.pending.setdefault(sid, collections.deque()).append(r)
         return r
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw an edit that has not reached the device yet.  An edit already in a
+        batch runs to completion (its device work is not interrupted); returns whether
+        the edit was withdrawn."""
+        q = self.pending.get(req.session)
+        if req.cancelled or q is None or req not in q:
+            return False
+        q.remove(req)
+        req.cancelled = True
+        self.stats.cancelled += 1
+        return True
+
+    def cancel_session_edits(self, sid: int) -> int:
+        """Withdraw every edit of a session that has not reached the device; returns how
+        many.  The session can close once its in-flight edit (if any) completes."""
+        q = self.pending.get(sid)
+        if not q:
+            return 0
+        n = len(q)
+        for r in q:
+            r.cancelled = True
+        q.clear()
+        self.stats.cancelled += n
+        return n
+
+    def withdraw_waiting(self, sid: int) -> bool:
+        """Drop a session that is still waiting for admission (it never held budget)."""
+        for spec in list(self.waiting):
+            if spec.sid == sid:
+                self.waiting.remove(spec)
+                while self.waiting and self.used + self.waiting[0].device_bytes <= self.budget:
+                    self._admit(self.waiting.popleft())
+                return True
+        return False
 
     def has_work(self) -> bool:
         return bool(self.inflight) or any(self.pending.values())

@@ -1,6 +1,7 @@
 """Scheduler of the serving loop, on the CPU with a fake executor: HBM-budget admission,
 one edit per session per batch in arrival order, a fixed number of batches in flight,
-latency from arrival to completion, and sessions leaving only when idle."""
+latency from arrival to completion, sessions leaving only when idle, and cancelled
+requests (withdrawn before they reach the device) and withdrawn waiting sessions."""
 import pytest
 
 from paper_2407_21552_gb300.serving import Scheduler, SessionSpec
@@ -102,3 +103,54 @@ def test_max_batch_and_rotation():
     ex.launched[0]["done"] = True
     s.poll()
     assert ex.launched[1]["reqs"] == [(2, "s2")]
+
+
+def test_cancelled_requests_never_reach_the_device():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=1)
+    s.open_session(SessionSpec(0, 1))
+    s.open_session(SessionSpec(1, 1))
+    a0 = s.submit(0, "a0")
+    a1 = s.submit(0, "a1")
+    a2 = s.submit(0, "a2")
+    b0 = s.submit(1, "b0")
+    s.poll()                                           # batch {a0, b0} on the device
+    assert ex.launched[0]["reqs"] == [(0, "a0"), (1, "b0")]
+    assert not s.cancel(a0)                            # in flight: runs to completion
+    assert s.cancel(a1) and a1.cancelled
+    assert not s.cancel(a1)                            # already withdrawn
+    ex.launched[0]["done"] = True
+    s.poll()                                           # next batch skips a1
+    assert ex.launched[1]["reqs"] == [(0, "a2")]
+    assert s.stats.cancelled == 1
+    ex.launched[1]["done"] = True
+    s.poll()
+    assert not s.has_work()
+    assert [r.tf for r in s.completed] == ["a0", "b0", "a2"]
+
+
+def test_cancel_session_edits_then_close():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=1)
+    s.open_session(SessionSpec(0, 4))
+    reqs = [s.submit(0, f"e{i}") for i in range(5)]
+    s.poll()                                           # e0 on the device
+    assert s.cancel_session_edits(0) == 4
+    assert all(r.cancelled for r in reqs[1:]) and not reqs[0].cancelled
+    with pytest.raises(RuntimeError):
+        s.close_session(0)                             # e0 still in flight
+    ex.launched[0]["done"] = True
+    s.poll()
+    s.close_session(0)
+    assert ex.released == [0] and s.used == 0 and len(ex.launched) == 1
+
+
+def test_withdraw_a_waiting_session():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=1)
+    assert s.open_session(SessionSpec(0, 8))
+    assert not s.open_session(SessionSpec(1, 5))       # waits for budget
+    assert not s.open_session(SessionSpec(2, 2))       # queued behind 1
+    assert s.withdraw_waiting(1)                       # 2 now fits and is admitted
+    assert ex.admitted == [0, 2] and s.used == 10
+    assert not s.withdraw_waiting(1)
