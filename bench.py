@@ -39,15 +39,15 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
 # taken on; reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # k_update_fused on ct (G = 2,097,152), edits with |S| = 7: 14,768,896 B read, 0 B
+    # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,075,968 B read, 0 B
     # written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "9d8d3d8722cfcdfe", "G": 2097152,
-           "read_per_active_plane": 14768896 / 7, "write": 0.0},
-    # k_update_fused on the 1024x1024x448 cut of the large recipe (G = 7,340,032), an edit
-    # with |S| = 31: 227,641,344 B read, 7,651,584 B written; scaled to the large grid by
-    # G (the traffic is |S| * G + G + a fixed 0.1 MB); profiles/update_kernel_mid.md
-    "large": {"source_sha": "9d8d3d8722cfcdfe", "G": 7340032,
-              "read_per_active_plane": 227641344 / 31, "write": 7651584.0},
+    "ct": {"source_sha": "1cd92e98ef5ffe29", "G": 2097152,
+           "read_per_active_plane": 21075968 / 10, "write": 0.0},
+    # k_update_fused on the large workload itself (G = 29,425,664), an edit with |S| = 31:
+    # 912,317,952 B read, 20,611,712 B written (mean of two launches);
+    # profiles/update_kernel_large.md
+    "large": {"source_sha": "1cd92e98ef5ffe29", "G": 29425664,
+              "read_per_active_plane": 912317952 / 31, "write": 20611712.0},
 }
 
 

@@ -8,8 +8,10 @@
 //
 // §3.1 step 2, Eq. 1: D'(x,y,z) = min over p in S of PDM_p(x,y,z).  A pure streaming
 // kernel: each thread owns 16-byte chunks of the map, reads the same chunk of every active
-// plane (independent 16-byte loads, several in flight) and folds them with __vminu4.  The
-// HBM traffic is (|S| + 1) * G bytes, the algorithmic minimum.  An empty S yields 255.
+// plane (independent 16-byte loads, several in flight) and folds them with __vminu4.  On
+// large maps the chunks are taken in plane-major tiles: a warp reads 4 KiB of one plane
+// per step and keeps 8 accumulators per thread.  The HBM traffic is (|S| + 1) * G bytes,
+// the algorithmic minimum.  An empty S yields 255.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -217,6 +219,67 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
     cp_async_wait0();
 }
 
+// D' for large maps, plane-major: a CTA walks tiles of kTileChunks chunks; within a tile a
+// warp owns 256 consecutive chunks (4 KiB), lane l chunks base + 32 k + l for k < 8.
+// One step loads the warp's 4 KiB of one plane (8 cp.async per thread, each instruction
+// 512 contiguous bytes), so every DRAM burst of a step is 4 KiB of one plane; the 8
+// per-thread accumulators fold the planes and are stored once per tile.
+constexpr int kPM = 8;                                        // chunks per thread per tile
+__device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__ pdm,
+                                                     const int64_t* s_off, int n, int64_t ntiles,
+                                                     int64_t tile0, int64_t tstride, uint4* stage,
+                                                     int ld, uint8_t* __restrict__ out, int warp,
+                                                     int lane, int warps)
+{
+    const int64_t tile_chunks = int64_t(warps) * 32 * kPM;
+    auto chunk_of = [&](int64_t t, int k) {
+        return t * tile_chunks + int64_t(warp) * (32 * kPM) + k * 32 + lane;
+    };
+    int64_t t = tile0;
+    if (t >= ntiles) return;
+    if (n == 0) {
+        for (; t < ntiles; t += tstride)
+#pragma unroll
+            for (int k = 0; k < kPM; ++k)
+                __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), make_uint4(~0u, ~0u, ~0u, ~0u));
+        return;
+    }
+    auto issue = [&](int64_t tt, int p, int slot) {
+        const uint8_t* src = pdm + s_off[p];
+#pragma unroll
+        for (int k = 0; k < kPM; ++k)
+            cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
+        cp_async_commit();
+    };
+    uint4 acc[kPM];
+#pragma unroll
+    for (int k = 0; k < kPM; ++k) acc[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    int p = 0, slot = 0;
+    issue(t, 0, 0);
+    while (true) {
+        int64_t nt = t;
+        int np = p + 1;
+        if (np == n) { np = 0; nt = t + tstride; }
+        const bool more = nt < ntiles;
+        if (more) issue(nt, np, slot ^ 1); else cp_async_commit();
+        cp_async_wait1();
+#pragma unroll
+        for (int k = 0; k < kPM; ++k) acc[k] = vmin4(acc[k], stage[(slot * kPM + k) * ld]);
+        if (p == n - 1) {
+#pragma unroll
+            for (int k = 0; k < kPM; ++k) {
+                __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), acc[k]);
+                acc[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+            }
+        }
+        if (!more) break;
+        t = nt;
+        p = np;
+        slot ^= 1;
+    }
+    cp_async_wait0();
+}
+
 __global__ void __launch_bounds__(kCombineThreads)
 k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
           const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
@@ -322,9 +385,21 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     const int64_t t0 = int64_t(blockIdx.x) * kFusedThreads + tid;
     int64_t done = 0;
     if (vec_ok) {
-        combine_chunks_async(pdm, s_off, n, G >> 4, t0, stride, s_stage + tid, kFusedThreads,
-                             out);
-        done = (G >> 4) << 4;
+        // Large maps: whole plane-major tiles while every CTA gets at least two and they
+        // spread evenly (all of them when the last round fills three quarters of the CTAs,
+        // else a multiple of the grid); every other chunk through the per-chunk path.
+        const int64_t nvec = G >> 4;
+        const int64_t tile_chunks = int64_t(kFusedThreads) * kPM;
+        const int64_t grid = gridDim.x;
+        int64_t ntiles = nvec / tile_chunks;
+        if (ntiles < 2 * grid) ntiles = 0;
+        else if (ntiles % grid != 0 && 4 * (ntiles % grid) < 3 * grid) ntiles -= ntiles % grid;
+        if (ntiles > 0)
+            combine_tiles_planar(pdm, s_off, n, ntiles, blockIdx.x, grid, s_stage + tid,
+                                 kFusedThreads, out, warp, lane, kFusedThreads / 32);
+        combine_chunks_async(pdm, s_off, n, nvec, ntiles * tile_chunks + t0, stride,
+                             s_stage + tid, kFusedThreads, out);
+        done = nvec << 4;
     }
     for (int64_t i = done + t0; i < G; i += stride) {
         unsigned acc = 255;

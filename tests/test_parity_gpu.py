@@ -308,3 +308,23 @@ def test_random_configs(seed):
     tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 4) + T.special_tfs(N, bd)
     check_updates(eng, vd, vol, ref, tfs, b, a, borders, exact_every=5)
     eng.close()
+
+
+@pytest.mark.parametrize("shape", [(271, 269, 277),     # 308 tiles: a grid multiple of them
+                                   (303, 303, 303)])    # 424 tiles: all of them
+def test_plane_major_tiles_of_large_maps(shape):
+    """Maps of 20-28 M blocks (b = 1) take the update's plane-major tiles; whole tiles, the
+    chunks past them and a ragged byte tail all match the oracle."""
+    rng = np.random.default_rng(sum(shape))
+    vol = rand_volume(rng, shape, 256, np.uint8, blob=9)
+    N, K = 256, 4
+    eng = _engine(vol, 1, 0, N, K)
+    eng.build_partitions(_to_dev(vol))
+    _, pdm, _, _ = oracle.build_partitions(vol, 1, 0, N, K)
+    assert eng.G % 16 != 0 and eng.G // 16 // (512 * 8) >= 2 * 152
+    bd = T.uniform_borders(N, K)
+    for tf in T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 3) + T.special_tfs(N, bd)[:3]:
+        got = eng.update_tf(torch.from_numpy(tf).cuda()).cpu().numpy()
+        want, _ = oracle.update_tf(pdm, tf)
+        assert np.array_equal(got.reshape(want.shape), want)
+    eng.close()
