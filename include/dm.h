@@ -190,7 +190,7 @@ typedef struct dm_batch_item {
 } dm_batch_item;
 
 typedef struct dm_batch_tuning {
-    int32_t combine_ctas_per_sm;   /* persistent combine grid: CTAs per SM (0 = default 2) */
+    int32_t combine_ctas_per_sm;   /* persistent combine grid: CTAs per SM (0 = default 12) */
     int32_t reserved[3];
 } dm_batch_tuning;
 

@@ -16,7 +16,7 @@ import torch
 
 from . import _abi as A
 
-CTAS_PER_SM = (1, 2, 4, 8)
+CTAS_PER_SM = (2, 4, 8, 12, 16)
 
 
 @dataclass

@@ -110,7 +110,7 @@ __device__ __forceinline__ void item_tail(const Item& it, int lane)
 // Eq. 1 over every item's work units; CTA b takes a contiguous range of units.
 __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constant__ Params P)
 {
-    constexpr int kB = 8;                                     // plane loads per group
+    constexpr int kB = 4;                                     // plane loads per group
     __shared__ int64_t s_off[kMaxPartitions + kB];
     __shared__ int s_n;
     extern __shared__ uint4 s_dyn[];                          // [2][kB][kThreads] staging
@@ -204,9 +204,11 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = P.unit_prefix[n];
-    int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 2);
+    // many small CTAs (32 KiB of staging each, about 6 resident per SM) over 4 KiB units:
+    // the hardware's CTA scheduling balances items of different cost
+    int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 12);
     if (ctas > total) ctas = total;
-    const size_t smem = size_t(2) * 8 * kThreads * sizeof(uint4);
+    const size_t smem = size_t(2) * 4 * kThreads * sizeof(uint4);
     e = ensure_dynamic_smem<k_combine_batch>(int(smem));
     if (e != cudaSuccess) return e;
     return launch_pdl(k_combine_batch, dim3(unsigned(ctas)), dim3(kThreads), smem, s, P);

@@ -63,7 +63,7 @@ def test_batch_matches_oracle_and_single_updates():
         assert torch.equal(single, outs[i]), i
 
 
-@pytest.mark.parametrize("per_sm", [1, 2, 8])
+@pytest.mark.parametrize("per_sm", [1, 2, 8, 12, 24])
 def test_batch_longer_than_one_launch_and_tuning(per_sm):
     from paper_2407_21552_gb300 import _abi as A
     items = _engines(_small_specs(70, 10))          # > DM_BATCH_MAX_ITEMS: split in two
