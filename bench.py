@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload",
-                    choices=["ct", "tiny", "large", "mid", "batch", "serving", "render"],
+                    choices=["ct", "tiny", "large", "mid", "batch", "serving", "render",
+                             "sweep"],
                     default="ct")
     ap.add_argument("--serve-seconds", type=float, default=1.5,
                     help="serving workload: arrival window per rate and server")
@@ -796,6 +797,75 @@ def run_serving(args, ws, rank, local):
     print(json.dumps(res))
 
 
+# ---------------------------------------------------------------- partition-count sweep
+def run_sweep(args, ws, rank, local):
+    """The shape of the paper's Table 1 on the ct volume: for K = 4 .. 64 partitions, the
+    one-time precompute, the partitioned update and the plain min/max full recompute over
+    the same TF edits (CUDA events, L2 flushed before every call).  Update time grows with
+    the number of maps combined; the full recompute does not depend on K."""
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U16
+    from paper_2407_21552_gb300.build import build as build_lib
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    build_lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.WORKLOADS["ct"]
+    X, Y, Z = w["dims"]
+    vol = synth.make_volume("ct", device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush_w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush_r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.int64, device=dev)
+    E = max(8, min(args.steps, 200))
+    tfs = torch.from_numpy(np.stack(synth.tf_edit_sequence(w["seed"], w["N"], E))).to(dev)
+
+    def timed(fn, reps):
+        ts = []
+        for k in range(reps + args.warmup):
+            flush_w.zero_()
+            flush_r.max()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(k)
+            b.record(stream)
+            b.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return ts
+
+    rows = []
+    for K in (4, 8, 16, 32, 64):
+        eng = PartitionedDistanceMaps((X, Y, Z), DM_U16, w["block"], w["apron"], K, w["N"],
+                                      device=dev)
+        out = torch.empty(eng.G, dtype=torch.uint8, device=dev)
+        am = torch.zeros((E, 1), dtype=torch.int64, device=dev)
+        pre = timed(lambda k: eng.build_partitions(vol), 3)
+        upd = timed(lambda k: eng.update_tf(tfs[k % E], out=out,
+                                            active_mask=am[k % E]), E)
+        full = timed(lambda k: eng.full_recompute(tfs[k % E], out=out), E)
+        nact = np.array([bin(int(x)).count("1") for x in am.cpu().numpy().view(np.uint64)[:, 0]])
+        rows.append({"K": K, "precompute_ms": pct(pre, 50), "update_p50_ms": pct(upd, 50),
+                     "update_p99_ms": pct(upd, 99), "full_recompute_p50_ms": pct(full, 50),
+                     "speedup_p50": pct(full, 50) / pct(upd, 50),
+                     "mean_active_partitions": float(nact.mean()),
+                     "pdm_mib": K * eng.plane_stride / 2**20})
+        eng.close()
+        del eng, out
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC + " (partition-count sweep)", "value": rows[3]["update_p50_ms"],
+        "unit": "ms", "n_gpus": ws, "higher_is_better": False, "data": "synthetic",
+        "config": {"workload": workload_name("ct", w) + "; K swept over 4..64",
+                   "edits": E, "l2": "flushed before every timed call"},
+        "rows": rows,
+        "paper_context": "Table 1 reports, per dataset, the update time growing with the "
+                         "number of partitions n and a roughly linear init time in n"}))
+
+
 # --------------------------------------------------------------------- render workload
 def run_render(args, ws, rank, local):
     """Frame times of the ray caster at 2160^2 (§4.1) on the CT volume, camera circling the
@@ -908,6 +978,8 @@ def main():
         run_serving(args, ws, rank, local)
     elif args.workload == "render":
         run_render(args, ws, rank, local)
+    elif args.workload == "sweep":
+        run_sweep(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
