@@ -215,6 +215,9 @@ class DeviceExecutor:
         self.device = torch.device(device)
         self.mode = mode                      # "partitioned" or "full"
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        # one completion event per slot: a slot takes a new batch only after its last one
+        # completed, so the event is free to record again
+        self.events = [torch.cuda.Event() for _ in range(slots)]
         self.sessions = {}
         self.results = {}                     # rid -> device D' (kept if keep_results)
         self.keep_results = False
@@ -254,7 +257,7 @@ class DeviceExecutor:
             if self.keep_results:
                 for r in requests:
                     self.results[r.rid] = self.sessions[r.session]["out"][slot].clone()
-            ev = torch.cuda.Event()
+            ev = self.events[slot]
             ev.record(st)
         return ev
 
