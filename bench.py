@@ -11,14 +11,18 @@ region; the L2 is flushed (a 256 MiB write, then a 256 MiB read, so no dirty lin
 before every timed call; kernels are timed
 with CUDA events on the stream they run on; clocks are sampled with nvidia-smi during the
 timed region.  `value` is the p50 latency of the partitioned update (ms, lower is better).
+The default run (ct, 512^3) adds a leg on the large workload (1024x1024x1795), where the
+maps stream from HBM, and the CPU oracle timed on the host cores.  Other workloads:
+tiny, large, mid, batch (64 uneven volumes, one batched launch pair), serving (Poisson TF
+edits over 32 resident sessions), render (empty-space skipping) and sweep (K = 4 .. 64).
 `--impl reference` times the CPU oracle (plain C) on the host cores instead.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
-import re
 import json
+import re
 import os
 import statistics
 import subprocess
