@@ -8,13 +8,14 @@
 // and two passes of the 1D max-min transform h(i) = min_j max(|i-j|, g(j)).  Clamping
 // commutes with every min and max here, so saturating uint8 arithmetic stays exact.
 //
-// x pass: warp ballots turn a row's occupancy into a bit line in shared memory; for every
-// 32-bit word the nearest set bit left of it and right of it are precomputed.  The K-map
-// pass gives each thread 16 consecutive blocks of one bit line: their left and right
-// neighbours' nearest bits come from the rest of the word or those tables, two 16-step
-// scans give the 16 distances, and one 16-byte store writes them.  The one-map pass (full
-// recompute) takes one masked clz/ffs plus the two lookups per output, four outputs per
-// 32-bit store.
+// x pass: a row's occupancy becomes one bit line per partition in shared memory (the
+// K-map pass transposes each warp's 32 blocks x 32 partitions bit matrix with shuffles;
+// the one-map pass takes one ballot per 32 blocks); for every 32-bit word the nearest set
+// bit left of it and right of it are precomputed.  The K-map pass gives each thread 16
+// consecutive blocks of one bit line: their left and right neighbours' nearest bits come
+// from the rest of the word or those tables, two 16-step scans give the 16 distances, and
+// one 16-byte store writes them.  The one-map pass (full recompute) takes one masked
+// clz/ffs plus the two lookups per output, four outputs per 32-bit store.
 //
 // y / z passes: a CTA stages a tile of 16 or 32 neighbouring lines (full line length) in
 // shared memory and builds a doubling table of window minima (level j holds the min over
@@ -89,6 +90,22 @@ __device__ __forceinline__ void nearest_tables(const uint32_t* bits, int nw, int
     }
 }
 
+// 32x32 bit-matrix transpose across a warp: lane i holds row i (bit j = element (i, j))
+// and ends holding column i (bit j = element (j, i)).  Each stage swaps the off-diagonal
+// s x s blocks of every 2s x 2s block with the partner lane i ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t r, int lane)
+{
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int s = 16 >> k;
+        const uint32_t m = masks[k];
+        const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, r, s);
+        r = (lane & s) ? ((r & ~m) | ((o & ~m) >> s)) : ((r & m) | ((o & m) << s));
+    }
+    return r;
+}
+
 // K planes from the POM masks; one CTA per block row, 64 partitions (one mask word) at a
 // time.  Shared memory: bits [cap][nw] uint32, prev / next [cap][nw] int16, cap = min(64, K).
 // Outputs: one thread per (partition, 16 consecutive blocks); the nearest set bit left and
@@ -118,9 +135,12 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
             const int x = x0 + tid;
             const uint64_t m = x < xg.gx ? mask[(rbase + x) * W + w] : 0;
             const int wi = (x0 >> 5) + warp;
-            for (int q = 0; q < np; ++q) {
-                const unsigned bal = __ballot_sync(0xFFFFFFFFu, (m >> q) & 1);
-                if (lane == 0) s_bits[q * nw + wi] = bal;
+            // bit lines of 32 blocks: lane q receives partition q's word (and 32 + q's)
+            const uint32_t lo = warp_transpose32(uint32_t(m), lane);
+            if (lane < np) s_bits[lane * nw + wi] = lo;
+            if (np > 32) {                                   // warp-uniform
+                const uint32_t hi = warp_transpose32(uint32_t(m >> 32), lane);
+                if (lane + 32 < np) s_bits[(lane + 32) * nw + wi] = hi;
             }
         }
         __syncthreads();
