@@ -328,3 +328,35 @@ def test_plane_major_tiles_of_large_maps(shape):
         want, _ = oracle.update_tf(pdm, tf)
         assert np.array_equal(got.reshape(want.shape), want)
     eng.close()
+
+
+def random_large_config(seed):
+    """Larger random shapes (sides up to 240 voxels, grids up to 300 K blocks) so that every
+    kernel spans several CTAs and tiles per axis; K up to 64, N up to 65536."""
+    rng = np.random.default_rng(50000 + seed)
+    b = int(rng.choice([1, 2, 3, 4, 4, 4, 5, 8, 16]))
+    a = int(rng.integers(0, min(b, 2) + 1)) if rng.random() < 0.8 else int(rng.integers(0, b + 1))
+    u16 = rng.random() < 0.5
+    N = int(rng.choice([256, 1000, 4096, 65536])) if u16 else int(rng.choice([64, 256]))
+    K = int(rng.integers(1, min(N, 64) + 1))
+    while True:
+        shape = tuple(int(rng.integers(1, 241)) for _ in range(3))
+        if (np.prod([-(-s // b) for s in shape]) <= 300_000
+                and np.prod(shape) <= 8_000_000):
+            break
+    borders = None
+    if K > 1 and rng.random() < 0.3:
+        inner = np.sort(rng.choice(np.arange(1, N), K - 1, replace=False))
+        borders = [0] + [int(v) for v in inner] + [N]
+    return shape, b, a, N, K, (np.uint16 if u16 else np.uint8), borders, rng
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_large_configs(seed):
+    shape, b, a, N, K, dt, borders, rng = random_large_config(seed)
+    vol = rand_volume(rng, shape, N, dt, blob=int(rng.integers(1, 9)))
+    eng, vd, ref = check_build(vol, b, a, N, K, borders)
+    bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
+    tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 3) + T.special_tfs(N, bd)[:4]
+    check_updates(eng, vd, vol, ref, tfs, b, a, borders, exact_every=4)
+    eng.close()
