@@ -124,8 +124,13 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
     const int64_t total = P.unit_prefix[P.n];
     const int64_t per = (total + gridDim.x - 1) / gridDim.x;
     const int64_t u0 = int64_t(blockIdx.x) * per, u1 = min(total, u0 + per);
+    // the item holding unit u0: the last i with unit_prefix[i] <= u0 (binary search)
     int item = 0;
-    while (item < P.n && P.unit_prefix[item + 1] <= u0) ++item;
+    for (int lo = 0, hi = P.n - 1; lo <= hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (P.unit_prefix[mid] <= u0) { item = mid; lo = mid + 1; } else hi = mid - 1;
+    }
+    while (item < P.n && P.unit_prefix[item + 1] <= u0) ++item;   // skip empty items
     int loaded = -1;
     for (int64_t u = u0; u < u1; ++u) {
         while (P.unit_prefix[item + 1] <= u) ++item;
