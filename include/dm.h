@@ -41,7 +41,7 @@ extern "C" {
 typedef int32_t dm_status;
 #define DM_OK 0
 #define DM_ERR_INVALID_ARG 1   /* null / misaligned pointer, bad size or value */
-#define DM_ERR_UNSUPPORTED 2   /* valid but outside what this build handles */
+#define DM_ERR_UNSUPPORTED 2   /* valid but outside what this library version handles */
 #define DM_ERR_CUDA 3          /* a CUDA launch or an earlier asynchronous CUDA error */
 #define DM_ERR_NOT_BOUND 4     /* buffers not bound with dm_bind() */
 
@@ -96,7 +96,7 @@ typedef struct dm_sizes {
 
 /*
  * Validate `cfg` and create a context (host memory only).  Returns DM_ERR_INVALID_ARG for
- * a malformed config and DM_ERR_UNSUPPORTED for limits of this build.  *out is set only
+ * a malformed config and DM_ERR_UNSUPPORTED for limits of this library version.  *out is set only
  * on DM_OK.  Partition borders: §3.1 (integer borders rho_min^p, rho_max^p; uniform split
  * or not, e.g. a separate partition for the minimum intensity).
  */
