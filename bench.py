@@ -942,6 +942,8 @@ def run_reference(args, ws, rank):
     import synth
     import oracle
     oracle.build()
+    if args.workload not in synth.WORKLOADS:      # batch / serving / render / sweep: ct
+        args.workload = "ct"
     w = synth.WORKLOADS[args.workload]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     vol_np = synth.as_numpy(synth.make_volume(args.workload, device=dev))
@@ -967,8 +969,8 @@ def run_reference(args, ws, rank):
                                       f"oracle TF update per step, scaled by "
                                       f"G/G_slab = {s['scale']:.3f}"},
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "note": "the paper's own GLSL implementation needs a graphics stack (unavailable on "
-                   "this box); the reference arm is the plain CPU oracle"}
+           "note": "the paper's own GLSL implementation needs a graphics stack, which is not "
+                   "available here; the reference arm is the plain CPU oracle"}
     print(json.dumps(res))
 
 

@@ -55,3 +55,25 @@ def test_reduce_max_single_rank_is_identity():
 def test_percentile_helper(q, expect):
     import bench
     assert bench.pct([1.0, 2.0, 3.0], q) == expect
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """`bench.py --impl reference` launched by torchrun with two ranks (gloo on CPU): rank 0
+    times the oracle and prints one JSON line, the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr=127.0.0.1", f"--master-port={_free_port()}",
+           os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "tiny",
+           "--gpus", "2", "--steps", "3", "--warmup", "1"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 3
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
