@@ -176,7 +176,7 @@ dm_status dm_mark_built(dm_ctx *ctx, uint64_t hash, int32_t with_minmax, void *s
  * differ in size, voxel type, K and N; each must have been built (dm_build_partitions)
  * with pdm and scratch bound, and a context may appear at most once per call (its scratch
  * holds the item's active set).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an
- * active-set kernel with one CTA per item, then one persistent combine over all items);
+ * active-set kernel with one CTA per item, then one combine over all items);
  * longer batches are split.  tuning may be NULL (defaults).  Asynchronous on `stream`; the
  * launch pair has no host-side dependency on the items, so it can be captured in a CUDA
  * graph.  Errors: DM_ERR_INVALID_ARG (null / repeated context, null buffers),
@@ -190,7 +190,7 @@ typedef struct dm_batch_item {
 } dm_batch_item;
 
 typedef struct dm_batch_tuning {
-    int32_t combine_ctas_per_sm;   /* persistent combine grid: CTAs per SM (0 = default 12) */
+    int32_t combine_ctas_per_sm;   /* combine grid: CTAs per SM (0 = default 24) */
     int32_t reserved[3];
 } dm_batch_tuning;
 

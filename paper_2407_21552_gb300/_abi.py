@@ -212,13 +212,24 @@ def dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, border
         raise DmError(st, "dm_update_tf_noalloc")
 
 
+class PreparedBatch:
+    """The C item array of a batch, marshalled once from (ctx, d_tf_rgba, d_out) triples and
+    reusable by every dm_update_tf_batch call on the same pointers."""
+
+    def __init__(self, items):
+        self.n = len(items)
+        self.arr = (dm_batch_item * max(1, self.n))()
+        for i, (c, tf, out) in enumerate(items):
+            self.arr[i].ctx, self.arr[i].d_tf_rgba, self.arr[i].d_out = c, tf, out
+        self.first_ctx = items[0][0] if self.n else None
+
+
 def dm_update_tf_batch(items, tuning=None, stream=None):
-    """items: sequence of (ctx, d_tf_rgba, d_out) device pointers; tuning: ctas per SM of
-    the persistent combine (None = library default)."""
-    n = len(items)
-    arr = (dm_batch_item * max(1, n))()
-    for i, (c, tf, out) in enumerate(items):
-        arr[i].ctx, arr[i].d_tf_rgba, arr[i].d_out = c, tf, out
+    """items: sequence of (ctx, d_tf_rgba, d_out) device pointers, or a PreparedBatch of
+    them; tuning: ctas per SM of the combine (None = library default)."""
+    if not isinstance(items, PreparedBatch):
+        items = PreparedBatch(items)
+    n, arr = items.n, items.arr
     tp = None
     if tuning is not None:
         t = dm_batch_tuning()
@@ -226,7 +237,7 @@ def dm_update_tf_batch(items, tuning=None, stream=None):
         tp = ctypes.byref(t)
     st = load().dm_update_tf_batch(arr, n, tp, stream)
     if st != DM_OK:
-        detail = load().dm_last_error_string(items[0][0]).decode() if n else ""
+        detail = load().dm_last_error_string(items.first_ctx).decode() if n else ""
         raise DmError(st, "dm_update_tf_batch", detail)
 
 

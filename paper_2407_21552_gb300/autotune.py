@@ -1,7 +1,7 @@
 """Autotuner for the batched update: block size and combine schedule by measurement.
 
 For a batch of volumes it times the batched update (CUDA events on the launching stream,
-L2 flushed before every rep) for each persistent-combine grid size, and picks the block
+L2 flushed before every rep) for each combine grid size, and picks the block
 size: b = 4 (the paper's choice, §3.1) when its best schedule meets the latency target,
 else b = 8, whose maps are 8x smaller but coarser for empty-space skipping.  Every timed
 call goes through libdm; this module only chooses parameters.
@@ -16,7 +16,7 @@ import torch
 
 from . import _abi as A
 
-CTAS_PER_SM = (2, 4, 8, 12, 16)
+CTAS_PER_SM = (4, 8, 12, 16, 24, 32)
 
 
 @dataclass
@@ -42,6 +42,7 @@ def time_batch(items, ctas_per_sm, reps=20, warmup=3, device="cuda"):
     stream = torch.cuda.current_stream(device)
     sp = ctypes.c_void_p(stream.cuda_stream)
     flush = _flusher(device)
+    items = A.PreparedBatch(items) if not isinstance(items, A.PreparedBatch) else items
     for _ in range(warmup):
         A.dm_update_tf_batch(items, ctas_per_sm, sp)
     ts = []

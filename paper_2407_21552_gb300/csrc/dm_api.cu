@@ -154,7 +154,7 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     size_t o = 0;
     x->off_lut = o;   o = align_up(o + size_t(N), 256);
     x->off_cnt = o;   o = align_up(o + size_t(N + 1) * 4, 256);
-    x->off_act = o;   o = align_up(o + size_t(dmk::kMaxPartitions) * 2, 256);
+    x->off_act = o;   o = align_up(o + size_t(dmk::kMaxPartitions + 8) * 2, 256);
     x->off_nact = o;  o = align_up(o + 64, 64);
     x->off_smask = o; o = align_up(o + 64, 256);
     x->off_tf = o;    o = align_up(o + size_t(N) * 16, 256);

@@ -3,7 +3,7 @@
 // Each item is one volume's resident PDMs (§3.1) with its own TF.  Two launches cover up
 // to kMaxBatch items: an active-set kernel with one CTA per item (§3.1 step 1, from the
 // item's partition table built at precompute time; all loads of a batch issued before any
-// is used), then a persistent combine (Eq. 1) over one flattened list of 4 KiB work units
+// is used), then a combine (Eq. 1) over one flattened list of 4 KiB work units
 // of all items, launched with programmatic dependent launch.  The bytes past an item's
 // last whole 16-byte chunk are folded by one warp per item, its lanes over the planes.
 // Per-item descriptors are passed by value as kernel parameters, so the pair needs no
@@ -48,7 +48,13 @@ __device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
                  : "memory");
 }
 
-// §3.1 step 1 for item blockIdx.x: partition lut[i] is active when alpha_i > 0.
+// §3.1 step 1 for item blockIdx.x: partition lut[i] is active when alpha_i > 0.  A warp
+// holds 32 consecutive intensities, so its visible partitions fall in few mask words: it
+// ORs each word over the warp and one lane sets it, with no same-address shared atomics
+// between the lanes.  The list is followed by kPad copies of its first entry, so that the
+// combine can read it in groups of kPad without knowing its length first.
+constexpr int kPad = 4;
+
 __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_constant__ Params P)
 {
     pdl_trigger();
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
     __shared__ uint16_t s_list[kMaxPartitions + 8];
     __shared__ int s_scan[9];
     const Item& it = P.it[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid < kMaxPartitions / 32) s_S[tid] = 0;
     __syncthreads();
     constexpr int kLB = 8;                                    // loads issued before any use
@@ -70,14 +76,20 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
             c[k] = i < it.N ? it.lut[i] : uint8_t(0);
         }
 #pragma unroll
-        for (int k = 0; k < kLB; ++k)
-            if (a[k] > 0.0f) atomicOr(&s_S[c[k] >> 5], 1u << (c[k] & 31));
+        for (int k = 0; k < kLB; ++k) {
+            const bool vis = a[k] > 0.0f;
+            const unsigned w = c[k] >> 5;
+            const unsigned wlo = __reduce_min_sync(0xFFFFFFFFu, vis ? w : 8u);
+            const unsigned whi = __reduce_max_sync(0xFFFFFFFFu, vis ? w : 0u);
+            for (unsigned ww = wlo; ww <= whi; ++ww) {        // usually one word
+                const unsigned m = __reduce_or_sync(0xFFFFFFFFu, (vis && w == ww) ? 1u << (c[k] & 31) : 0u);
+                if (lane == 0 && m) atomicOr(&s_S[ww], m);
+            }
+        }
     }
     __syncthreads();
-    (void)lane;
-    (void)warp;
     const int n = plan_maps(s_S, it.K, it.J, s_list, s_scan);
-    for (int j = tid; j < n; j += kActThreads) it.act[j] = s_list[j];
+    for (int j = tid; j < n + kPad; j += kActThreads) it.act[j] = n ? s_list[j < n ? j : 0] : uint16_t(0);
     if (tid == 0) *it.nact = n;
 }
 
@@ -111,41 +123,39 @@ __device__ __forceinline__ void item_tail(const Item& it, int lane)
 __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constant__ Params P)
 {
     constexpr int kB = 4;                                     // plane loads per group
+    static_assert(kB == kPad, "the list padding covers one load group");
     __shared__ int64_t s_off[kMaxPartitions + kB];
-    __shared__ int s_n;
     extern __shared__ uint4 s_dyn[];                          // [2][kB][kThreads] staging
     uint4 (*s_stage)[kB][kThreads] = reinterpret_cast<uint4 (*)[kB][kThreads]>(s_dyn);
-    pdl_wait();                                               // active sets are visible
     const int tid = threadIdx.x;
-    // bytes past the last whole chunk of each vectorised item: one warp per item
-    for (int i = int(blockIdx.x) * (kThreads / 32) + (tid >> 5); i < P.n;
-         i += int(gridDim.x) * (kThreads / 32))
-        if (P.it[i].vec) item_tail(P.it[i], tid & 31);
+    // this CTA's units and the item holding the first one (the last i with unit_prefix[i]
+    // <= u0, by binary search): kernel parameters only, found while the active sets build
     const int64_t total = P.unit_prefix[P.n];
-    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
-    const int64_t u0 = int64_t(blockIdx.x) * per, u1 = min(total, u0 + per);
-    // the item holding unit u0: the last i with unit_prefix[i] <= u0 (binary search)
+    const int64_t u0 = total * blockIdx.x / gridDim.x;         // balanced: floor or ceil
+    const int64_t u1 = total * (blockIdx.x + 1) / gridDim.x;
     int item = 0;
     for (int lo = 0, hi = P.n - 1; lo <= hi;) {
         const int mid = (lo + hi) >> 1;
         if (P.unit_prefix[mid] <= u0) { item = mid; lo = mid + 1; } else hi = mid - 1;
     }
     while (item < P.n && P.unit_prefix[item + 1] <= u0) ++item;   // skip empty items
-    int loaded = -1;
+    pdl_wait();                                               // active sets are visible
+    // bytes past the last whole chunk of each vectorised item: one warp per item
+    for (int i = int(blockIdx.x) * (kThreads / 32) + (tid >> 5); i < P.n;
+         i += int(gridDim.x) * (kThreads / 32))
+        if (P.it[i].vec) item_tail(P.it[i], tid & 31);
+    int loaded = -1, n = 0;
     for (int64_t u = u0; u < u1; ++u) {
         while (P.unit_prefix[item + 1] <= u) ++item;
         const Item& it = P.it[item];
         if (item != loaded) {                                 // this item's active planes
-            __syncthreads();
-            if (tid == 0) s_n = *it.nact;
-            __syncthreads();
-            const int n = s_n;
+            if (loaded >= 0) __syncthreads();                 // the last item's offsets are read
+            n = *it.nact;                                     // issued with the list loads
             for (int j = tid; j < kMaxPartitions + kB; j += kThreads)
-                s_off[j] = int64_t(it.act[j < n ? j : 0]) * it.plane;
+                s_off[j] = int64_t(it.act[j]) * it.plane;     // only [0, n + kB) is ever used
             __syncthreads();
             loaded = item;
         }
-        const int n = s_n;
         const int64_t lane_unit = (u - P.unit_prefix[item]) * kThreads + tid;
         if (it.vec) {
             const int64_t nvec = it.G >> 4;
@@ -209,9 +219,10 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = P.unit_prefix[n];
-    // many small CTAs (32 KiB of staging each, about 6 resident per SM) over 4 KiB units:
-    // the hardware's CTA scheduling balances items of different cost
-    int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 12);
+    // many small CTAs (32 KiB of staging each, about 6 resident per SM) over 4 KiB units,
+    // by default one unit each on batches of up to 24 units per SM: the hardware's CTA
+    // scheduling balances items of different cost
+    int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 24);
     if (ctas > total) ctas = total;
     const size_t smem = size_t(2) * 4 * kThreads * sizeof(uint4);
     e = ensure_dynamic_smem<k_combine_batch>(int(smem));

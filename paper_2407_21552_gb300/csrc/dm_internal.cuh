@@ -224,8 +224,8 @@ struct BatchDesc {
     int32_t J;                         // index levels (-1: no index)
 };
 
-// Active sets of up to kMaxBatch items (one CTA each), then one persistent combine over
-// all their work units (PDL); `ctas_per_sm` sizes the combine grid (<= 0: 2).
+// Active sets of up to kMaxBatch items (one CTA each), then one combine over
+// all their work units (PDL); `ctas_per_sm` sizes the combine grid (<= 0: 24).
 cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, int num_sms,
                                 cudaStream_t s);
 

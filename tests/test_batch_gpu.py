@@ -24,7 +24,8 @@ def _engines(specs):
         vol = synth.volume_of(sp["kind"], sp["dims"], sp["seed"])
         X, Y, Z = sp["dims"]
         eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if sp["kind"] == "u8" else DM_U16,
-                                      sp.get("b", 4), 1, sp["K"], sp["N"])
+                                      sp.get("b", 4), 1, sp["K"], sp["N"],
+                                      index_mode=sp.get("index", 0))
         eng.build_partitions(vol.cuda())
         out.append((sp, vol, eng))
     torch.cuda.synchronize()
@@ -74,6 +75,35 @@ def test_batch_longer_than_one_launch_and_tuning(per_sm):
                           for i, (_, _, eng) in enumerate(items)], per_sm, _stream())
     for i, (_, _, eng) in enumerate(items):
         assert torch.equal(eng.update_tf(tfs[i]), outs[i]), i
+
+
+@pytest.mark.parametrize("index", [False, True])
+def test_batch_special_tfs_and_shrinking_active_sets(index):
+    """The degenerate TFs in one batch (empty S, one partition, every partition, unions of
+    whole partitions, NaN and -0.0 alpha), three calls in a row on the same items: the first
+    makes every partition active, so the later, shorter active lists sit over longer stale
+    ones in the items' scratch.  Each D' equals the oracle's."""
+    from paper_2407_21552_gb300 import _abi as A, DM_INDEX_RANGES
+    specs = _small_specs(16, 12)
+    for sp in specs:
+        sp["index"] = DM_INDEX_RANGES if index else 0
+    items = _engines(specs)
+    oracle_maps = [oracle.build_partitions(synth.as_numpy(vol), sp.get("b", 4), 1, sp["N"],
+                                           sp["K"])[1] for sp, vol, _ in items]
+    outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in items]
+    for call in range(3):
+        tfs = []
+        for i, (sp, _, _) in enumerate(items):
+            special = T.special_tfs(sp["N"], T.uniform_borders(sp["N"], sp["K"]))
+            tf = T.all_visible_tf(sp["N"]) if call == 0 else special[(i + 5 * call) % len(special)]
+            tfs.append(torch.from_numpy(tf).cuda())
+        A.dm_update_tf_batch([(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr())
+                              for i, (_, _, eng) in enumerate(items)], None, _stream())
+        torch.cuda.synchronize()
+        for i, (sp, _, eng) in enumerate(items):
+            want, _ = oracle.update_tf(oracle_maps[i], tfs[i].cpu().numpy())
+            got = outs[i].cpu().numpy().reshape(want.shape)
+            assert np.array_equal(got, want), (call, i)
 
 
 def test_batch_rejects_repeated_context():
