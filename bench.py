@@ -47,24 +47,29 @@ SPIN_CYCLES = 200_000
 # dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
 # taken on; reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,075,968 B read, 0 B
-    # written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "1cd92e98ef5ffe29", "G": 2097152,
-           "read_per_active_plane": 21075968 / 10, "write": 0.0},
+    # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,074,304 B read (mean of
+    # two launches), 0 B written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
+    "ct": {"source_sha": "9364469084b85666", "G": 2097152,
+           "read_per_active_plane": 21074304 / 10, "write": 0.0},
     # k_update_fused on the large workload itself (G = 29,425,664), an edit with |S| = 31:
-    # 912,317,952 B read, 20,611,712 B written (mean of two launches);
+    # 912,314,368 B read, 20,962,944 B written (mean of two launches);
     # profiles/update_kernel_large.md
-    "large": {"source_sha": "1cd92e98ef5ffe29", "G": 29425664,
-              "read_per_active_plane": 912317952 / 31, "write": 20611712.0},
+    "large": {"source_sha": "9364469084b85666", "G": 29425664,
+              "read_per_active_plane": 912314368 / 31, "write": 20962944.0},
 }
+
+
+def update_kernel_sources(csrc):
+    """The update kernel's file and the header whose device helpers it inlines."""
+    return [os.path.join(csrc, "dm_update.cu"), os.path.join(csrc, "dm_internal.cuh")]
 
 
 def ncu_traffic(workload, G, mean_active):
     """DRAM bytes per update launch from the committed ncu capture, scaled to this grid and
     to the mean number of active planes; None once the kernel source has changed."""
     tr = NCU_TRAFFIC.get(workload)
-    src = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc", "dm_update.cu")
-    if not tr or tr.get("source_sha") != code_sha(src):
+    csrc = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc")
+    if not tr or tr.get("source_sha") != code_sha(*update_kernel_sources(csrc)):
         return None
     return float((tr["read_per_active_plane"] * mean_active + tr["write"]) * G / tr["G"])
 
@@ -112,14 +117,16 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
 
 
-def code_sha(path):
-    """Hash of a source file's code with comments and whitespace removed, so that the
+def code_sha(*paths):
+    """Hash of source files' code with comments and whitespace removed, so that the
     recorded ncu traffic stays tied to the kernel and not to its comments."""
-    text = open(path).read()
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    text = re.sub(r"//[^\n]*", " ", text)
-    text = " ".join(text.split())
-    return hashlib.sha256(text.encode()).hexdigest()[:16]
+    parts = []
+    for path in paths:
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        parts.append(" ".join(text.split()))
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
 
 
 class ClockSampler:

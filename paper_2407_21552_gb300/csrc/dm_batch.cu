@@ -31,15 +31,10 @@ struct Item {
 
 struct Params {
     int n;
+    int64_t q, r;                              // CTA b takes q units, plus one if b < r
     int64_t unit_prefix[kMaxBatch + 1];        // work units before item i (256 lanes each)
     Item it[kMaxBatch];
 };
-
-__device__ __forceinline__ uint4 vmin4(uint4 a, uint4 b)
-{
-    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
-                      __vminu4(a.w, b.w));
-}
 
 __device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
 {
@@ -130,9 +125,9 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
     const int tid = threadIdx.x;
     // this CTA's units and the item holding the first one (the last i with unit_prefix[i]
     // <= u0, by binary search): kernel parameters only, found while the active sets build
-    const int64_t total = P.unit_prefix[P.n];
-    const int64_t u0 = total * blockIdx.x / gridDim.x;         // balanced: floor or ceil
-    const int64_t u1 = total * (blockIdx.x + 1) / gridDim.x;
+    const int64_t cta = blockIdx.x;                           // balanced: q or q + 1 units
+    const int64_t u0 = cta * P.q + min(cta, P.r);
+    const int64_t u1 = u0 + P.q + (cta < P.r ? 1 : 0);
     int item = 0;
     for (int lo = 0, hi = P.n - 1; lo <= hi;) {
         const int mid = (lo + hi) >> 1;
@@ -161,7 +156,8 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
             const int64_t nvec = it.G >> 4;
             if (lane_unit < nvec) {
                 const uint8_t* src = it.pdm + (lane_unit << 4);
-                uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+                ByteMin16 acc;
+                acc.reset();
                 const int nb = (n + kB - 1) / kB;
                 if (nb > 0) {
                     for (int k = 0; k < kB; ++k) cp_async16(&s_stage[0][k][tid], src + s_off[k]);
@@ -174,10 +170,10 @@ __global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constan
                     asm volatile("cp.async.commit_group;" ::: "memory");
                     asm volatile("cp.async.wait_group 1;" ::: "memory");
 #pragma unroll
-                    for (int k = 0; k < kB; ++k) acc = vmin4(acc, s_stage[b & 1][k][tid]);
+                    for (int k = 0; k < kB; ++k) acc.fold(s_stage[b & 1][k][tid]);
                 }
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
-                __stcs(reinterpret_cast<uint4*>(it.out + (lane_unit << 4)), acc);
+                __stcs(reinterpret_cast<uint4*>(it.out + (lane_unit << 4)), acc.value());
             }
         } else if (lane_unit < it.G) {
             unsigned a = 255;
@@ -224,6 +220,8 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
     // scheduling balances items of different cost
     int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 24);
     if (ctas > total) ctas = total;
+    P.q = total / ctas;
+    P.r = total % ctas;
     const size_t smem = size_t(2) * 4 * kThreads * sizeof(uint4);
     e = ensure_dynamic_smem<k_combine_batch>(int(smem));
     if (e != cudaSuccess) return e;

@@ -83,6 +83,41 @@ cudaError_t ensure_dynamic_smem(int bytes)
     return e;
 }
 
+// ---------------------------------------------------------------- byte-wise minimum
+// The PDM combine folds bytes with min.u16x2: every 32-bit word of a running minimum is
+// kept as its even bytes (w & 0x00FF00FF) and its odd bytes (w & 0xFF00FF00) in two
+// registers.  A byte in one half of a 16-bit lane whose other half is zero orders like the
+// byte itself, so one 16x2 min folds two bytes; splitting a loaded word costs two logic
+// operations, and the halves are OR-ed back together once per output word.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+struct ByteMin16 {                                   // running byte minimum of 16 bytes
+    uint32_t e[4], o[4];
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { e[k] = 0x00FF00FFu; o[k] = 0xFF00FF00u; }
+    }
+    __device__ __forceinline__ void fold(const uint4& v)
+    {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e[k] = min_u16x2(e[k], w[k] & 0x00FF00FFu);
+            o[k] = min_u16x2(o[k], w[k] & 0xFF00FF00u);
+        }
+    }
+    __device__ __forceinline__ uint4 value() const
+    {
+        return make_uint4(e[0] | o[0], e[1] | o[1], e[2] | o[2], e[3] | o[3]);
+    }
+};
+
 // ---------------------------------------------------------------- partition-range index
 // Optional sparse index over the K PDMs: plane (k, i) = min of PDM_i .. PDM_{i + 2^k - 1}
 // for k = 0..J (level 0 = the PDMs), J = floor(log2 K).  Level k starts at plane

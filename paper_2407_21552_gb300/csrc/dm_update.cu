@@ -8,9 +8,9 @@
 //
 // §3.1 step 2, Eq. 1: D'(x,y,z) = min over p in S of PDM_p(x,y,z).  A pure streaming
 // kernel: each thread owns 16-byte chunks of the map, reads the same chunk of every active
-// plane (independent 16-byte loads, several in flight) and folds them with __vminu4.  On
-// large maps the chunks are taken in plane-major tiles: a warp reads 4 KiB of one plane
-// per step and keeps 8 accumulators per thread.  The HBM traffic is (|S| + 1) * G bytes,
+// plane (independent 16-byte loads, several in flight) and folds them byte-wise, two bytes
+// per min.u16x2 (ByteMin16).  On large maps the chunks are taken in plane-major tiles: a
+// warp reads 4 KiB of one plane per step and keeps 8 accumulators per thread.  The HBM traffic is (|S| + 1) * G bytes,
 // the algorithmic minimum.  An empty S yields 255.
 #include "dm_internal.cuh"
 
@@ -196,7 +196,8 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
     if (v >= nvec) return;
     issue(v, 0, 0);
     int slot = 0;
-    uint4 acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+    ByteMin16 acc;
+    acc.reset();
     while (true) {
         // next step
         int64_t nv = v;
@@ -206,10 +207,10 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
         if (more) issue(nv, njb, slot ^ 1); else cp_async_commit();
         cp_async_wait1();                                     // step (v, jb) landed
 #pragma unroll
-        for (int k = 0; k < kAsyncBatch; ++k) acc = vmin4(acc, stage[(slot * kAsyncBatch + k) * ld]);
+        for (int k = 0; k < kAsyncBatch; ++k) acc.fold(stage[(slot * kAsyncBatch + k) * ld]);
         if (jb == nb - 1) {
-            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc);
-            acc = make_uint4(~0u, ~0u, ~0u, ~0u);
+            __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc.value());
+            acc.reset();
         }
         if (!more) break;
         v = nv;
@@ -251,9 +252,9 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
             cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
         cp_async_commit();
     };
-    uint4 acc[kPM];
+    ByteMin16 acc[kPM];
 #pragma unroll
-    for (int k = 0; k < kPM; ++k) acc[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (int k = 0; k < kPM; ++k) acc[k].reset();
     int p = 0, slot = 0;
     issue(t, 0, 0);
     while (true) {
@@ -264,12 +265,12 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
         if (more) issue(nt, np, slot ^ 1); else cp_async_commit();
         cp_async_wait1();
 #pragma unroll
-        for (int k = 0; k < kPM; ++k) acc[k] = vmin4(acc[k], stage[(slot * kPM + k) * ld]);
+        for (int k = 0; k < kPM; ++k) acc[k].fold(stage[(slot * kPM + k) * ld]);
         if (p == n - 1) {
 #pragma unroll
             for (int k = 0; k < kPM; ++k) {
-                __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), acc[k]);
-                acc[k] = make_uint4(~0u, ~0u, ~0u, ~0u);
+                __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), acc[k].value());
+                acc[k].reset();
             }
         }
         if (!more) break;

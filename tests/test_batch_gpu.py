@@ -106,6 +106,62 @@ def test_batch_special_tfs_and_shrinking_active_sets(index):
             assert np.array_equal(got, want), (call, i)
 
 
+@pytest.fixture(scope="module")
+def bench_batch():
+    """The benchmark's batch: 64 volumes, sides U[64, 384], b = 4 as tuned, one edit each;
+    the oracle's POM masks of every volume."""
+    from paper_2407_21552_gb300 import DM_U8, DM_U16
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    import __graft_entry__ as g
+    g.build()
+    items = []
+    for sp in synth.batch_specs():
+        vol = synth.volume_of(sp["kind"], sp["dims"], sp["seed"], device="cuda")
+        X, Y, Z = sp["dims"]
+        eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if sp["kind"] == "u8" else DM_U16, 4,
+                                      1, sp["K"], sp["N"], with_minmax=False)
+        eng.build_partitions(vol)
+        eng.release_mask()
+        mask = oracle.pom(synth.as_numpy(vol), 4, 1, sp["N"], sp["K"])[0]
+        del vol
+        tf = T.tf_edit_sequence(sp["seed"], sp["N"], 3)[-1]
+        items.append((sp, eng, mask, tf, torch.from_numpy(tf).cuda(),
+                      torch.empty(eng.G, dtype=torch.uint8, device="cuda")))
+    torch.cuda.synchronize()
+    return items
+
+
+@pytest.mark.parametrize("per_sm", [None, 12])
+def test_batch_at_bench_size_sampled(bench_batch, per_sm):
+    """The benchmark's batch launched as the benchmark launches it (library default: one
+    4 KiB unit per combine CTA) and with two units per CTA.  For every item: S is the
+    oracle's, D' is 0 exactly on the union of the oracle's POMs over S, D' equals the item's
+    own single update, and sampled blocks carry the oracle's exact Chebyshev distance."""
+    from paper_2407_21552_gb300 import _abi as A
+    rng = np.random.default_rng(404)
+    for *_, out in bench_batch:
+        out.fill_(7)
+    A.dm_update_tf_batch([(e.ctx, tfd.data_ptr(), out.data_ptr())
+                          for _, e, _, _, tfd, out in bench_batch], per_sm, _stream())
+    torch.cuda.synchronize()
+    for i, (sp, eng, mask, tf, tfd, out) in enumerate(bench_batch):
+        am = torch.zeros(1, dtype=torch.int64, device="cuda")
+        single = eng.update_tf(tfd, active_mask=am)
+        assert torch.equal(single, out), i
+        S = oracle.active_set(tf, sp["K"])
+        got_S = int(am.cpu().numpy().view(np.uint64)[0])
+        assert [p for p in range(sp["K"]) if (got_S >> p) & 1] == S, i
+        union = oracle.union_plane(mask, S)
+        dprime = out.cpu().numpy().reshape(union.shape)
+        assert np.array_equal(dprime == 0, union == 1), i
+        gz, gy, gx = union.shape
+        pts = np.concatenate([np.array([[0, 0, 0], [gx - 1, gy - 1, gz - 1]]),
+                              np.stack([rng.integers(0, gx, 6), rng.integers(0, gy, 6),
+                                        rng.integers(0, gz, 6)], 1)])
+        for (x, y, z), wv in zip(pts, oracle.dt_at_many(union, pts)):
+            assert dprime[z, y, x] == wv, (i, x, y, z)
+
+
 def test_batch_rejects_repeated_context():
     from paper_2407_21552_gb300 import _abi as A
     items = _engines(_small_specs(2, 11))

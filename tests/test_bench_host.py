@@ -1,0 +1,30 @@
+"""bench.py's host-side bookkeeping of the recorded ncu traffic: the source hash ignores
+comments and whitespace but not code, and a record taken on other kernel code is reported
+as null rather than as a stale figure."""
+import bench
+
+
+def test_code_sha_ignores_comments_and_whitespace_not_code(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("int f(int x) { return x + 1; }  // one\n")
+    b.write_text("/* header */\nint f(int x)\n{\n    return x + 1;   // other words\n}\n")
+    c.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.code_sha(str(a)) == bench.code_sha(str(b))
+    assert bench.code_sha(str(a)) != bench.code_sha(str(c))
+    assert bench.code_sha(str(a), str(c)) != bench.code_sha(str(a))
+
+
+def test_ncu_traffic_scales_the_record_and_drops_stale_ones(monkeypatch):
+    import os
+    csrc = os.path.join(bench.ROOT, "paper_2407_21552_gb300", "csrc")
+    sha = bench.code_sha(*bench.update_kernel_sources(csrc))
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {
+        "cur": {"source_sha": sha, "G": 1000, "read_per_active_plane": 1000.0, "write": 50.0},
+        "old": {"source_sha": "0" * 16, "G": 1000, "read_per_active_plane": 1000.0,
+                "write": 50.0}})
+    # 2000 blocks, 3 active planes: (3 * 1000 + 50) * 2000 / 1000
+    assert bench.ncu_traffic("cur", 2000, 3.0) == 6100.0
+    assert bench.ncu_traffic("old", 2000, 3.0) is None
+    assert bench.ncu_traffic("none", 2000, 3.0) is None
