@@ -47,15 +47,15 @@ SPIN_CYCLES = 200_000
 # dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
 # taken on; reported as null once the source has changed.
 NCU_TRAFFIC = {
-    # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,074,304 B read (mean of
-    # two launches), 0 B written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
-    "ct": {"source_sha": "9364469084b85666", "G": 2097152,
-           "read_per_active_plane": 21074304 / 10, "write": 0.0},
+    # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,074,944 B read (both
+    # launches), 0 B written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
+    "ct": {"source_sha": "cbfa8b66d9d8882c", "G": 2097152,
+           "read_per_active_plane": 21074944 / 10, "write": 0.0},
     # k_update_fused on the large workload itself (G = 29,425,664), an edit with |S| = 31:
-    # 912,314,368 B read, 20,962,944 B written (mean of two launches);
+    # 912,313,600 B read, 21,098,240 B written (mean of two launches);
     # profiles/update_kernel_large.md
-    "large": {"source_sha": "9364469084b85666", "G": 29425664,
-              "read_per_active_plane": 912314368 / 31, "write": 20962944.0},
+    "large": {"source_sha": "cbfa8b66d9d8882c", "G": 29425664,
+              "read_per_active_plane": 912313600 / 31, "write": 21098240.0},
 }
 
 

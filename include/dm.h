@@ -111,7 +111,10 @@ dm_status dm_query_sizes(const dm_ctx *ctx, dm_sizes *out);
  * the full recompute is never used in DM_OCC_MINMAX mode), d_scratch (scratch_bytes,
  * 256-byte aligned).  d_mask is only written and read by dm_build_partitions (the POMs are
  * an intermediate, §5) and may be released afterwards by binding NULL.  Rebinding is
- * allowed between calls.
+ * allowed between calls.  The scratch buffer holds a per-context table (the partition of
+ * every intensity) that dm_build_partitions and dm_mark_built write: binding another pdm
+ * or scratch buffer marks the context unbuilt, and the updates return DM_ERR_NOT_BOUND
+ * until one of those two calls has run on the new buffers.
  */
 dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *d_scratch);
 

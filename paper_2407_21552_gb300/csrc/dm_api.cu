@@ -15,6 +15,7 @@
 struct dm_ctx {
     dm_config cfg;
     dmk::Borders borders;
+    bool uniform_borders;           // borders[p] == floor(p N / K) for every p
     dmk::Geometry geo;
     dm_sizes sizes;
     int W;
@@ -117,6 +118,9 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     for (int p = 0; p <= K; ++p)
         x->borders.v[p] = c.borders ? c.borders[p] : int32_t((int64_t(p) * N) / K);
     for (int p = K + 1; p <= dmk::kMaxPartitions; ++p) x->borders.v[p] = N;
+    x->uniform_borders = true;
+    for (int p = 0; p <= K; ++p)
+        x->uniform_borders &= x->borders.v[p] == int32_t((int64_t(p) * N) / K);
     dmk::Geometry& g = x->geo;
     g.X = c.dims[0];
     g.Y = c.dims[1];
@@ -187,7 +191,9 @@ dm_status dm_bind(dm_ctx* ctx, void* d_mask, void* d_pdm, void* d_minmax, void* 
         (d_minmax && !aligned(d_minmax, 16)) || (d_scratch && !aligned(d_scratch, 256)))
         return fail(ctx, DM_ERR_INVALID_ARG, "dm_bind: misaligned buffer (mask/pdm/minmax need "
                     "16 bytes, scratch 256)");
-    if (d_pdm != ctx->d_pdm) ctx->built = false;
+    // the scratch holds the partition table that dm_build_partitions / dm_mark_built write:
+    // another pdm or scratch buffer needs one of them again
+    if (d_pdm != ctx->d_pdm || d_scratch != ctx->d_scratch) ctx->built = false;
     if (d_minmax != ctx->d_minmax) ctx->minmax_built = false;
     ctx->d_mask = d_mask;
     ctx->d_pdm = d_pdm;
@@ -239,7 +245,8 @@ static dm_status check_update(dm_ctx* ctx, const void* tf, const void* out, cons
     if (!ctx->d_pdm || !ctx->d_scratch)
         return fail(ctx, DM_ERR_NOT_BOUND, "%s: pdm and scratch must be bound", who);
     if (!ctx->built)
-        return fail(ctx, DM_ERR_NOT_BOUND, "%s: dm_build_partitions has not run on the bound pdm", who);
+        return fail(ctx, DM_ERR_NOT_BOUND, "%s: dm_build_partitions (or dm_mark_built) has not "
+                    "run on the bound pdm and scratch", who);
     return DM_OK;
 }
 
@@ -258,7 +265,8 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         }
         cudaError_t e = dmk::launch_update_fused(static_cast<const uint8_t*>(ctx->d_pdm),
                                                  ctx->geo.plane, ctx->geo.G, d_tf, N, K,
-                                                 ctx->J, ctx->borders, act, nact, smask,
+                                                 ctx->J, ctx->borders, ctx->uniform_borders ? 1 : 0,
+                                                 act, nact, smask,
                                                  d_active_mask_out, d_out, ctx->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "update");
         if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)

@@ -235,8 +235,10 @@ cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Border
 
 // Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
 bool update_fused_ok(int N);
+// `uniform`: the borders are the default floor(p N / K), which the kernel computes instead of
+// indexing the parameter array per thread.
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, int J, const Borders& bd, uint16_t* act,
+                                int N, int K, int J, const Borders& bd, int uniform, uint16_t* act,
                                 int32_t* nact, uint64_t* smask, uint64_t* smask_out,
                                 uint8_t* out, int num_sms, cudaStream_t s);
 

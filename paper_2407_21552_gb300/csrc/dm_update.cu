@@ -322,7 +322,7 @@ constexpr int kFusedMaxN = 8192;
 
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
-               const float* __restrict__ tf, int N, int K, int J, Borders bd,
+               const float* __restrict__ tf, int N, int K, int J, Borders bd, int uniform,
                uint16_t* __restrict__ act, int32_t* __restrict__ nact,
                uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
                uint8_t* __restrict__ out, int vec_ok)
@@ -356,7 +356,10 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     // ---- S: partition p active iff a visibility bit in [lo_p, hi_p] is set
     bool on = false;
     if (tid < K) {
-        const int lo = bd.v[tid], hi = bd.v[tid + 1] - 1;
+        // uniform borders are computed: indexing the parameter array by thread serialises
+        // the constant-cache reads of a warp
+        const int lo = uniform ? (tid * N) / K : bd.v[tid];
+        const int hi = (uniform ? ((tid + 1) * N) / K : bd.v[tid + 1]) - 1;
         for (int w = lo >> 5; w <= (hi >> 5) && !on; ++w) {
             uint32_t m = s_vis[w];
             if (w == (lo >> 5)) m &= 0xFFFFFFFFu << (lo & 31);
@@ -456,7 +459,7 @@ cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cu
 bool update_fused_ok(int N) { return N <= kFusedMaxN; }
 
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, int J, const Borders& bd, uint16_t* act,
+                                int N, int K, int J, const Borders& bd, int uniform, uint16_t* act,
                                 int32_t* nact, uint64_t* smask, uint64_t* smask_out,
                                 uint8_t* out, int num_sms, cudaStream_t s)
 {
@@ -470,7 +473,7 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
     const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
     cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
     if (e != cudaSuccess) return e;
-    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, act,
+    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform, act,
                                                       nact, smask, smask_out, out, vec_ok);
     return cudaGetLastError();
 }

@@ -7,6 +7,8 @@ tiles and partial tiles in every kernel, b in {1,2,3,4,8}, apron 0..2, K up to 2
 mask words), explicit borders (a separate partition for the minimum intensity, §4.2),
 voxels above the TF domain, lines longer than 255 blocks (clamping), degenerate volumes.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -124,6 +126,39 @@ def test_host_buffer_update_matches(tiny):
     h_out2 = torch.empty(eng.G, dtype=torch.uint8)
     eng.update_tf_host(torch.from_numpy(tf.copy()), h_out2)
     assert np.array_equal(h_out2.numpy().reshape(want.shape), want)
+
+
+def test_new_scratch_needs_mark_built(tiny):
+    """The scratch buffer carries a per-context table (the partition of every intensity):
+    after binding a fresh scratch buffer the updates refuse to run until dm_mark_built has
+    rewritten it, and then give the oracle's D' again, single and batched (explicit, uneven
+    borders: the kernels' non-uniform path)."""
+    from paper_2407_21552_gb300 import _abi as A
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    w = tiny["w"]
+    X, Y, Z = w["dims"]
+    borders = [0, 7, 40, 41, 100, 130, 200, 255, 256]          # explicit, uneven, K = 8
+    eng = PartitionedDistanceMaps((X, Y, Z), A.DM_U8, w["block"], w["apron"], 8, w["N"],
+                                  borders=borders)
+    eng.build_partitions(tiny["vd"])
+    tf = T.tf_edit_sequence(31, w["N"], 1)[0]
+    tfd = torch.from_numpy(tf).cuda()
+    _, pdm_o, _, _ = oracle.build_partitions(tiny["vol"], w["block"], w["apron"], w["N"], 8,
+                                             np.array(borders, dtype=np.int32))
+    want, _ = oracle.update_tf(pdm_o, tf, np.array(borders, dtype=np.int32))
+    assert np.array_equal(eng.update_tf(tfd).cpu().numpy().reshape(want.shape), want)
+    eng._scratch = torch.full_like(eng._scratch, 0xAB)            # tables not written here
+    eng._bind()
+    with pytest.raises(A.DmError):
+        eng.update_tf(tfd)
+    A.dm_mark_built(eng.ctx, A.dm_config_hash(eng.ctx), True,
+                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert np.array_equal(eng.update_tf(tfd).cpu().numpy().reshape(want.shape), want)
+    out = torch.empty(eng.G, dtype=torch.uint8, device="cuda")
+    A.dm_update_tf_batch([(eng.ctx, tfd.data_ptr(), out.data_ptr())], None,
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert np.array_equal(out.cpu().numpy().reshape(want.shape), want)
+    eng.close()
 
 
 def test_repeated_updates_on_other_stream(tiny):
