@@ -745,7 +745,9 @@ def run_serving(args, ws, rank, local):
     """32 sessions (12-bit volumes with sides U[256, 1024], K in {16, 32, 64}) admitted
     under a 150 GB HBM budget; TF edits arrive as a Poisson process over the sessions at
     200, 1000 and 5000 edits/s.  The partitioned server batches them continuously onto 3
-    streams; the comparison server runs a full recompute per edit in the same loop."""
+    streams; the comparison server runs a full recompute per edit in the same loop.  A last
+    run serves 1000 edits/s under a budget of 40 % of the sessions' bytes, evicting idle
+    sessions to host memory and readmitting them for their next edit."""
     import torch
     import synth
     from paper_2407_21552_gb300 import DM_U16
@@ -800,6 +802,38 @@ def run_serving(args, ws, rank, local):
                 "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
                 "offered_edits_per_s": rate, "batches": sch.stats.batches,
                 "mean_batch": float(np.mean(sch.stats.batch_sizes))}
+    # eviction: a budget of 40 % of the sessions' device bytes; idle sessions' maps move
+    # to pinned host memory and come back (no recompute) for their next edit
+    ev_budget = int(0.4 * sum(sp.device_bytes for sp in specs))
+    rate = 1000
+    ex = DeviceExecutor(slots=3, mode="partitioned", device=dev)
+    sch = Scheduler(ex, ev_budget, slots=3, evict_idle=True)
+    for sp in specs:
+        sch.open_session(sp)
+    n_req = max(50, int(rate * args.serve_seconds))
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    sess = rng.integers(0, n_sess, size=n_req)
+    ev0, re0 = sch.stats.evictions, sch.stats.readmissions
+    t0 = time.perf_counter()
+    k = 0
+    while k < n_req or sch.has_work():
+        now = time.perf_counter() - t0
+        while k < n_req and arrive[k] <= now:
+            sch.submit(int(sess[k]), tfs[k % len(tfs)], t_arrival=t0 + arrive[k])
+            k += 1
+        sch.poll()
+    wall = time.perf_counter() - t0
+    lat = np.array(sch.stats.latencies) * 1e3
+    results[f"partitioned+evict@{rate}"] = {
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
+        "offered_edits_per_s": rate, "batches": sch.stats.batches,
+        "mean_batch": float(np.mean(sch.stats.batch_sizes)),
+        "budget_gb": ev_budget / 1e9,
+        "evictions": sch.stats.evictions - ev0, "readmissions": sch.stats.readmissions - re0,
+        "evictions_at_open": ev0}
+    for e in engines:                             # every session resident again
+        e.reload()
     if rank != 0:
         return
     sides = [e.grid[0] * 4 for e in engines]

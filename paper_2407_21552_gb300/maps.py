@@ -57,14 +57,15 @@ class PartitionedDistanceMaps:
         self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
         self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc) if with_minmax else None
         self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
+        self._host = None                                   # maps while offloaded
         self._bind()
 
     def _bind(self):
         A.dm_bind(self.ctx,
                   self._mask.data_ptr() if self._mask is not None else None,
-                  self._pdm.data_ptr(),
+                  self._pdm.data_ptr() if self._pdm is not None else None,
                   self._minmax.data_ptr() if self._minmax is not None else None,
-                  self._scratch.data_ptr())
+                  self._scratch.data_ptr() if self._scratch is not None else None)
 
     # ------------------------------------------------------------------ the three calls
     def build_partitions(self, volume: torch.Tensor, stream=None):
@@ -147,6 +148,56 @@ class PartitionedDistanceMaps:
             self._minmax[: self.sizes.minmax_bytes].copy_(torch.from_numpy(z["minmax"]))
         torch.cuda.current_stream().synchronize()
         A.dm_mark_built(self.ctx, h, mm, _stream_handle(stream))
+
+    # ------------------------------------------------------------------ eviction
+    def offload(self, stream=None):
+        """Move the built maps (PDM planes, and min/max if kept) to pinned host memory and
+        free their device buffers and the scratch; reload() brings them back without a
+        recompute.  The context stays valid but unbuilt in between (updates refuse to run)."""
+        if self._host is not None:
+            return
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st.wait_stream(torch.cuda.current_stream(self.device))   # the maps' last writer
+        host = {"hash": A.dm_config_hash(self.ctx), "pdm": None, "minmax": None}
+        with torch.cuda.stream(st):
+            host["pdm"] = torch.empty(self.sizes.pdm_bytes, dtype=torch.uint8, pin_memory=True)
+            host["pdm"].copy_(self._pdm[: self.sizes.pdm_bytes], non_blocking=True)
+            if self._minmax is not None:
+                host["minmax"] = torch.empty(self.sizes.minmax_bytes, dtype=torch.uint8,
+                                             pin_memory=True)
+                host["minmax"].copy_(self._minmax[: self.sizes.minmax_bytes], non_blocking=True)
+        st.synchronize()
+        self._host = host
+        self._pdm = None
+        self._minmax = None
+        self._scratch = None
+        self._mask = None
+        A.dm_bind(self.ctx, None, None, None, None)
+
+    def reload(self, stream=None):
+        """Inverse of offload(): device buffers again, the maps copied back, the context
+        marked built (dm_mark_built rewrites the scratch's partition table); waits."""
+        h = self._host
+        if h is None:
+            return
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        s = self.sizes
+        alloc = dict(dtype=torch.uint8, device=self.device)
+        with torch.cuda.stream(st):
+            self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
+            self._pdm[: s.pdm_bytes].copy_(h["pdm"], non_blocking=True)
+            if h["minmax"] is not None:
+                self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc)
+                self._minmax[: s.minmax_bytes].copy_(h["minmax"], non_blocking=True)
+            self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
+        self._bind()
+        A.dm_mark_built(self.ctx, h["hash"], h["minmax"] is not None, _stream_handle(st))
+        st.synchronize()
+        self._host = None
+
+    @property
+    def offloaded(self) -> bool:
+        return self._host is not None
 
     def release_mask(self):
         """The POMs are an intermediate (§5): drop their buffer after the precompute."""

@@ -11,6 +11,12 @@ different sessions overlap on the device.  A request completes when its batch's
 completion event has fired; its latency is arrival to completion.  An edit can be withdrawn
 until it joins a batch; a session still waiting for admission can be withdrawn too.
 
+With eviction enabled, a session that needs room (a new one, or an evicted one that got an
+edit) evicts the least recently used admitted sessions that are idle (no edit pending or
+on the device): their maps move to host memory and their budget is freed.  An evicted
+session stays open; its next edit queues it for readmission, which copies the maps back
+without recomputing them (the PDMs depend on the volume only, §3.1).
+
 The scheduler (`Scheduler`) holds no GPU state and is tested with a fake executor; the
 executor for the GPU (`DeviceExecutor`) does every step through libdm: the host TFs are
 copied to each session's device TF buffer on the slot's stream, then one
@@ -57,20 +63,28 @@ class Stats:
     admitted: list = field(default_factory=list)
     rejected_waits: int = 0
     cancelled: int = 0
+    evictions: int = 0
+    readmissions: int = 0
 
 
 class Scheduler:
     """Admission by budget, per-session FIFO, at most one edit of a session on the device
     at a time, a fixed number of batches in flight.  `executor` provides admit(spec), release(sid),
-    launch(slot, requests) -> handle, done(handle) -> bool, and clock() -> seconds."""
+    launch(slot, requests) -> handle, done(handle) -> bool, and clock() -> seconds; with
+    `evict_idle`, also evict(sid) and readmit(spec)."""
 
-    def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 64):
+    def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 64,
+                 evict_idle: bool = False):
         self.ex = executor
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.max_batch = int(max_batch)
+        self.evict_idle = bool(evict_idle)
         self.used = 0
         self.sessions = {}                     # sid -> spec (admitted)
+        self.evicted = {}                      # sid -> spec (open, maps on the host)
+        self.last_use = {}                     # sid -> launch counter (LRU order)
+        self._uses = 0
         self.waiting = collections.deque()     # specs not admitted yet
         self.pending = collections.OrderedDict()   # sid -> deque of requests
         self.inflight = []                     # batches on the device
@@ -82,10 +96,11 @@ class Scheduler:
 
     # ------------------------------------------------------------------ sessions
     def open_session(self, spec: SessionSpec) -> bool:
-        """Admit now if the budget allows, else queue it; returns whether admitted."""
+        """Admit now if the budget allows (evicting idle sessions when enabled), else queue
+        it; returns whether admitted."""
         if spec.device_bytes > self.budget:
             raise ValueError(f"session {spec.sid} needs more than the whole budget")
-        if not self.waiting and self.used + spec.device_bytes <= self.budget:
+        if not self.waiting and self._room_for(spec.device_bytes):
             self._admit(spec)
             return True
         self.waiting.append(spec)
@@ -93,26 +108,73 @@ class Scheduler:
         return False
 
     def _admit(self, spec):
-        self.ex.admit(spec)
+        if spec.sid in self.evicted:
+            del self.evicted[spec.sid]
+            self.ex.readmit(spec)
+            self.stats.readmissions += 1
+        else:
+            self.ex.admit(spec)
+            self.stats.admitted.append(spec.sid)
         self.sessions[spec.sid] = spec
         self.used += spec.device_bytes
-        self.stats.admitted.append(spec.sid)
+        self.last_use[spec.sid] = self._uses
+
+    def _idle(self, sid) -> bool:
+        return sid not in self.busy and not self.pending.get(sid)
+
+    def _room_for(self, nbytes: int) -> bool:
+        """Whether nbytes fit the budget, after evicting least recently used idle sessions
+        if eviction is enabled (nothing is evicted unless enough can be freed)."""
+        if self.used + nbytes <= self.budget:
+            return True
+        if not self.evict_idle:
+            return False
+        idle = sorted((sid for sid in self.sessions if self._idle(sid)),
+                      key=lambda sid: self.last_use.get(sid, 0))
+        need, victims = self.used + nbytes - self.budget, []
+        for sid in idle:
+            if need <= 0:
+                break
+            victims.append(sid)
+            need -= self.sessions[sid].device_bytes
+        if need > 0:
+            return False
+        for sid in victims:
+            spec = self.sessions.pop(sid)
+            self.ex.evict(sid)
+            self.used -= spec.device_bytes
+            self.evicted[sid] = spec
+            self.stats.evictions += 1
+        return True
+
+    def _admit_waiting(self):
+        while self.waiting and self._room_for(self.waiting[0].device_bytes):
+            self._admit(self.waiting.popleft())
 
     def close_session(self, sid: int):
         """Leave once no edit of the session is pending or in flight; frees its budget."""
         if any(r.session == sid for b in self.inflight for r in b.requests):
             raise RuntimeError("session has edits in flight")
         self.pending.pop(sid, None)
-        spec = self.sessions.pop(sid)
-        self.ex.release(sid)
-        self.used -= spec.device_bytes
-        while self.waiting and self.used + self.waiting[0].device_bytes <= self.budget:
-            self._admit(self.waiting.popleft())
+        self.last_use.pop(sid, None)
+        if sid in self.evicted:                 # maps on the host: nothing on the device
+            self.evicted.pop(sid)
+            self.waiting = collections.deque(sp for sp in self.waiting if sp.sid != sid)
+            self.ex.release(sid)
+        else:
+            spec = self.sessions.pop(sid)
+            self.ex.release(sid)
+            self.used -= spec.device_bytes
+        self._admit_waiting()
 
     # ------------------------------------------------------------------ requests
     def submit(self, sid: int, tf, t_arrival: float | None = None) -> Request:
-        if sid not in self.sessions:
+        """Queue an edit of an admitted session, or of an evicted one (which then waits
+        for readmission)."""
+        if sid not in self.sessions and sid not in self.evicted:
             raise KeyError(f"session {sid} is not admitted")
+        if sid in self.evicted and all(sp.sid != sid for sp in self.waiting):
+            self.waiting.append(self.evicted[sid])
         r = Request(session=sid, tf=tf,
                     t_arrival=self.ex.clock() if t_arrival is None else t_arrival,
                     rid=self._rid)
@@ -143,15 +205,16 @@ class Scheduler:
             r.cancelled = True
         q.clear()
         self.stats.cancelled += n
+        if sid in self.evicted:                 # nothing left to readmit it for
+            self.waiting = collections.deque(sp for sp in self.waiting if sp.sid != sid)
         return n
 
     def withdraw_waiting(self, sid: int) -> bool:
         """Drop a session that is still waiting for admission (it never held budget)."""
         for spec in list(self.waiting):
-            if spec.sid == sid:
+            if spec.sid == sid and sid not in self.evicted:
                 self.waiting.remove(spec)
-                while self.waiting and self.used + self.waiting[0].device_bytes <= self.budget:
-                    self._admit(self.waiting.popleft())
+                self._admit_waiting()
                 return True
         return False
 
@@ -174,10 +237,11 @@ class Scheduler:
             else:
                 still.append(b)
         self.inflight = still
+        self._admit_waiting()                   # room freed by retired batches
         while self.free_slots:
             reqs = []
             for sid, q in self.pending.items():
-                if q and sid not in self.busy:
+                if q and sid not in self.busy and sid in self.sessions:
                     reqs.append(q.popleft())
                     if len(reqs) == self.max_batch:
                         break
@@ -188,6 +252,9 @@ class Scheduler:
             for r in reqs:
                 r.t_submit = t
             self.busy.update(r.session for r in reqs)
+            self._uses += 1
+            for r in reqs:
+                self.last_use[r.session] = self._uses
             b = Batch(slot=slot, requests=reqs)
             b.handle = self.ex.launch(slot, reqs)
             self.inflight.append(b)
@@ -219,6 +286,8 @@ class DeviceExecutor:
         # completed, so the event is free to record again
         self.events = [torch.cuda.Event() for _ in range(slots)]
         self.sessions = {}
+        self.evicted = {}                     # sid -> engine whose maps are on the host
+        self.side = torch.cuda.Stream(device=self.device)   # eviction / readmission copies
         self.results = {}                     # rid -> device D' (kept if keep_results)
         self.keep_results = False
 
@@ -236,6 +305,22 @@ class DeviceExecutor:
 
     def release(self, sid):
         self.sessions.pop(sid, None)
+        self.evicted.pop(sid, None)
+
+    def evict(self, sid):
+        """Maps to pinned host memory, device buffers freed (the scheduler evicts only
+        sessions with nothing pending or on the device)."""
+        s = self.sessions.pop(sid)
+        with self.torch.cuda.stream(self.side):
+            s["engine"].offload(self.side)
+        self.evicted[sid] = s["engine"]
+
+    def readmit(self, spec):
+        """Maps back to the device (no recompute), then the per-slot buffers."""
+        self.evicted.pop(spec.sid, None)
+        with self.torch.cuda.stream(self.side):
+            spec.payload["engine"].reload(self.side)
+        self.admit(spec)
 
     def launch(self, slot, requests):
         from . import _abi as A

@@ -1,7 +1,8 @@
 """Scheduler of the serving loop, on the CPU with a fake executor: HBM-budget admission,
 one edit per session per batch in arrival order, a fixed number of batches in flight,
 latency from arrival to completion, sessions leaving only when idle, and cancelled
-requests (withdrawn before they reach the device) and withdrawn waiting sessions."""
+requests (withdrawn before they reach the device), withdrawn waiting sessions, and the
+eviction of idle sessions (least recently used first) with readmission on their next edit."""
 import pytest
 
 from paper_2407_21552_gb300.serving import Scheduler, SessionSpec
@@ -154,3 +155,102 @@ def test_withdraw_a_waiting_session():
     assert s.withdraw_waiting(1)                       # 2 now fits and is admitted
     assert ex.admitted == [0, 2] and s.used == 10
     assert not s.withdraw_waiting(1)
+
+
+class EvictExec(FakeExec):
+    def __init__(self):
+        super().__init__()
+        self.events = []
+
+    def evict(self, sid):
+        self.events.append(("evict", sid))
+
+    def readmit(self, spec):
+        self.events.append(("readmit", spec.sid))
+
+
+def _finish_all(ex, sch):
+    for h in ex.launched:
+        h["done"] = True
+    sch.poll()
+
+
+def test_eviction_frees_room_from_the_least_recently_used_idle_session():
+    ex = EvictExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=1, evict_idle=True)
+    for sid in (0, 1):
+        assert sch.open_session(SessionSpec(sid, 50))
+    sch.submit(0, "a")                        # session 0 used last
+    sch.poll()
+    _finish_all(ex, sch)
+    # a third session needs room: session 1 (never used) goes, session 0 stays
+    assert sch.open_session(SessionSpec(2, 50))
+    assert ex.events == [("evict", 1)] and sch.used == 100
+    assert set(sch.sessions) == {0, 2} and set(sch.evicted) == {1}
+    assert sch.stats.evictions == 1
+
+
+def test_busy_or_pending_sessions_are_never_evicted():
+    ex = EvictExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=1, evict_idle=True)
+    for sid in (0, 1):
+        sch.open_session(SessionSpec(sid, 50))
+    sch.submit(0, "a")
+    sch.poll()                                # session 0 on the device
+    sch.submit(1, "b")                        # session 1 pending (slot busy)
+    assert not sch.open_session(SessionSpec(2, 50))
+    assert ex.events == [] and [sp.sid for sp in sch.waiting] == [2]
+    _finish_all(ex, sch)                      # 0 idle now; 1's edit launched
+    # session 0 is idle and is evicted for session 2; session 1 is on the device
+    assert ex.events == [("evict", 0)] and 2 in sch.sessions
+    assert ex.admitted == [0, 1, 2]
+
+
+def test_an_edit_of_an_evicted_session_readmits_it_in_order():
+    ex = EvictExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=2, evict_idle=True)
+    sch.open_session(SessionSpec(0, 60))
+    sch.open_session(SessionSpec(1, 60))      # evicts 0
+    assert ex.events == [("evict", 0)]
+    r1 = sch.submit(0, "x")                   # 0 is evicted: queued for readmission
+    r2 = sch.submit(0, "y")
+    assert [sp.sid for sp in sch.waiting] == [0]
+    sch.poll()                                # 1 is idle: evicted, 0 readmitted, x launched
+    assert ex.events == [("evict", 0), ("evict", 1), ("readmit", 0)]
+    assert ex.launched[-1]["reqs"] == [(0, "x")]
+    _finish_all(ex, sch)
+    assert ex.launched[-1]["reqs"] == [(0, "y")]
+    _finish_all(ex, sch)
+    assert r1.t_done is not None and r2.t_done is not None and not sch.has_work()
+    assert sch.stats.readmissions == 1 and sch.used == 60
+    assert ex.admitted == [0, 1]              # readmission is not a new admission
+
+
+def test_no_eviction_unless_enabled_and_closing_an_evicted_session():
+    ex = EvictExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=1)
+    sch.open_session(SessionSpec(0, 60))
+    assert not sch.open_session(SessionSpec(1, 60))
+    assert ex.events == []
+    ex2 = EvictExec()
+    sch2 = Scheduler(ex2, budget_bytes=100, slots=1, evict_idle=True)
+    sch2.open_session(SessionSpec(0, 60))
+    sch2.open_session(SessionSpec(1, 60))     # evicts 0
+    sch2.submit(0, "x")                       # 0 waits for readmission
+    sch2.close_session(0)                     # closing drops the waiting readmission too
+    assert not sch2.waiting and 0 not in sch2.evicted and ex2.released == [0]
+    assert sch2.used == 60
+    with pytest.raises(KeyError):
+        sch2.submit(0, "z")
+
+
+def test_cancelling_an_evicted_sessions_edits_drops_its_readmission():
+    ex = EvictExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=1, evict_idle=True)
+    sch.open_session(SessionSpec(0, 60))
+    sch.open_session(SessionSpec(1, 60))      # evicts 0
+    sch.submit(0, "x")
+    assert sch.cancel_session_edits(0) == 1
+    assert not sch.waiting
+    sch.poll()
+    assert ("readmit", 0) not in ex.events and not sch.has_work()

@@ -1,7 +1,7 @@
 """Serving loop on the GPU: edits from several sessions arrive while earlier batches are
 still running, are batched (one edit per session per batch) on three streams, and every
 result equals the same update computed alone -- for the partitioned server and for the
-full-recompute server."""
+full-recompute server, also when idle sessions are evicted to host memory and readmitted."""
 import numpy as np
 import pytest
 import torch
@@ -53,3 +53,50 @@ def test_each_result_is_the_same_alone_and_in_the_mix(mode):
         tfd = r.tf.cuda()
         alone = eng.update_tf(tfd) if mode == "partitioned" else eng.full_recompute(tfd)
         assert torch.equal(ex.results[r.rid], alone), r.rid
+
+
+@pytest.mark.parametrize("mode", ["partitioned", "full"])
+def test_eviction_and_readmission_keep_every_result(mode):
+    """A budget that holds the largest session but not all of them, with eviction: idle
+    sessions' maps move to host memory and come back for their next edit, many times over;
+    every result still equals the same update computed before the loop, with all maps
+    resident."""
+    from paper_2407_21552_gb300.serving import DeviceExecutor, Scheduler, SessionSpec
+    sess = _sessions(count=6, seed=23)
+    rng = np.random.default_rng(4)
+    plan = []
+    for k in range(60):
+        sid = int(rng.integers(0, len(sess)))
+        tf = torch.from_numpy(T.tf_edit_sequence(300 + k, sess[sid][0]["N"], 1)[0]).pin_memory()
+        eng = sess[sid][1]
+        tfd = tf.cuda()
+        want = eng.update_tf(tfd) if mode == "partitioned" else eng.full_recompute(tfd)
+        plan.append((sid, tf, want.clone()))
+    torch.cuda.synchronize()
+    sizes = [eng.sizes.pdm_bytes + eng.sizes.minmax_bytes for _, eng in sess]
+    ex = DeviceExecutor(slots=3, mode=mode)
+    ex.keep_results = True
+    budget = max(max(sizes), sum(sizes) // 2)            # the largest fits, not all
+    assert budget < sum(sizes)
+    sch = Scheduler(ex, budget_bytes=budget, slots=3, max_batch=4, evict_idle=True)
+    for sid, (sp, eng) in enumerate(sess):
+        sch.open_session(SessionSpec(sid, sizes[sid], dict(engine=eng)))
+    reqs = []
+    for k, (sid, tf, _) in enumerate(plan):
+        reqs.append(sch.submit(sid, tf))
+        if k % 2 == 0:
+            sch.poll()
+    sch.drain()
+    assert len(sch.completed) == len(reqs)
+    assert sch.stats.evictions > 0 and sch.stats.readmissions > 0
+    assert sch.used <= sch.budget
+    for r, (sid, _, want) in zip(reqs, plan):
+        assert torch.equal(ex.results[r.rid], want), r.rid
+    # an evicted engine holds no device maps and refuses updates until reloaded
+    off = [eng for _, eng in sess if eng.offloaded]
+    assert off
+    from paper_2407_21552_gb300 import _abi as A
+    with pytest.raises(A.DmError):
+        off[0].update_tf(torch.zeros((off[0].N, 4), device="cuda"))
+    off[0].reload()
+    assert not off[0].offloaded
