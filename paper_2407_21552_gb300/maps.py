@@ -55,9 +55,13 @@ class PartitionedDistanceMaps:
         alloc = dict(dtype=torch.uint8, device=self.device)
         self._mask = torch.empty(max(16, s.mask_bytes), **alloc)
         self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
+        self._with_minmax = bool(with_minmax)
         self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc) if with_minmax else None
         self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
-        self._host = None                                   # maps while offloaded
+        self._host = None                                   # set while offloaded
+        self._host_bufs = None                              # pinned copies, reused
+        self._host_valid = False                            # they hold the current maps
+        self.ready_event = None                             # end of an async reload
         self._bind()
 
     def _bind(self):
@@ -71,7 +75,20 @@ class PartitionedDistanceMaps:
     def build_partitions(self, volume: torch.Tensor, stream=None):
         assert volume.is_cuda and volume.is_contiguous()
         assert _dtype_code(volume) == self.cfg.dtype
+        if self._mask is None or self._pdm is None:    # released or offloaded before
+            alloc = dict(dtype=torch.uint8, device=self.device)
+            s = self.sizes
+            if self._mask is None:
+                self._mask = torch.empty(max(16, s.mask_bytes), **alloc)
+            if self._pdm is None:
+                self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
+                self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
+                if self._with_minmax:
+                    self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc)
+                self._host = None
+            self._bind()
         A.dm_build_partitions(self.ctx, volume.data_ptr(), _stream_handle(stream))
+        self._host_valid = False
 
     def update_tf(self, tf: torch.Tensor, out: torch.Tensor | None = None,
                   active_mask: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -148,52 +165,84 @@ class PartitionedDistanceMaps:
             self._minmax[: self.sizes.minmax_bytes].copy_(torch.from_numpy(z["minmax"]))
         torch.cuda.current_stream().synchronize()
         A.dm_mark_built(self.ctx, h, mm, _stream_handle(stream))
+        self._host_valid = False
 
     # ------------------------------------------------------------------ eviction
-    def offload(self, stream=None):
+    def offload(self, stream=None, wait: bool = True):
         """Move the built maps (PDM planes, and min/max if kept) to pinned host memory and
         free their device buffers and the scratch; reload() brings them back without a
-        recompute.  The context stays valid but unbuilt in between (updates refuse to run)."""
+        recompute.  The context stays valid but unbuilt in between (updates refuse to run).
+        The host buffers are kept: the maps depend on the volume only (§3.1), so a later
+        offload copies nothing unless the maps were rebuilt or loaded since.  With
+        wait=False the copy stays queued on `stream`; the device memory is handed back to
+        torch's allocator only once that copy has run."""
         if self._host is not None:
             return
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         st.wait_stream(torch.cuda.current_stream(self.device))   # the maps' last writer
-        host = {"hash": A.dm_config_hash(self.ctx), "pdm": None, "minmax": None}
+        s = self.sizes
+        if self._host_bufs is None:
+            self._host_bufs = {
+                "pdm": torch.empty(s.pdm_bytes, dtype=torch.uint8, pin_memory=True),
+                "minmax": (torch.empty(s.minmax_bytes, dtype=torch.uint8, pin_memory=True)
+                           if self._minmax is not None else None)}
+        hb = self._host_bufs
+        copy = not self._host_valid or (self._minmax is not None and hb["minmax"] is None)
         with torch.cuda.stream(st):
-            host["pdm"] = torch.empty(self.sizes.pdm_bytes, dtype=torch.uint8, pin_memory=True)
-            host["pdm"].copy_(self._pdm[: self.sizes.pdm_bytes], non_blocking=True)
-            if self._minmax is not None:
-                host["minmax"] = torch.empty(self.sizes.minmax_bytes, dtype=torch.uint8,
-                                             pin_memory=True)
-                host["minmax"].copy_(self._minmax[: self.sizes.minmax_bytes], non_blocking=True)
-        st.synchronize()
-        self._host = host
+            if copy:
+                if self._minmax is not None and hb["minmax"] is None:
+                    hb["minmax"] = torch.empty(s.minmax_bytes, dtype=torch.uint8,
+                                               pin_memory=True)
+                hb["pdm"].copy_(self._pdm[: s.pdm_bytes], non_blocking=True)
+                if self._minmax is not None:
+                    hb["minmax"].copy_(self._minmax[: s.minmax_bytes], non_blocking=True)
+            moved = torch.cuda.Event()
+            moved.record(st)
+        self._host_valid = True
+        for t in (self._pdm, self._minmax, self._scratch, self._mask):
+            if t is not None:
+                t.record_stream(st)
+        self._host = {"hash": A.dm_config_hash(self.ctx), "minmax": self._minmax is not None,
+                      "moved": moved}
         self._pdm = None
         self._minmax = None
         self._scratch = None
         self._mask = None
+        self.ready_event = None
         A.dm_bind(self.ctx, None, None, None, None)
+        if wait:
+            moved.synchronize()
 
-    def reload(self, stream=None):
+    def reload(self, stream=None, wait: bool = True):
         """Inverse of offload(): device buffers again, the maps copied back, the context
-        marked built (dm_mark_built rewrites the scratch's partition table); waits."""
+        marked built (dm_mark_built rewrites the scratch's partition table).  With
+        wait=False the work stays queued on `stream` and `ready_event` marks its end: work
+        on another stream that reads the maps must wait for that event first."""
         h = self._host
         if h is None:
             return
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st.wait_event(h["moved"])                               # the offload's copy landed
         s = self.sizes
+        hb = self._host_bufs
         alloc = dict(dtype=torch.uint8, device=self.device)
         with torch.cuda.stream(st):
             self._pdm = torch.empty(max(16, s.pdm_bytes), **alloc)
-            self._pdm[: s.pdm_bytes].copy_(h["pdm"], non_blocking=True)
-            if h["minmax"] is not None:
+            self._pdm[: s.pdm_bytes].copy_(hb["pdm"], non_blocking=True)
+            if h["minmax"]:
                 self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc)
-                self._minmax[: s.minmax_bytes].copy_(h["minmax"], non_blocking=True)
+                self._minmax[: s.minmax_bytes].copy_(hb["minmax"], non_blocking=True)
             self._scratch = torch.empty(max(256, s.scratch_bytes), **alloc)
         self._bind()
-        A.dm_mark_built(self.ctx, h["hash"], h["minmax"] is not None, _stream_handle(st))
-        st.synchronize()
+        A.dm_mark_built(self.ctx, h["hash"], h["minmax"], _stream_handle(st))
+        ready = torch.cuda.Event()
+        ready.record(st)
         self._host = None
+        if wait:
+            ready.synchronize()
+            self.ready_event = None
+        else:
+            self.ready_event = ready
 
     @property
     def offloaded(self) -> bool:

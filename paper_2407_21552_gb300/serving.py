@@ -308,18 +308,18 @@ class DeviceExecutor:
         self.evicted.pop(sid, None)
 
     def evict(self, sid):
-        """Maps to pinned host memory, device buffers freed (the scheduler evicts only
-        sessions with nothing pending or on the device)."""
+        """Maps to pinned host memory, device buffers freed once the copy has run (the
+        scheduler evicts only sessions with nothing pending or on the device).  The copy is
+        queued on the side stream; the host does not wait for it."""
         s = self.sessions.pop(sid)
-        with self.torch.cuda.stream(self.side):
-            s["engine"].offload(self.side)
+        s["engine"].offload(self.side, wait=False)
         self.evicted[sid] = s["engine"]
 
     def readmit(self, spec):
-        """Maps back to the device (no recompute), then the per-slot buffers."""
+        """Maps back to the device (no recompute), queued on the side stream; the session's
+        next batch waits for that copy on the device, not on the host."""
         self.evicted.pop(spec.sid, None)
-        with self.torch.cuda.stream(self.side):
-            spec.payload["engine"].reload(self.side)
+        spec.payload["engine"].reload(self.side, wait=False)
         self.admit(spec)
 
     def launch(self, slot, requests):
@@ -330,6 +330,11 @@ class DeviceExecutor:
         with torch.cuda.stream(st):
             for r in requests:
                 s = self.sessions[r.session]
+                eng = s["engine"]
+                if eng.ready_event is not None:       # readmitted: its maps are in transit
+                    st.wait_event(eng.ready_event)
+                    if eng.ready_event.query():
+                        eng.ready_event = None
                 s["tf"][slot].copy_(r.tf, non_blocking=True)
                 items.append((s["engine"].ctx, s["tf"][slot].data_ptr(), s["out"][slot].data_ptr()))
             sh = ctypes.c_void_p(st.cuda_stream)

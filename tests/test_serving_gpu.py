@@ -100,3 +100,31 @@ def test_eviction_and_readmission_keep_every_result(mode):
         off[0].update_tf(torch.zeros((off[0].N, 4), device="cuda"))
     off[0].reload()
     assert not off[0].offloaded
+
+
+def test_offload_copies_the_maps_again_after_a_rebuild():
+    """The host copy is reused while the maps are unchanged and refreshed after a rebuild:
+    offload, reload, rebuild from another volume, offload, reload; the update then equals
+    a fresh engine's built from that other volume."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_2407_21552_gb300 import DM_U8
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    dims = (40, 33, 27)
+    v1 = synth.volume_of("u8", dims, 11).cuda()
+    v2 = synth.volume_of("u8", dims, 12).cuda()
+    eng = PartitionedDistanceMaps(dims, DM_U8, 4, 1, 16, 256)
+    ref = PartitionedDistanceMaps(dims, DM_U8, 4, 1, 16, 256)
+    eng.build_partitions(v1)
+    ref.build_partitions(v2)
+    tf = torch.from_numpy(T.tf_edit_sequence(9, 256, 1)[0]).cuda()
+    want1 = eng.update_tf(tf).clone()
+    for _ in range(2):                                   # the second offload copies nothing
+        eng.offload()
+        eng.reload()
+        assert torch.equal(eng.update_tf(tf), want1)
+    eng.build_partitions(v2)
+    eng.offload()
+    eng.reload()
+    assert torch.equal(eng.update_tf(tf), ref.update_tf(tf))
+    assert not torch.equal(want1, ref.update_tf(tf))
