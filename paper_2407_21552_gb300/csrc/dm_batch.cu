@@ -215,7 +215,7 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = P.unit_prefix[n];
-    // many small CTAs (32 KiB of staging each, about 6 resident per SM) over 4 KiB units,
+    // many small CTAs (32 KiB of staging each, about 5 resident per SM) over 4 KiB units,
     // by default one unit each on batches of up to 24 units per SM: the hardware's CTA
     // scheduling balances items of different cost
     int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 24);
