@@ -114,8 +114,9 @@ __device__ __forceinline__ void item_tail(const Item& it, int lane)
     }
 }
 
-// Eq. 1 over every item's work units; CTA b takes a contiguous range of units.
-__global__ void __launch_bounds__(kThreads) k_combine_batch(const __grid_constant__ Params P)
+// Eq. 1 over every item's work units; CTA b takes a contiguous range of units.  At most 40
+// registers a thread, so that 6 CTAs fit an SM next to their 6 x 34 KiB of shared memory.
+__global__ void __launch_bounds__(kThreads, 6) k_combine_batch(const __grid_constant__ Params P)
 {
     constexpr int kB = 4;                                     // plane loads per group
     static_assert(kB == kPad, "the list padding covers one load group");
@@ -215,7 +216,7 @@ cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = P.unit_prefix[n];
-    // many small CTAs (32 KiB of staging each, about 5 resident per SM) over 4 KiB units,
+    // many small CTAs (32 KiB of staging each, 6 resident per SM) over 4 KiB units,
     // by default one unit each on batches of up to 24 units per SM: the hardware's CTA
     // scheduling balances items of different cost
     int64_t ctas = int64_t(num_sms > 0 ? num_sms : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 24);
