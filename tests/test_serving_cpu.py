@@ -254,3 +254,97 @@ def test_cancelling_an_evicted_sessions_edits_drops_its_readmission():
     assert not sch.waiting
     sch.poll()
     assert ("readmit", 0) not in ex.events and not sch.has_work()
+
+
+class CheckingExec(EvictExec):
+    """Fake executor that checks, at every call, what the device side may assume: a
+    session is evicted only when nothing of it is on the device, launched only while
+    resident, and readmitted only after an eviction."""
+
+    def __init__(self):
+        super().__init__()
+        self.resident, self.on_device = set(), set()
+
+    def admit(self, spec):
+        assert spec.sid not in self.resident
+        self.resident.add(spec.sid)
+        super().admit(spec)
+
+    def release(self, sid):
+        assert sid not in self.on_device
+        self.resident.discard(sid)
+        super().release(sid)
+
+    def evict(self, sid):
+        assert sid in self.resident and sid not in self.on_device
+        self.resident.discard(sid)
+        super().evict(sid)
+
+    def readmit(self, spec):
+        assert spec.sid not in self.resident
+        self.resident.add(spec.sid)
+        super().readmit(spec)
+
+    def launch(self, slot, reqs):
+        for r in reqs:
+            assert r.session in self.resident and r.session not in self.on_device
+            self.on_device.add(r.session)
+        return super().launch(slot, reqs)
+
+    def finish(self, h):
+        h["done"] = True
+        for sid, _ in h["reqs"]:
+            self.on_device.discard(sid)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_workload_with_eviction_keeps_invariants(seed):
+    import random
+    rnd = random.Random(seed)
+    ex = CheckingExec()
+    sch = Scheduler(ex, budget_bytes=100, slots=rnd.choice([1, 2, 3]),
+                    max_batch=rnd.choice([1, 3, 64]), evict_idle=True)
+    sizes = {sid: rnd.choice([10, 20, 30, 45]) for sid in range(8)}
+    opened, closed, submitted = set(), set(), {}
+    for step in range(400):
+        op = rnd.random()
+        if op < 0.1 and len(opened) < len(sizes):
+            sid = len(opened)
+            sch.open_session(SessionSpec(sid, sizes[sid]))
+            opened.add(sid)
+        elif op < 0.7 and opened - closed:
+            sid = rnd.choice(sorted(opened - closed))
+            if sid in sch.sessions or sid in sch.evicted:
+                submitted.setdefault(sid, []).append(sch.submit(sid, (sid, step)))
+        elif op < 0.9:
+            for h in ex.launched:
+                if not h["done"] and rnd.random() < 0.6:
+                    ex.finish(h)
+            sch.poll()
+        elif op < 0.95 and submitted:
+            sid = rnd.choice(sorted(submitted))
+            q = [r for r in submitted[sid] if not r.cancelled and not r.t_done]
+            if q:
+                sch.cancel(rnd.choice(q))
+        else:
+            sch.poll()
+        assert sch.used <= sch.budget
+        assert sch.used == sum(sp.device_bytes for sp in sch.sessions.values())
+        assert not (set(sch.sessions) & set(sch.evicted))
+    # drain: the device finishes everything
+    for _ in range(2000):
+        if not sch.has_work():
+            break
+        for h in ex.launched:
+            if not h["done"]:
+                ex.finish(h)
+        sch.poll()
+    assert not sch.has_work()
+    # every edit ran or was cancelled, and each session's edits ran in submission order
+    done = {r.rid for r in sch.completed}
+    for sid, reqs in submitted.items():
+        ran = [r for r in reqs if not r.cancelled]
+        assert all(r.rid in done for r in ran)
+        order = [tf for h in ex.launched for s, tf in h["reqs"] if s == sid]
+        assert order == [r.tf for r in ran]
+    assert sch.stats.evictions > 0 and sch.stats.readmissions > 0
