@@ -3,11 +3,11 @@
 // Each item is one volume's resident PDMs (§3.1) with its own TF.  Two launches cover up
 // to kMaxBatch items: an active-set kernel with one CTA per item (§3.1 step 1, from the
 // item's partition table built at precompute time; all loads of a batch issued before any
-// is used), then a combine (Eq. 1) over one flattened list of 4 KiB work units
-// of all items, launched with programmatic dependent launch.  The bytes past an item's
-// last whole 16-byte chunk are folded by one warp per item, its lanes over the planes.
-// Per-item descriptors are passed by value as kernel parameters, so the pair needs no
-// device-side setup and can be captured in a CUDA graph.
+// is used), then a combine (Eq. 1) over one flattened list of 4 KiB work units of all
+// items, launched with programmatic dependent launch; by default each combine CTA takes
+// one unit.  The bytes past an item's last whole 16-byte chunk are folded by one warp per
+// item, its lanes over the planes.  Per-item descriptors are passed by value as kernel
+// parameters, so the pair needs no device-side setup and can be captured in a CUDA graph.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -77,14 +77,16 @@ __global__ void __launch_bounds__(kActThreads) k_active_batch(const __grid_const
             const unsigned wlo = __reduce_min_sync(0xFFFFFFFFu, vis ? w : 8u);
             const unsigned whi = __reduce_max_sync(0xFFFFFFFFu, vis ? w : 0u);
             for (unsigned ww = wlo; ww <= whi; ++ww) {        // usually one word
-                const unsigned m = __reduce_or_sync(0xFFFFFFFFu, (vis && w == ww) ? 1u << (c[k] & 31) : 0u);
+                const unsigned bit = (vis && w == ww) ? 1u << (c[k] & 31) : 0u;
+                const unsigned m = __reduce_or_sync(0xFFFFFFFFu, bit);
                 if (lane == 0 && m) atomicOr(&s_S[ww], m);
             }
         }
     }
     __syncthreads();
     const int n = plan_maps(s_S, it.K, it.J, s_list, s_scan);
-    for (int j = tid; j < n + kPad; j += kActThreads) it.act[j] = n ? s_list[j < n ? j : 0] : uint16_t(0);
+    for (int j = tid; j < n + kPad; j += kActThreads)
+        it.act[j] = n ? s_list[j < n ? j : 0] : uint16_t(0);
     if (tid == 0) *it.nact = n;
 }
 
