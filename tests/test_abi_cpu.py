@@ -185,3 +185,37 @@ def test_config_hash_tracks_everything_that_shapes_the_maps():
         assert lib.dm_mark_built(ctx, hashes[0], 0, None) == A.DM_ERR_NOT_BOUND
     finally:
         A.dm_destroy(ctx)
+
+
+def test_batched_update_is_refused_on_the_host_for_bad_items():
+    """dm_update_tf_batch checks every item before it launches: a null context or buffer,
+    an unbuilt context and a context given twice are refused, whether the items come as
+    a list or as a PreparedBatch (marshalled once)."""
+    c, keep = cfg()
+    ctxs = [A.dm_create(c) for _ in range(2)]
+    lib = A.load()
+    fake = (1 << 20)
+    try:
+        for ctx in ctxs:
+            assert lib.dm_bind(ctx, ctypes.c_void_p(fake), ctypes.c_void_p(fake),
+                               ctypes.c_void_p(fake), ctypes.c_void_p(fake)) == A.DM_OK
+        items = [(ctxs[0], fake, fake + 4096), (ctxs[1], fake + 64, fake + 8192)]
+        pb = A.PreparedBatch(items)
+        assert pb.n == 2 and pb.first_ctx == ctxs[0]
+        assert [(pb.arr[i].d_tf_rgba, pb.arr[i].d_out) for i in range(2)] == \
+            [(fake, fake + 4096), (fake + 64, fake + 8192)]
+        for form in (items, pb):                          # bound, never built
+            with pytest.raises(A.DmError) as e:
+                A.dm_update_tf_batch(form, None, None)
+            assert e.value.status == A.DM_ERR_NOT_BOUND
+            assert "not built" in str(e.value)
+        with pytest.raises(A.DmError) as e:               # misaligned TF
+            A.dm_update_tf_batch([(ctxs[0], fake + 2, fake)], None, None)
+        assert e.value.status == A.DM_ERR_INVALID_ARG
+        with pytest.raises(A.DmError) as e:               # null output
+            A.dm_update_tf_batch(A.PreparedBatch([(ctxs[1], fake, None)]), 12, None)
+        assert e.value.status == A.DM_ERR_INVALID_ARG
+        A.dm_update_tf_batch([], None, None)              # nothing to do
+    finally:
+        for ctx in ctxs:
+            A.dm_destroy(ctx)
