@@ -176,14 +176,15 @@ dm_status dm_mark_built(dm_ctx *ctx, uint64_t hash, int32_t with_minmax, void *s
  * Batched per-TF update over several volumes (§3.1 steps 1 and 2 for each item).  Item i
  * updates context items[i].ctx with its device TF (float32 [N_i][4]) into its device
  * output (uint8 [G_i]); results are those of dm_update_tf on each item alone.  Contexts may
- * differ in size, voxel type, K and N; each must have been built (dm_build_partitions)
- * with pdm and scratch bound, and a context may appear at most once per call (its scratch
- * holds the item's active set).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an
+ * differ in size, voxel type, K and N; each must have been built (dm_build_partitions or
+ * dm_mark_built) on its bound pdm and scratch, and a context may appear at most once per
+ * call (its scratch holds the item's active set).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an
  * active-set kernel with one CTA per item, then one combine over all items);
  * longer batches are split.  tuning may be NULL (defaults).  Asynchronous on `stream`; the
  * launch pair has no host-side dependency on the items, so it can be captured in a CUDA
- * graph.  Errors: DM_ERR_INVALID_ARG (null / repeated context, null buffers),
- * DM_ERR_NOT_BOUND (a context not built).
+ * graph.  Errors, all found on the host before anything is enqueued: DM_ERR_INVALID_ARG
+ * (null / repeated context, null buffers, a TF not 4-byte aligned), DM_ERR_NOT_BOUND (a
+ * context not built).
  */
 #define DM_BATCH_MAX_ITEMS 64
 typedef struct dm_batch_item {
