@@ -35,9 +35,11 @@ def build(force: bool = False) -> str:
 
 
 def _load():
+    """The oracle library: this package's build, or the one DM_ORACLE_LIB names (the
+    planted-mistake tests load altered builds of the same source that way)."""
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(os.environ.get("DM_ORACLE_LIB") or build())
         P = ctypes.c_void_p
         i32, i64 = ctypes.c_int32, ctypes.c_int64
         sig = {
