@@ -50,6 +50,18 @@ MUTANTS = [
     ("grid rounds the block count down",
      "static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }",
      "static int64_t cdiv(int64_t a, int64_t b) { return a / b > 0 ? a / b : 1; }"),
+    ("POM sets every partition bit in the first mask word",
+     "mask[blk * W + p / 64] |= (uint64_t)1 << (p % 64);",
+     "mask[blk * W] |= (uint64_t)1 << (p % 64);"),
+    ("exact occupancy counts zero alpha as visible",
+     "if (tf_rgba[4 * i + 3] > 0.0f) o = 1;",
+     "if (tf_rgba[4 * i + 3] >= 0.0f) o = 1;"),
+    ("DT without its backward pass",
+     "int after = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));",
+     "int after = 0;"),
+    ("an empty S combines to 0 instead of 255",
+     "for (int64_t i = 0; i < G; ++i) out[i] = 255;",
+     "for (int64_t i = 0; i < G; ++i) out[i] = 0;"),
 ]
 
 
