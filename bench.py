@@ -1,21 +1,22 @@
 """Benchmark: partitioned-distance-map TF update vs the plain full recompute on one GB300.
 
-A step is one TF edit through the whole per-edit hot path: the partitioned update (active
-set from the TF, then the Eq. 1 combine of the resident PDMs) and, on the same edit, the
-plain full recompute it replaces (min/max occupancy + a fresh distance transform).  The
-one-time precompute (partition table, POMs, K distance transforms) runs once per volume,
-as in the paper (§3.1), and is timed separately.
+The headline workload is the large one (1024x1024x1795 12-bit, 256x256x449 blocks, K = 64,
+1000 TF edits), whose maps stream from HBM.  A step is one session of it, one pass of the
+whole hot path: the one-time precompute of the volume (partition table, POM masks, K
+distance transforms; §3.1), then every TF edit of the workload through the partitioned
+update (active set from the TF, then the Eq. 1 combine of the resident PDMs) and, on the
+same edit, the plain full recompute it replaces (min/max occupancy + a fresh distance
+transform).  `value` is the p50 latency of the timed updates (ms, lower is better).
 
-Rules kept: inputs (volume, PDMs, all TF edits) are resident in HBM before the timed
-region; the L2 is flushed (a 256 MiB write, then a 256 MiB read, so no dirty lines remain)
-before every timed call; kernels are timed
-with CUDA events on the stream they run on; clocks are sampled with nvidia-smi during the
-timed region.  `value` is the p50 latency of the partitioned update (ms, lower is better).
-The default run (ct, 512^3) adds a leg on the large workload (1024x1024x1795), where the
-maps stream from HBM, and the CPU oracle timed on the host cores.  Other workloads:
-tiny, large, mid, batch (64 uneven volumes, one batched launch pair), serving (Poisson TF
-edits over 32 resident sessions), render (empty-space skipping) and sweep (K = 4 .. 64).
-`--impl reference` times the CPU oracle (plain C) on the host cores instead.
+Rules kept: inputs (volume, all TF edits) are resident in HBM before the timed region; the
+L2 is flushed (a 256 MiB write, then a 256 MiB read, so no dirty lines remain) before every
+timed call; kernels are timed with CUDA events on the stream they run on; clocks are
+sampled with nvidia-smi during the timed region.  The line also carries the same edits
+through the optional range index, an end-to-end figure through the host-buffer entry
+point, the CPU oracle timed on the host cores, and the ct workload (512^3) as a sub-leg.
+Other workloads: tiny, ct, mid, batch (64 uneven volumes, one batched launch pair),
+serving (Poisson TF edits over 32 resident sessions), render (empty-space skipping) and
+sweep (K = 4 .. 64).  `--impl reference` times the CPU oracle (plain C) on the host cores.
 """
 from __future__ import annotations
 
@@ -43,17 +44,16 @@ L2_FLUSH_BYTES = 256 << 20
 # slow (the 64-item batch), so that the start event is reached only once the call is queued
 # and the interval holds device time alone.
 SPIN_CYCLES = 200_000
-# DRAM bytes per combine launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by workload, with the hash of the kernel source it was
-# taken on; reported as null once the source has changed.
+# DRAM bytes per update launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by workload, with the hash of the kernel code it was taken
+# on; reported as null once that code has changed.
 NCU_TRAFFIC = {
     # k_update_fused on ct (G = 2,097,152), edits with |S| = 10: 21,074,944 B read (both
-    # launches), 0 B written (D' stays in L2); profiles/update_and_recompute_kernels_ct.md
+    # launches), 0 B written (D' stays in L2)
     "ct": {"source_sha": "cbfa8b66d9d8882c", "G": 2097152,
            "read_per_active_plane": 21074944 / 10, "write": 0.0},
     # k_update_fused on the large workload itself (G = 29,425,664), an edit with |S| = 31:
-    # 912,313,600 B read, 21,098,240 B written (mean of two launches);
-    # profiles/update_kernel_large.md
+    # 912,313,600 B read, 21,098,240 B written (mean of two launches)
     "large": {"source_sha": "cbfa8b66d9d8882c", "G": 29425664,
               "read_per_active_plane": 912313600 / 31, "write": 21098240.0},
 }
@@ -77,13 +77,17 @@ def ncu_traffic(workload, G, mean_active):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5,
+                    help="timed steps; a step is one session of the workload (precompute "
+                         "plus every TF edit)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload",
-                    choices=["ct", "tiny", "large", "mid", "batch", "serving", "render",
+                    choices=["large", "ct", "tiny", "mid", "batch", "serving", "render",
                              "sweep"],
-                    default="ct")
+                    default="large")
+    ap.add_argument("--edits", type=int, default=None,
+                    help="TF edits per step (default: the workload's, 1000 for ct and large)")
     ap.add_argument("--serve-seconds", type=float, default=1.5,
                     help="serving workload: arrival window per rate and server")
     ap.add_argument("--batch-target-us", type=float, default=2000.0,
@@ -91,9 +95,8 @@ def parse():
     ap.add_argument("--cpu-edits", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-large-leg", action="store_true",
-                    help="skip the large-workload roofline leg of the default ct run")
-    ap.add_argument("--large-steps", type=int, default=40)
+    ap.add_argument("--no-ct-leg", action="store_true",
+                    help="skip the ct sub-leg of the default large run")
     return ap.parse_args()
 
 
@@ -227,21 +230,35 @@ def barrier(ws):
 
 
 # ------------------------------------------------------------------------- CPU oracle
-def oracle_sample(vol_np, w, edits, n_edits, n_full=3):
-    """The CPU oracle, as it stands, on a bounded sample of the workload: a z-slab of the
-    volume (whole block-slices, about 1M blocks), its one-time precompute untimed, then
-    `n_edits` TF updates and `n_full` min/max full recomputes timed single-threaded; times
-    scale to the whole volume by G / G_slab (both are linear in G)."""
-    import oracle
-    b, a, N, K = w["block"], w["apron"], w["N"], w["K"]
-    Z, Y, X = vol_np.shape
+def oracle_slab(name, w):
+    """The workload's volume cut to a z-slab of whole block-slices (about 1M blocks), as a
+    host numpy array, with G / G_slab.  The volume is generated on the GPU when there is
+    one (the CPU generator is slow at this size) and only the slab is copied to the host."""
+    import torch
+    import synth
+    b = w["block"]
+    X, Y, Z = w["dims"]
     gx, gy, gz = -(-X // b), -(-Y // b), -(-Z // b)
     slab_bz = max(1, min(gz, (1 << 20) // (gx * gy)))
     zs = min(Z, slab_bz * b)
-    sub = np.ascontiguousarray(vol_np[:zs])
-    G = gx * gy * gz
-    Gs = gx * gy * (-(-zs // b))
-    scale = G / Gs
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    vol = synth.make_volume(name, device=dev)
+    sub = np.ascontiguousarray(synth.as_numpy(vol[:zs]))
+    del vol
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    return sub, (gx * gy * gz) / (gx * gy * (-(-zs // b)))
+
+
+def oracle_sample(name, w, edits, n_edits, n_full=3):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: a z-slab of the
+    volume (whole block-slices, about 1M blocks), its one-time precompute timed once, then
+    `n_edits` TF updates and `n_full` min/max full recomputes timed single-threaded; times
+    scale to the whole volume by G / G_slab (all three are linear in G)."""
+    import oracle
+    b, a, N, K = w["block"], w["apron"], w["N"], w["K"]
+    sub, scale = oracle_slab(name, w)
+    zs, Y, X = sub.shape
     t0 = time.perf_counter()
     _, pdm, vmin, vmax = oracle.build_partitions(sub, b, a, N, K)
     pre_s = time.perf_counter() - t0
@@ -294,26 +311,220 @@ def cpu_baseline_block(s, n_edits):
 
 
 # --------------------------------------------------------------------------- our arm
+def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True, index=True):
+    """One workload measured as sessions.  A step is one pass of the whole hot path over
+    the workload: the one-time precompute of its volume (partition table, POM masks, K
+    distance transforms; §3.1), then every TF edit of the workload (1000 for ct and large)
+    through the partitioned update (step 1 + Eq. 1) and, on the same edit, the plain min/max
+    full recompute it replaces.  The L2 is flushed before every timed call, and every call
+    is timed with CUDA events on its stream.  After the timed steps: the same edits with the
+    optional range index, and end to end through the host-buffer entry point."""
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U8, DM_U16, DM_INDEX_RANGES, dm_set_profile_events
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    w = synth.WORKLOADS[name]
+    X, Y, Z = w["dims"]
+    dtype = DM_U8 if w["dtype"] == "u8" else DM_U16
+    stream = torch.cuda.current_stream(dev)
+    vol = synth.make_volume(name, device=dev)
+    vol_sha = synth.volume_sha256(vol) if vol.numel() <= (1 << 28) else None
+    eng = PartitionedDistanceMaps((X, Y, Z), dtype, w["block"], w["apron"], w["K"], w["N"],
+                                  device=dev)
+    G, V = eng.G, X * Y * Z
+    s_bytes = 1 if w["dtype"] == "u8" else 2
+    E = int(edits or w["edits"])
+    edit_list = synth.tf_edit_sequence(w["seed"], w["N"], E)
+    tfs = torch.from_numpy(np.stack(edit_list)).to(dev)            # [E, N, 4], resident
+    Wm = (w["K"] + 63) // 64
+    am = torch.zeros((E, Wm), dtype=torch.int64, device=dev)
+    out = torch.empty(G, dtype=torch.uint8, device=dev)
+    out_full = torch.empty(G, dtype=torch.uint8, device=dev)
+
+    def step(ev=None):
+        """One session; `ev` = (pre0, pre1, ua, ub, fa, fb) events, or None (warm-up)."""
+        flush()
+        if ev:
+            ev[0].record(stream)
+        eng.build_partitions(vol)
+        if ev:
+            ev[1].record(stream)
+        for e in range(E):
+            flush()
+            if ev:
+                ev[2][e].record(stream)
+            eng.update_tf(tfs[e], out=out, active_mask=am[e])
+            if ev:
+                ev[3][e].record(stream)
+            flush()
+            if ev:
+                ev[4][e].record(stream)
+            eng.full_recompute(tfs[e], out=out_full)
+            if ev:
+                ev[5][e].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    mk = lambda n: [torch.cuda.Event(enable_timing=True) for _ in range(n)]  # noqa: E731
+    evs = [(*mk(2), mk(E), mk(E), mk(E), mk(E)) for _ in range(steps)]
+    for ev in evs:                   # torch creates each CUDA event on its first record
+        for e in ev[:2]:
+            e.record(stream)
+        for lst in ev[2:]:
+            for e in lst:
+                e.record(stream)
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(smi_gpu_id(dev))
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    region0.record(stream)
+    for k in range(steps):
+        step(evs[k])
+    region1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    region_ms = region0.elapsed_time(region1)
+    pre = [ev[0].elapsed_time(ev[1]) for ev in evs]
+    upd = [ev[2][e].elapsed_time(ev[3][e]) for ev in evs for e in range(E)]
+    full = [ev[4][e].elapsed_time(ev[5][e]) for ev in evs for e in range(E)]
+    del evs
+    masks = am.cpu().numpy().view(np.uint64)
+    nact = np.array([sum(bin(int(x)).count("1") for x in row) for row in masks])
+    bytes_upd = np.tile((nact + 1) * G, steps).astype(np.float64)  # per launch, algorithmic
+    upd_a = np.asarray(upd)
+    # the update of an N <= 8192 TF is one kernel (k_update_fused): its events bracket it
+    fused = w["N"] <= 8192
+    achieved = float(bytes_upd.sum() / (upd_a.sum() * 1e-3)) / 1e9 if fused else None
+
+    # ---- the same edits with the optional partition-range index (DM_INDEX_RANGES)
+    idx = None
+    if index:
+        idx_eng = PartitionedDistanceMaps((X, Y, Z), dtype, w["block"], w["apron"], w["K"],
+                                          w["N"], device=dev, with_minmax=False,
+                                          index_mode=DM_INDEX_RANGES)
+        idx_eng.build_partitions(vol)
+        idx_eng.release_mask()
+        for e in range(min(warmup, E)):
+            idx_eng.update_tf(tfs[e], out=out)
+        ia, ib = mk(E), mk(E)
+        torch.cuda.synchronize(dev)
+        for e in range(E):
+            flush()
+            ia[e].record(stream)
+            idx_eng.update_tf(tfs[e], out=out)
+            ib[e].record(stream)
+        torch.cuda.synchronize(dev)
+        upd_idx = [ia[e].elapsed_time(ib[e]) for e in range(E)]
+        idx = {"p50_ms": pct(upd_idx, 50), "p99_ms": pct(upd_idx, 99),
+               "pdm_planes": int(idx_eng.sizes.pdm_planes), "edits": E}
+        idx_eng.close()
+        del idx_eng
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the host-buffer entry point: pinned TF in, D' out to pinned
+    #      host memory, stream sync; host wall clock per call.  The update kernel is timed
+    #      inside the same calls (profile events) and the TF copy alone with events, which
+    #      splits the wall time into its parts.
+    e2e_res = None
+    if e2e:
+        h_tf = torch.empty((E, w["N"], 4), dtype=torch.float32).pin_memory()
+        h_tf.copy_(tfs.cpu())
+        h_out = torch.empty(G, dtype=torch.uint8).pin_memory()
+        views = [h_tf[k] for k in range(E)]          # the per-edit host TFs, made up front
+        for k in range(min(warmup, E)):
+            eng.update_tf_host(views[k], h_out)
+        ka, kb = mk(E), mk(E)
+        for e in ka + kb:
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+        lat = []
+        barrier(ws)
+        for k in range(E):
+            dm_set_profile_events(eng.ctx, ka[k].cuda_event, kb[k].cuda_event)
+            t0 = time.perf_counter()
+            eng.update_tf_host(views[k], h_out)
+            lat.append((time.perf_counter() - t0) * 1e3)
+        dm_set_profile_events(eng.ctx, None, None)
+        barrier(ws)
+        kern = [ka[k].elapsed_time(kb[k]) for k in range(E)]
+        tf_dev = torch.empty((w["N"], 4), dtype=torch.float32, device=dev)
+        ca, cb = mk(50), mk(50)
+        for k in range(50):
+            ca[k].record(stream)
+            tf_dev.copy_(views[k % E], non_blocking=True)
+            cb[k].record(stream)
+        torch.cuda.synchronize(dev)
+        copy_ms = pct([ca[k].elapsed_time(cb[k]) for k in range(50)], 50)
+        p50 = pct(lat, 50)
+        e2e_res = {"value": p50, "unit": "ms", "p99": pct(lat, 99), "edits": E,
+                   "h2d_bytes_per_step": int(V * s_bytes + E * w["N"] * 16),
+                   "d2h_bytes_per_step": int(E * G),
+                   "per_edit": {"h2d_bytes": int(w["N"] * 16), "d2h_bytes": int(G)},
+                   "breakdown_p50_ms": {
+                       "tf_h2d_copy": copy_ms,
+                       "update_kernel_writing_host_memory": pct(kern, 50),
+                       "host_side_rest": p50 - pct(kern, 50) - copy_ms},
+                   "how": "dm_update_tf_host per edit: pinned TF -> device, step 1 + Eq. 1 with "
+                          "D' written into pinned host memory, stream sync; host wall clock "
+                          "per call over the workload's edits.  Per step the volume is also "
+                          "uploaded once (counted in h2d_bytes_per_step)"}
+    eng.close()
+    del eng, vol, tfs, out, out_full
+    torch.cuda.empty_cache()
+    p50u, p99u, p50f, p99f, region_max = reduce_max(
+        [pct(upd, 50), pct(upd, 99), pct(full, 50), pct(full, 99), region_ms], ws)
+    pre_ms = float(np.median(pre))
+    pre_bytes = s_bytes * V + w["K"] * G
+    res = {
+        "workload": workload_name(name, w), "volume_xyz": [X, Y, Z], "grid_G": G,
+        "edits_per_step": E, "volume_sha256": vol_sha, "region_ms": region_max,
+        "update": {"p50_ms": p50u, "p99_ms": p99u, "mean_ms": float(upd_a.mean()),
+                   "calls": len(upd),
+                   "gbs_p50": float(np.median(bytes_upd / (upd_a * 1e-3)) / 1e9),
+                   "voxels_per_s_p50": V / (p50u * 1e-3)},
+        "full_recompute": {"p50_ms": p50f, "p99_ms": p99f, "mean_ms": float(np.mean(full)),
+                           "mode": "min/max occupancy", "voxels_per_s_p50": V / (p50f * 1e-3)},
+        "speedup_vs_full_recompute_p50": p50f / p50u,
+        "active_partitions": {"mean": float(nact.mean()), "min": int(nact.min()),
+                              "max": int(nact.max()), "K": w["K"]},
+        "precompute": {"ms": pre_ms, "min_ms": float(np.min(pre)),
+                       "algorithmic_gb": pre_bytes / 1e9,
+                       "gbs": pre_bytes / (pre_ms * 1e-3) / 1e9,
+                       "frac_of_hbm": pre_bytes / (pre_ms * 1e-3) / 1e9 / peak[0]},
+        "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak[0], "unit": "GB/s",
+                     "frac": achieved / peak[0] if achieved else None,
+                     "traffic": ncu_traffic(name, G, float(nact.mean())),
+                     "peak_source": peak[1],
+                     "algorithmic_bytes_per_launch": float(bytes_upd.mean()),
+                     "mean_launch_us": float(upd_a.mean() * 1e3)},
+        "clocks": clk,
+        "e2e": e2e_res,
+        "gpu_launches": steps * (5 + E * ((1 if fused else 2) + 4)),
+    }
+    if idx:
+        idx["speedup_vs_full_recompute_p50"] = p50f / idx["p50_ms"]
+        idx["note"] = ("optional DM_INDEX_RANGES: same D', two index planes per run of active "
+                       f"partitions; memory {idx['pdm_planes']}/{w['K']} of the plain PDMs")
+        res["update_range_index"] = idx
+    return res, edit_list
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import synth
-    from paper_2407_21552_gb300 import DM_U8, DM_U16, dm_set_profile_events
     from paper_2407_21552_gb300.build import build as build_lib
-    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
 
     build_lib()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     w = synth.WORKLOADS[args.workload]
-    X, Y, Z = w["dims"]
-    vol = synth.make_volume(args.workload, device=dev)
-    vol_sha = synth.volume_sha256(vol) if args.workload != "large" else None
-    eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if w["dtype"] == "u8" else DM_U16,
-                                  w["block"], w["apron"], w["K"], w["N"], device=dev)
-    G = eng.G
-    V = X * Y * Z
-    s_bytes = 1 if w["dtype"] == "u8" else 2
-    stream = torch.cuda.current_stream(dev)
+    peak = measured_peak()
     flush_w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush_r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.int64, device=dev)
 
@@ -323,273 +534,49 @@ def run_ours(args, ws, rank, local):
         flush_w.zero_()
         flush_r.max()
 
-    # ---- one-time precompute, timed on its own (3 runs, median)
-    pre = []
-    for _ in range(3):
-        flush()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        eng.build_partitions(vol)
-        e1.record(stream)
-        e1.synchronize()
-        pre.append(e0.elapsed_time(e1))
-    eng.sync()
-
-    edits = synth.tf_edit_sequence(w["seed"], w["N"], w["edits"])
-    tfs = torch.from_numpy(np.stack(edits)).to(dev)                # [E, N, 4], resident
-    E = tfs.shape[0]
-    Wm = (w["K"] + 63) // 64
-    am = torch.zeros((args.steps, Wm), dtype=torch.int64, device=dev)
-    out = torch.empty(G, dtype=torch.uint8, device=dev)
-    out_full = torch.empty(G, dtype=torch.uint8, device=dev)
-
-    for k in range(args.warmup):
-        tf = tfs[k % E]
-        eng.update_tf(tf, out=out)
-        eng.full_recompute(tf, out=out_full)
-    torch.cuda.synchronize(dev)
-
-    K = args.steps
-    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(K)]  # noqa: E731
-    ua, ub, ca, cb, fa, fb = mk(), mk(), mk(), mk(), mk(), mk()
-    region0 = torch.cuda.Event(enable_timing=True)
-    region1 = torch.cuda.Event(enable_timing=True)
-    for ev in ca + cb:            # torch creates the CUDA event on first record
-        ev.record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = ClockSampler(smi_gpu_id(dev))
-    clocks.start()
-    barrier(ws)
-    torch.cuda.synchronize(dev)
-    region0.record(stream)
-    for k in range(K):
-        tf = tfs[k % E]
-        flush()
-        ua[k].record(stream)
-        eng.update_tf(tf, out=out, active_mask=am[k])
-        ub[k].record(stream)
-        flush()
-        fa[k].record(stream)
-        eng.full_recompute(tf, out=out_full)
-        fb[k].record(stream)
-        # the same update once more with events around the combine kernel alone (kept
-        # out of the timed update above: an event between its two kernels would stop the
-        # combine from launching while the active-set kernel runs)
-        flush()
-        dm_set_profile_events(eng.ctx, ca[k].cuda_event, cb[k].cuda_event)
-        eng.update_tf(tf, out=out)
-        dm_set_profile_events(eng.ctx, None, None)
-    region1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(ws)
-    clk = clocks.stop()
-    region_ms = region0.elapsed_time(region1)
-    upd = [ua[k].elapsed_time(ub[k]) for k in range(K)]
-    comb = [ca[k].elapsed_time(cb[k]) for k in range(K)]
-    full = [fa[k].elapsed_time(fb[k]) for k in range(K)]
-    masks = am.cpu().numpy().view(np.uint64)
-    nact = np.array([sum(bin(int(x)).count("1") for x in row) for row in masks])
-    bytes_comb = (nact + 1) * G                                   # per launch, algorithmic
-    achieved = float(bytes_comb.sum() / (np.sum(comb) * 1e-3)) / 1e9   # GB/s
-    peak, peak_src = measured_peak()
-    traffic = ncu_traffic(args.workload, G, float(nact.mean()))
-
-    # ---- the same edits with the optional partition-range index (DM_INDEX_RANGES): the
-    #      update reads two index planes per run of active partitions
-    from paper_2407_21552_gb300 import DM_INDEX_RANGES
-    idx_eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if w["dtype"] == "u8" else DM_U16,
-                                      w["block"], w["apron"], w["K"], w["N"], device=dev,
-                                      with_minmax=False, index_mode=DM_INDEX_RANGES)
-    idx_eng.build_partitions(vol)
-    idx_eng.release_mask()
-    for k in range(args.warmup):
-        idx_eng.update_tf(tfs[k % E], out=out)
-    torch.cuda.synchronize(dev)
-    ia, ib = mk(), mk()
-    for k in range(K):
-        flush()
-        ia[k].record(stream)
-        idx_eng.update_tf(tfs[k % E], out=out)
-        ib[k].record(stream)
-    torch.cuda.synchronize(dev)
-    upd_idx = [ia[k].elapsed_time(ib[k]) for k in range(K)]
-    idx_planes = int(idx_eng.sizes.pdm_planes)
-    idx_eng.close()
-    del idx_eng
-    torch.cuda.empty_cache()
-
-    # ---- end to end through the host-buffer entry point
-    e2e = None
-    if not args.no_e2e:
-        h_tf = torch.empty((E, w["N"], 4), dtype=torch.float32).pin_memory()
-        h_tf.copy_(tfs.cpu())
-        h_out = torch.empty(G, dtype=torch.uint8).pin_memory()
-        views = [h_tf[k] for k in range(E)]          # the per-edit host TFs, made up front
-        for k in range(min(args.warmup, E)):
-            eng.update_tf_host(views[k], h_out)
-        lat = []
-        barrier(ws)
-        for k in range(K):
-            t0 = time.perf_counter()
-            eng.update_tf_host(views[k % E], h_out)
-            lat.append((time.perf_counter() - t0) * 1e3)
-        barrier(ws)
-        e2e = {"value": pct(lat, 50), "unit": "ms", "p99": pct(lat, 99),
-               "h2d_bytes_per_step": int(w["N"] * 16), "d2h_bytes_per_step": int(G),
-               "how": "dm_update_tf_host: pinned TF -> device, step 1 + Eq. 1, D' -> pinned host, "
-                      "stream sync; host wall clock per call"}
-
-    p50u, p99u, p50f, p99f, p50c, region_max = reduce_max(
-        [pct(upd, 50), pct(upd, 99), pct(full, 50), pct(full, 99), pct(comb, 50), region_ms], ws)
-    if e2e is not None:
-        e2e["value"] = reduce_max([e2e["value"]], ws)[0]
-
+    main, edits = session_leg(dev, args.workload, args.steps, args.warmup, flush, peak, ws,
+                              edits=args.edits, e2e=not args.no_e2e)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(synth.as_numpy(vol), w, edits, args.cpu_edits)
+        s = oracle_sample(args.workload, w, edits, args.cpu_edits)
         cpu = cpu_baseline_block(s, args.cpu_edits)
-
-    large = None
-    grid_xyz = list(eng.grid)
-    if ws == 1 and args.workload == "ct" and not args.no_large_leg:
-        eng.close()
-        del eng, vol, tfs, out, out_full
-        torch.cuda.empty_cache()
-        large = large_leg(dev, flush, args.large_steps, args.warmup, peak)
-
+    sub = None
+    if ws == 1 and args.workload == "large" and not args.no_ct_leg:
+        sub, _ = session_leg(dev, "ct", 1, 1, flush, peak, ws, e2e=not args.no_e2e)
     if rank != 0:
         return
-    # our kernels per step: the update (1, or 2 when N > 8192), the full recompute (4) and
-    # the profiled update
-    upd_launches = 1 if w["N"] <= 8192 else 2
-    launches_per_step = upd_launches + 4 + upd_launches
+    X, Y, Z = w["dims"]
+    K = args.steps
     res = {
-        "metric": METRIC, "value": p50u, "unit": "ms", "n_gpus": ws, "steps": K,
-        "warmup": args.warmup, "ms_per_step": region_max / K, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": workload_name(args.workload, w), "volume_xyz": [X, Y, Z],
-                   "grid_xyz": grid_xyz, "G": G, "edits": E,
+        "metric": METRIC, "value": main["update"]["p50_ms"], "unit": "ms", "n_gpus": ws,
+        "steps": K, "warmup": args.warmup, "ms_per_step": main["region_ms"] / K,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": main["workload"], "volume_xyz": [X, Y, Z],
+                   "grid_G": main["grid_G"], "edits_per_step": main["edits_per_step"],
                    "l2": "flushed before every timed call (256 MiB device write, then a "
                          "256 MiB read)",
-                   "volume_sha256": vol_sha, "parallelism": f"replicas x{ws}"},
-        "step": "one TF edit: partitioned update (active set + combine) and, on the same "
-                "edit, the plain min/max full recompute; then the update once more with "
-                "events around the combine kernel for the roofline; ms_per_step includes "
-                "all three and the three L2 flushes",
-        "update": {"p50_ms": p50u, "p99_ms": p99u, "mean_ms": float(np.mean(upd)),
-                   "gbs_p50": float(np.median((nact + 1) * G / (np.array(upd) * 1e-3)) / 1e9),
-                   "voxels_per_s_p50": V / (p50u * 1e-3)},
-        "full_recompute": {"p50_ms": p50f, "p99_ms": p99f, "mode": "min/max occupancy",
-                           "voxels_per_s_p50": V / (p50f * 1e-3)},
-        "speedup_vs_full_recompute_p50": p50f / p50u,
-        "update_range_index": {"p50_ms": pct(upd_idx, 50), "p99_ms": pct(upd_idx, 99),
-                               "speedup_vs_full_recompute_p50": p50f / pct(upd_idx, 50),
-                               "pdm_planes": idx_planes,
-                               "note": "optional DM_INDEX_RANGES: same D', two index planes "
-                                       "per run of active partitions; memory "
-                                       f"{idx_planes}/{w['K']} of the plain PDMs"},
-        "active_partitions": {"mean": float(nact.mean()), "min": int(nact.min()),
-                              "max": int(nact.max()), "K": w["K"]},
-        "precompute": {"ms": float(np.median(pre)),
-                       "algorithmic_gb": (s_bytes * V + w["K"] * G) / 1e9,
-                       "gbs": (s_bytes * V + w["K"] * G) / (np.median(pre) * 1e-3) / 1e9},
-        "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)" if upd_launches == 1
-                     else "k_combine (Eq. 1)", "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": float(bytes_comb.mean()),
-                     "mean_launch_us": float(np.mean(comb) * 1e3)},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "large_workload": large,
-        "gpu_launches": K * launches_per_step,
-        "clocks": clk,
-        "paper_context": "paper: up to 30x faster DM update (RTX 4090, OpenGL/GLSL, Table 1); "
-                         "not re-run here (no graphics stack)",
+                   "volume_sha256": main["volume_sha256"],
+                   "parallelism": f"replicas x{ws}"},
+        "step": "one session of the workload: the one-time precompute of its volume, then "
+                f"its {main['edits_per_step']} TF edits, each through the partitioned update "
+                "(step 1 + Eq. 1) and the plain min/max full recompute; value = p50 of the "
+                f"{main['update']['calls']} timed updates",
     }
+    for key in ("update", "full_recompute", "speedup_vs_full_recompute_p50",
+                "update_range_index", "active_partitions", "precompute", "roofline"):
+        if key in main:
+            res[key] = main[key]
+    res["cpu_baseline"] = cpu
+    res["e2e"] = main["e2e"]
+    res["ct_workload"] = sub
+    res["gpu_launches"] = main["gpu_launches"]
+    res["clocks"] = main["clocks"]
+    res["paper_context"] = ("paper: up to 30x faster DM update (RTX 4090, OpenGL/GLSL, "
+                            "Table 1; kingsnake 1024x1024x795 at n = 64: 1.23-1.99 ms update, "
+                            "7.28-21.40 ms DM recompute, 913.7 ms init); not re-run here (no "
+                            "graphics stack)")
     print(json.dumps(res))
-
-
-def large_leg(dev, flush, steps, warmup, peak):
-    """The 1024x1024x1795 workload (K = 64, 449 block slices) inside the default run, after
-    the ct engine is freed: here the maps stream from HBM (about 1.3 GB per edit), so the
-    update kernel's roofline fraction is a bandwidth figure rather than a launch-latency
-    one.  Same protocol as the ct leg: L2 flushed before every timed call; the update, the
-    min/max full recompute, and the update again with events around its kernel."""
-    import torch
-    import synth
-    from paper_2407_21552_gb300 import DM_U16, dm_set_profile_events
-    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
-    w = synth.WORKLOADS["large"]
-    X, Y, Z = w["dims"]
-    stream = torch.cuda.current_stream(dev)
-    vol = synth.make_volume("large", device=dev)
-    eng = PartitionedDistanceMaps((X, Y, Z), DM_U16, w["block"], w["apron"], w["K"], w["N"],
-                                  device=dev)
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    flush()
-    p0, p1 = ev(), ev()
-    p0.record(stream)
-    eng.build_partitions(vol)
-    p1.record(stream)
-    torch.cuda.synchronize(dev)
-    pre_ms = p0.elapsed_time(p1)
-    del vol
-    torch.cuda.empty_cache()
-    G = eng.G
-    edits = synth.tf_edit_sequence(w["seed"], w["N"], steps + warmup)
-    tfs = torch.from_numpy(np.stack(edits)).to(dev)
-    out = torch.empty(G, dtype=torch.uint8, device=dev)
-    out_full = torch.empty(G, dtype=torch.uint8, device=dev)
-    am = torch.zeros((steps, (w["K"] + 63) // 64), dtype=torch.int64, device=dev)
-    for k in range(warmup):
-        eng.update_tf(tfs[steps + k], out=out)
-        eng.full_recompute(tfs[steps + k], out=out_full)
-    torch.cuda.synchronize(dev)
-    ua, ub, fa, fb, ca, cb = ([ev() for _ in range(steps)] for _ in range(6))
-    for e in ca + cb:
-        e.record(stream)
-    torch.cuda.synchronize(dev)
-    for k in range(steps):
-        flush()
-        ua[k].record(stream)
-        eng.update_tf(tfs[k], out=out, active_mask=am[k])
-        ub[k].record(stream)
-        flush()
-        fa[k].record(stream)
-        eng.full_recompute(tfs[k], out=out_full)
-        fb[k].record(stream)
-        flush()
-        dm_set_profile_events(eng.ctx, ca[k].cuda_event, cb[k].cuda_event)
-        eng.update_tf(tfs[k], out=out)
-        dm_set_profile_events(eng.ctx, None, None)
-    torch.cuda.synchronize(dev)
-    upd = [ua[k].elapsed_time(ub[k]) for k in range(steps)]
-    full = [fa[k].elapsed_time(fb[k]) for k in range(steps)]
-    comb = [ca[k].elapsed_time(cb[k]) for k in range(steps)]
-    masks = am.cpu().numpy().view(np.uint64)
-    nact = np.array([sum(bin(int(x)).count("1") for x in row) for row in masks])
-    bytes_comb = (nact + 1) * G
-    achieved = float(bytes_comb.sum() / (np.sum(comb) * 1e-3)) / 1e9
-    eng.close()
-    del eng, tfs, out, out_full
-    torch.cuda.empty_cache()
-    return {"workload": workload_name("large", w), "G": G, "edits_timed": steps,
-            "update": {"p50_ms": pct(upd, 50), "p99_ms": pct(upd, 99)},
-            "full_recompute": {"p50_ms": pct(full, 50), "p99_ms": pct(full, 99),
-                               "mode": "min/max occupancy"},
-            "speedup_vs_full_recompute_p50": pct(full, 50) / pct(upd, 50),
-            "active_partitions": {"mean": float(nact.mean()), "min": int(nact.min()),
-                                  "max": int(nact.max()), "K": w["K"]},
-            "precompute_ms": pre_ms,
-            "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": ncu_traffic("large", G, float(nact.mean())),
-                         "algorithmic_bytes_per_launch": float(bytes_comb.mean()),
-                         "mean_launch_us": float(np.mean(comb) * 1e3)},
-            "gpu_launches": steps * 6}
 
 
 # ------------------------------------------------------------ batched instances workload
@@ -984,26 +971,28 @@ def run_render(args, ws, rank, local):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    import torch
     import synth
     import oracle
     oracle.build()
     if args.workload not in synth.WORKLOADS:      # batch / serving / render / sweep: ct
         args.workload = "ct"
     w = synth.WORKLOADS[args.workload]
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    vol_np = synth.as_numpy(synth.make_volume(args.workload, device=dev))
     edits = synth.tf_edit_sequence(w["seed"], w["N"], w["edits"])
-    s = oracle_sample(vol_np, w, edits, 0, 0)
+    sub, scale = oracle_slab(args.workload, w)
+    zs, Y, X = sub.shape
+    pdm = oracle.build_partitions(sub, w["block"], w["apron"], w["N"], w["K"])[1]
+    del sub
+    # the steps walk the workload's edit sequence with an even stride
+    stride = max(1, len(edits) // max(1, args.steps))
     for k in range(args.warmup):
-        oracle.update_tf(s["pdm"], edits[k % len(edits)])
+        oracle.update_tf(pdm, edits[(k * stride + stride // 2) % len(edits)])
     lat = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        oracle.update_tf(s["pdm"], edits[k % len(edits)])
-        lat.append((time.perf_counter() - t0) * 1e3 * s["scale"])
-    X, Y, zs = s["slab"]
+        oracle.update_tf(pdm, edits[(k * stride) % len(edits)])
+        lat.append((time.perf_counter() - t0) * 1e3 * scale)
     v = pct(lat, 50)
+    s = {"scale": scale}
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(lat)),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",

@@ -233,10 +233,14 @@ dm_status dm_set_profile_events(dm_ctx *ctx, void *ev_begin, void *ev_end);
  * are checked on the host before anything is enqueued.
  *
  * The first call on each device looks up the array's device address (with that device
- * current) and caches it; make that first call outside any stream capture.  Every call
- * shares the array and it keeps the last call's contents (each call rewrites all of the
- * array that it reads); calls whose work overlaps on the GPU, e.g. on two unordered
- * streams, race on it.  Asynchronous on `stream`.
+ * current) and caches it; make that first call outside any stream capture.  The cached
+ * address is not valid after cudaDeviceReset() (the array may move when the library's
+ * device code is loaded again): do not call this entry point after resetting a device it
+ * was used on.  Every call shares the array and it keeps the last call's contents (each
+ * call rewrites all of the array that it reads); calls whose work overlaps on the GPU,
+ * e.g. on two unordered streams, race on it.  An error left by earlier CUDA work of the
+ * caller is returned as DM_ERR_CUDA and left in place (not cleared).  Asynchronous on
+ * `stream`.
  */
 #define DM_NOALLOC_MAX_TF_SIZE 16384
 #define DM_NOALLOC_SCRATCH_BYTES 4096

@@ -205,6 +205,9 @@ def dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, border
     `borders` is None (uniform) or a sequence of K+1 ints."""
     keep = None
     if borders is not None:
+        if len(borders) != int(num_partitions) + 1:
+            raise ValueError(f"borders holds {len(borders)} entries; the library reads "
+                             f"num_partitions + 1 = {int(num_partitions) + 1}")
         keep = (ctypes.c_int32 * len(borders))(*[int(v) for v in borders])
     st = load().dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, keep,
                                      tf_size, d_tf_rgba, d_out, stream)

@@ -15,10 +15,12 @@
 // cudaGetSymbolAddress, with that device current, and caches it.
 //
 // All calls share the one array and it keeps the last call's contents.  The active-set
-// kernel writes every word that the combine later reads (each visibility word, the count,
-// the list entries below the count and the bit set), so nothing needs clearing between
-// calls.  Two calls whose work overlaps on the GPU (different streams, no ordering) race
-// on the array.
+// kernel writes every word that the combine later reads (each visibility word, the count
+// and the list entries below the count), so nothing needs clearing between calls.  Two
+// calls whose work overlaps on the GPU (different streams, no ordering) race on the array.
+// The cached address belongs to the device's current context: after cudaDeviceReset the
+// library's module is loaded again and the array may move, so the cache is not valid
+// across a reset.
 #include <mutex>
 
 #include "../../include/dm.h"
@@ -30,7 +32,6 @@ constexpr int kMaxDevices = 64;
 constexpr int kThreads = 1024;
 // layout of the static array
 constexpr size_t kOffCount = 0;                   // int32: number of active partitions
-constexpr size_t kOffMask = 64;                   // 4 x uint64: active bit set
 constexpr size_t kOffAct = 128;                   // uint16[256]: ascending active list
 constexpr size_t kOffVis = 1024;                  // uint32[N/32]: visibility bits
 static_assert(kOffAct + 2 * dmk::kMaxPartitions <= kOffVis, "active list overlaps");
@@ -49,7 +50,6 @@ k_noalloc_active(const float* __restrict__ tf, int N, int K, dmk::Borders bd,
                  unsigned char* scratch)
 {
     __shared__ int s_cnt[8];
-    __shared__ uint32_t s_bits[8];
     uint32_t* vis = reinterpret_cast<uint32_t*>(scratch + kOffVis);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int base = 0; base < N; base += kThreads) {
@@ -71,10 +71,7 @@ k_noalloc_active(const float* __restrict__ tf, int N, int K, dmk::Borders bd,
         }
     }
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
-    if (lane == 0 && warp < 8) {
-        s_cnt[warp] = __popc(bal);
-        s_bits[warp] = bal;
-    }
+    if (lane == 0 && warp < 8) s_cnt[warp] = __popc(bal);
     __syncthreads();
     if (tid < 256) {
         int off = 0;
@@ -85,10 +82,6 @@ k_noalloc_active(const float* __restrict__ tf, int N, int K, dmk::Borders bd,
             int tot = 0;
             for (int w = 0; w < 8; ++w) tot += s_cnt[w];
             *reinterpret_cast<int32_t*>(scratch + kOffCount) = tot;
-        }
-        if (tid < 4) {
-            uint64_t* mask = reinterpret_cast<uint64_t*>(scratch + kOffMask);
-            mask[tid] = uint64_t(s_bits[2 * tid]) | (uint64_t(s_bits[2 * tid + 1]) << 32);
         }
     }
 }
@@ -130,16 +123,26 @@ extern "C" dm_status dm_update_tf_noalloc(const uint8_t* d_pdm, size_t plane_str
     unsigned char* scratch = nullptr;
     dm_status st = scratch_on_current_device(&scratch);
     if (st != DM_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    k_noalloc_active<<<1, kThreads, 0, s>>>(d_tf_rgba, N, K, bd, scratch);
-    if (cudaGetLastError() != cudaSuccess) return DM_ERR_CUDA;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DM_ERR_CUDA;
+    // An error left by earlier work of the caller is reported, not cleared: it stays with
+    // the caller, and only a failure of the launches below is this call's own.
+    if (cudaPeekAtLastError() != cudaSuccess) return DM_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    k_noalloc_active<<<1, kThreads, 0, s>>>(d_tf_rgba, N, K, bd, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return DM_ERR_CUDA;
+    }
     cudaError_t e = dmk::launch_combine(d_pdm, int64_t(plane_stride), num_blocks,
                                         reinterpret_cast<const uint16_t*>(scratch + kOffAct),
                                         reinterpret_cast<const int32_t*>(scratch + kOffCount),
                                         d_out, sms, s);
-    return e == cudaSuccess ? DM_OK : DM_ERR_CUDA;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DM_ERR_CUDA;
+    }
+    return DM_OK;
 }

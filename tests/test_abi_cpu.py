@@ -219,3 +219,12 @@ def test_batched_update_is_refused_on_the_host_for_bad_items():
     finally:
         for ctx in ctxs:
             A.dm_destroy(ctx)
+
+
+def test_noalloc_wrapper_checks_the_border_count():
+    """The C side reads num_partitions + 1 borders: a shorter or longer list is refused by
+    the binding before the call (no GPU needed: nothing reaches the library)."""
+    fake = 1 << 20
+    for borders in ([0, 128, 256], [0, 64, 128, 192, 256, 256]):
+        with pytest.raises(ValueError):
+            A.dm_update_tf_noalloc(fake, 64, 64, 4, borders, 256, fake, fake, None)

@@ -64,16 +64,32 @@ def test_batch_matches_oracle_and_single_updates():
         assert torch.equal(single, outs[i]), i
 
 
+@pytest.fixture(scope="module")
+def long_batch():
+    """71 small items (more than one launch pair holds), their TFs and the oracle's D'."""
+    items = _engines(_small_specs(71, 10))
+    tfs, wants = [], []
+    for i, (sp, vol, _) in enumerate(items):
+        tf = T.tf_edit_sequence(7 + i, sp["N"], 1)[0]
+        pdm_o = oracle.build_partitions(synth.as_numpy(vol), sp.get("b", 4), 1, sp["N"],
+                                        sp["K"])[1]
+        tfs.append(torch.from_numpy(tf).cuda())
+        wants.append(oracle.update_tf(pdm_o, tf)[0].reshape(-1))
+    return items, tfs, wants
+
+
 @pytest.mark.parametrize("per_sm", [1, 2, 8, 12, 24])
-def test_batch_longer_than_one_launch_and_tuning(per_sm):
+def test_batch_longer_than_one_launch_and_tuning(long_batch, per_sm):
+    """A batch split over two launch pairs (> DM_BATCH_MAX_ITEMS) under five combine grid
+    sizes: every item's D' is the oracle's and that of its own single update."""
     from paper_2407_21552_gb300 import _abi as A
-    items = _engines(_small_specs(70, 10))          # > DM_BATCH_MAX_ITEMS: split in two
-    tfs = [torch.from_numpy(T.tf_edit_sequence(7 + i, sp["N"], 1)[0]).cuda()
-           for i, (sp, _, _) in enumerate(items)]
-    outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in items]
+    items, tfs, wants = long_batch
+    outs = [torch.full((eng.G,), 5, dtype=torch.uint8, device="cuda") for _, _, eng in items]
     A.dm_update_tf_batch([(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr())
                           for i, (_, _, eng) in enumerate(items)], per_sm, _stream())
+    torch.cuda.synchronize()
     for i, (_, _, eng) in enumerate(items):
+        assert np.array_equal(outs[i].cpu().numpy(), wants[i]), i
         assert torch.equal(eng.update_tf(tfs[i]), outs[i]), i
 
 

@@ -273,6 +273,19 @@ def test_minmax_occupancy_matches_prefix_count(small_case):
                               scipy_chessboard(occ))
 
 
+def test_minmax_occupancy_interval_is_closed():
+    """Min/max occupancy (Krueger & Westermann blocks, §2) tests the closed range
+    [min, max]: a TF visible at exactly one intensity occupies a block iff that intensity
+    is the block's minimum, its maximum or lies between them."""
+    vmin = np.array([[[3, 5, 0, 9]]], dtype=np.uint16)
+    vmax = np.array([[[7, 5, 0, 12]]], dtype=np.uint16)
+    N = 16
+    for i in range(N):
+        want = ((vmin <= i) & (i <= vmax)).astype(np.uint8)
+        got = oracle.occ_minmax(vmin, vmax, T.single_intensity_tf(N, i))
+        assert np.array_equal(got, want), i
+
+
 def test_exact_occupancy_matches_filters(small_case):
     c = small_case
     for tf in T.tf_edit_sequence(4, c["N"], 4):

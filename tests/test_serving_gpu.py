@@ -1,11 +1,13 @@
 """Serving loop on the GPU: edits from several sessions arrive while earlier batches are
 still running, are batched (one edit per session per batch) on three streams, and every
-result equals the same update computed alone -- for the partitioned server and for the
-full-recompute server, also when idle sessions are evicted to host memory and readmitted."""
+result equals the oracle's map for that edit (Eq. 1 over the oracle's PDMs for the
+partitioned server, the min/max full recompute for the other) and the same update computed
+alone -- also when idle sessions are evicted to host memory and readmitted."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from synth import tfs as T
 
@@ -22,10 +24,21 @@ def _sessions(count=6, seed=21):
         X, Y, Z = sp["dims"]
         eng = PartitionedDistanceMaps((X, Y, Z), DM_U8 if sp["kind"] == "u8" else DM_U16, 4, 1,
                                       sp["K"], sp["N"])
-        eng.build_partitions(synth.volume_of(sp["kind"], sp["dims"], sp["seed"]).cuda())
+        vol = synth.volume_of(sp["kind"], sp["dims"], sp["seed"])
+        eng.build_partitions(vol.cuda())
+        _, pdm_o, vmin_o, vmax_o = oracle.build_partitions(synth.as_numpy(vol), 4, 1, sp["N"],
+                                                           sp["K"])
+        sp = dict(sp, pdm=pdm_o, vmin=vmin_o, vmax=vmax_o)
         out.append((sp, eng))
     torch.cuda.synchronize()
     return out
+
+
+def _oracle_map(sp, tf, mode):
+    """The oracle's result for one edit of a session, flattened like the device map."""
+    if mode == "partitioned":
+        return oracle.update_tf(sp["pdm"], tf)[0].reshape(-1)
+    return oracle.full_recompute_minmax(sp["vmin"], sp["vmax"], tf).reshape(-1)
 
 
 @pytest.mark.parametrize("mode", ["partitioned", "full"])
@@ -49,10 +62,12 @@ def test_each_result_is_the_same_alone_and_in_the_mix(mode):
     assert len(sch.completed) == len(reqs)
     assert max(sch.stats.batch_sizes) > 1 and sch.stats.batches < len(reqs)
     for r in sch.completed:
-        eng = sess[r.session][1]
+        sp, eng = sess[r.session]
         tfd = r.tf.cuda()
         alone = eng.update_tf(tfd) if mode == "partitioned" else eng.full_recompute(tfd)
         assert torch.equal(ex.results[r.rid], alone), r.rid
+        want = _oracle_map(sp, r.tf.numpy(), mode)
+        assert np.array_equal(ex.results[r.rid].cpu().numpy(), want), r.rid
 
 
 @pytest.mark.parametrize("mode", ["partitioned", "full"])
@@ -90,8 +105,10 @@ def test_eviction_and_readmission_keep_every_result(mode):
     assert len(sch.completed) == len(reqs)
     assert sch.stats.evictions > 0 and sch.stats.readmissions > 0
     assert sch.used <= sch.budget
-    for r, (sid, _, want) in zip(reqs, plan):
+    for r, (sid, tf, want) in zip(reqs, plan):
         assert torch.equal(ex.results[r.rid], want), r.rid
+        ref = _oracle_map(sess[sid][0], tf.numpy(), mode)
+        assert np.array_equal(ex.results[r.rid].cpu().numpy(), ref), r.rid
     # an evicted engine holds no device maps and refuses updates until reloaded
     off = [eng for _, eng in sess if eng.offloaded]
     assert off
