@@ -632,11 +632,11 @@ def run_batch(args, ws, rank, local):
     # graph of the batched pair reading fixed TF buffers
     tf_fixed = torch.zeros((n, NMAX, 4), dtype=torch.float32, device=dev)
     fixed_items = [(e.ctx, tf_fixed[i].data_ptr(), outs[i].data_ptr()) for i, e in enumerate(engs)]
-    A.dm_update_tf_batch(fixed_items, tr.ctas_per_sm, sp_)
+    A.dm_update_tf_batch(fixed_items, tr.tuning, sp_)
     torch.cuda.synchronize(dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        A.dm_update_tf_batch(fixed_items, tr.ctas_per_sm,
+        A.dm_update_tf_batch(fixed_items, tr.tuning,
                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     flush_w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush_r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.int64, device=dev)
@@ -647,7 +647,7 @@ def run_batch(args, ws, rank, local):
     for k in range(args.warmup):
         for i, e in enumerate(engs):
             e.update_tf(edits[k % E, i, : specs[i]["N"]], out=outs[i])
-        A.dm_update_tf_batch(items_for(tr.block, k % E), tr.ctas_per_sm, sp_)
+        A.dm_update_tf_batch(items_for(tr.block, k % E), tr.tuning, sp_)
         tf_fixed.copy_(edits[k % E])
         graph.replay()
     torch.cuda.synchronize(dev)
@@ -671,7 +671,7 @@ def run_batch(args, ws, rank, local):
         flush()
         torch.cuda._sleep(SPIN_CYCLES)              # the device is busy while the host issues
         ev[k][2].record(stream)
-        A.dm_update_tf_batch(prepared[kk], tr.ctas_per_sm, sp_)
+        A.dm_update_tf_batch(prepared[kk], tr.tuning, sp_)
         ev[k][3].record(stream)
         flush()
         ev[k][4].record(stream)
@@ -694,6 +694,7 @@ def run_batch(args, ws, rank, local):
     step_bytes = ((nact + 1) * Gs).sum(axis=1)
     bat_gbs = step_bytes / (np.array(bat) * 1e-3) / 1e9
     peak, peak_src = measured_peak()
+    multi = multi_edit_leg(engs, edits, specs, tr, flush, stream, min(8, E), reps=max(5, K))
     if rank != 0:
         return
     res = {
@@ -719,12 +720,74 @@ def run_batch(args, ws, rank, local):
                      "algorithmic_bytes_per_step": float(step_bytes.mean()),
                      "mean_active_partitions": float(nact.mean())},
         "autotune": {"block": tr.block, "combine_ctas_per_sm": tr.ctas_per_sm,
+                     "loads_per_stage": tr.loads_per_stage,
                      "target_us": args.batch_target_us,
-                     "table_us": {f"b{b}_c{c}": v for (b, c), v in tr.table.items()}},
+                     "table_us": {f"b{b}_c{c}_l{kb}": v for (b, c, kb), v in tr.table.items()}},
+        "several_edits_per_volume": multi,
         "gpu_launches": K * (n + 2 + 2),
         "clocks": clk,
     }
     print(json.dumps(res))
+
+
+def multi_edit_leg(engs, edits, specs, tr, flush, stream, n_edits, reps):
+    """Several TF edits per volume in one call: the batch's volumes with `n_edits` edits
+    each through dm_update_tf_batch_ws (a volume's edits share their plane reads), against
+    the same edits as `n_edits` single-edit batched calls.  CUDA events, L2 flushed first."""
+    import ctypes
+    import torch
+    from paper_2407_21552_gb300 import _abi as A
+    dev = edits.device
+    n = len(engs)
+    sp_ = ctypes.c_void_p(stream.cuda_stream)
+    outs = [[torch.empty(e.G, dtype=torch.uint8, device=dev) for e in engs]
+            for _ in range(n_edits)]
+    per_call = [A.PreparedBatch([(e.ctx, edits[k, i].data_ptr(), outs[k][i].data_ptr())
+                                 for i, e in enumerate(engs)]) for k in range(n_edits)]
+    every = A.PreparedBatch([(e.ctx, edits[k, i].data_ptr(), outs[k][i].data_ptr())
+                             for k in range(n_edits) for i, e in enumerate(engs)])
+    nbytes = A.dm_batch_workspace_bytes(every.n)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    # the active sets, for the algorithmic bytes
+    am = torch.zeros((n_edits, n, 4), dtype=torch.int64, device=dev)
+    for k in range(n_edits):
+        for i, e in enumerate(engs):
+            e.update_tf(edits[k, i, : specs[i]["N"]], out=outs[k][i], active_mask=am[k, i])
+    torch.cuda.synchronize(dev)
+    m = am.cpu().numpy().view(np.uint64)
+    Gs = np.array([e.G for e in engs], dtype=np.float64)
+    cnt = lambda row: sum(bin(int(x)).count("1") for x in row)  # noqa: E731
+    sep_bytes = sum((cnt(m[k, i]) + 1) * Gs[i] for k in range(n_edits) for i in range(n))
+    union = [np.bitwise_or.reduce(m[:, i], axis=0) for i in range(n)]
+    ws_bytes = sum((cnt(union[i]) + n_edits) * Gs[i] for i in range(n))
+    t_sep, t_ws = [], []
+    for r in range(reps + 2):
+        flush()
+        torch.cuda._sleep(SPIN_CYCLES)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(n_edits):
+            A.dm_update_tf_batch(per_call[k], tr.tuning, sp_)
+        b.record(stream)
+        flush()
+        torch.cuda._sleep(SPIN_CYCLES)
+        c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.record(stream)
+        A.dm_update_tf_batch_ws(every, tr.tuning, ws.data_ptr(), nbytes, sp_)
+        d.record(stream)
+        torch.cuda.synchronize(dev)
+        if r >= 2:
+            t_sep.append(a.elapsed_time(b))
+            t_ws.append(c.elapsed_time(d))
+    peak, _ = measured_peak()
+    p_ws = pct(t_ws, 50)
+    return {"volumes": n, "edits_per_volume": n_edits,
+            "separate_calls": {"p50_ms": pct(t_sep, 50), "calls": n_edits,
+                               "algorithmic_bytes": sep_bytes},
+            "one_call": {"p50_ms": p_ws, "algorithmic_bytes": ws_bytes,
+                         "gbs": ws_bytes / (p_ws * 1e-3) / 1e9,
+                         "frac": ws_bytes / (p_ws * 1e-3) / 1e9 / peak},
+            "speedup": pct(t_sep, 50) / p_ws}
 
 
 # -------------------------------------------------------------------- serving workload

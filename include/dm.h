@@ -178,15 +178,16 @@ dm_status dm_mark_built(dm_ctx *ctx, uint64_t hash, int32_t with_minmax, void *s
  * output (uint8 [G_i]); results are those of dm_update_tf on each item alone.  Contexts may
  * differ in size, voxel type, K and N; each must have been built (dm_build_partitions or
  * dm_mark_built) on its bound pdm and scratch, and a context may appear at most once per
- * call (its scratch holds the item's active set).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an
- * active-set kernel with one CTA per item, then one combine over all items);
- * longer batches are split.  tuning may be NULL (defaults).  Asynchronous on `stream`; the
- * launch pair has no host-side dependency on the items, so it can be captured in a CUDA
- * graph.  Errors, all found on the host before anything is enqueued: DM_ERR_INVALID_ARG
- * (null / repeated context, null buffers, a TF not 4-byte aligned), DM_ERR_NOT_BOUND (a
- * context not built).
+ * call (its scratch holds the item's active set; dm_update_tf_batch_ws below takes several
+ * TFs per context).  Up to DM_BATCH_MAX_ITEMS items share one launch pair (an active-set
+ * kernel with one CTA per item, then one combine over all items); longer batches are split.
+ * tuning may be NULL (defaults).  Asynchronous on `stream`; the launch pair has no
+ * host-side dependency on the items, so it can be captured in a CUDA graph.  Errors, all
+ * found on the host before anything is enqueued: DM_ERR_INVALID_ARG (null / repeated
+ * context, null buffers, a TF not 4-byte aligned), DM_ERR_NOT_BOUND (a context not built).
  */
 #define DM_BATCH_MAX_ITEMS 64
+#define DM_BATCH_MAX_EDITS_PER_GROUP 8
 typedef struct dm_batch_item {
     dm_ctx *ctx;
     const float *d_tf_rgba;
@@ -195,11 +196,34 @@ typedef struct dm_batch_item {
 
 typedef struct dm_batch_tuning {
     int32_t combine_ctas_per_sm;   /* combine grid: CTAs per SM (0 = default 24) */
-    int32_t reserved[3];
+    int32_t loads_per_stage;       /* plane loads per combine pipeline stage: 4 (0 = default)
+                                      or 8 */
+    int32_t reserved[2];
 } dm_batch_tuning;
 
 dm_status dm_update_tf_batch(const dm_batch_item *items, int32_t n,
                              const dm_batch_tuning *tuning, void *stream);
+
+/*
+ * Batched update in which a context may appear several times: several TF edits of one
+ * volume in one call, next to other volumes (§3.1 steps 1 and 2 for each item; results
+ * are those of dm_update_tf on each item alone).  The items of one context, in their
+ * order, form groups of up to DM_BATCH_MAX_EDITS_PER_GROUP; the combine reads every PDM
+ * plane that one of a group's TFs needs once and folds it into each of those TFs' maps,
+ * so a group's HBM traffic is (|S_1 u ... u S_E| + E) * G bytes instead of
+ * sum_e (|S_e| + 1) * G.  The active sets live in d_workspace, a caller-allocated device
+ * buffer of at least dm_batch_workspace_bytes(n) bytes, 256-byte aligned, which must not
+ * be used by other work while the call's kernels run (no context's scratch is written, so
+ * calls on other streams may share contexts but not a workspace).  Up to
+ * DM_BATCH_MAX_ITEMS groups share a launch pair; more are split.  Outputs must not overlap.
+ * Errors as for dm_update_tf_batch (a repeated context is allowed), plus
+ * DM_ERR_INVALID_ARG for a missing, misaligned or short workspace.  Asynchronous;
+ * capturable in a CUDA graph.
+ */
+size_t dm_batch_workspace_bytes(int32_t n);
+dm_status dm_update_tf_batch_ws(const dm_batch_item *items, int32_t n,
+                                const dm_batch_tuning *tuning, void *d_workspace,
+                                size_t workspace_bytes, void *stream);
 
 /*
  * Instrumentation: when set, dm_update_tf() records `ev_begin` on its stream right before

@@ -27,11 +27,13 @@ DM_MAX_BLOCK = 16
 DM_NOALLOC_MAX_TF_SIZE = 16384
 DM_NOALLOC_SCRATCH_BYTES = 4096
 DM_BATCH_MAX_ITEMS = 64
+DM_BATCH_MAX_EDITS_PER_GROUP = 8
 
 #: every function declared in include/dm.h
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_config_hash",
+            "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_batch_workspace_bytes",
+            "dm_update_tf_batch_ws", "dm_render", "dm_config_hash",
             "dm_mark_built", "dm_sync", "dm_destroy",
             "dm_last_error_string", "dm_status_string", "dm_version")
 
@@ -58,7 +60,8 @@ class dm_batch_item(ctypes.Structure):
 
 
 class dm_batch_tuning(ctypes.Structure):
-    _fields_ = [("combine_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+    _fields_ = [("combine_ctas_per_sm", ctypes.c_int32), ("loads_per_stage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class dm_camera(ctypes.Structure):
@@ -99,6 +102,10 @@ def load(path: str = LIB_PATH):
     lib.dm_update_tf_noalloc.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, S, P, S, P, P, P]
     lib.dm_update_tf_batch.argtypes = [ctypes.POINTER(dm_batch_item), S,
                                        ctypes.POINTER(dm_batch_tuning), P]
+    lib.dm_batch_workspace_bytes.argtypes = [S]
+    lib.dm_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.dm_update_tf_batch_ws.argtypes = [ctypes.POINTER(dm_batch_item), S,
+                                          ctypes.POINTER(dm_batch_tuning), P, ctypes.c_size_t, P]
     lib.dm_render.argtypes = [P, S, P, S, P, P, S, ctypes.POINTER(dm_camera), P, P, P]
     lib.dm_config_hash.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.dm_mark_built.argtypes = [P, ctypes.c_uint64, S, P]
@@ -112,8 +119,8 @@ def load(path: str = LIB_PATH):
     lib.dm_version.argtypes = []
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
-              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_render", "dm_config_hash",
-              "dm_mark_built", "dm_sync", "dm_version"):
+              "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_update_tf_batch_ws",
+              "dm_render", "dm_config_hash", "dm_mark_built", "dm_sync", "dm_version"):
         getattr(lib, n).restype = S
     _lib = lib
     return lib
@@ -227,21 +234,47 @@ class PreparedBatch:
         self.first_ctx = items[0][0] if self.n else None
 
 
+def _tuning(tuning):
+    """dm_batch_tuning from None (library defaults), an int (combine CTAs per SM) or a
+    (ctas_per_sm, loads_per_stage) pair."""
+    if tuning is None:
+        return None
+    t = dm_batch_tuning()
+    if isinstance(tuning, (tuple, list)):
+        t.combine_ctas_per_sm = int(tuning[0])
+        t.loads_per_stage = int(tuning[1])
+    else:
+        t.combine_ctas_per_sm = int(tuning)
+    return ctypes.byref(t)
+
+
 def dm_update_tf_batch(items, tuning=None, stream=None):
     """items: sequence of (ctx, d_tf_rgba, d_out) device pointers, or a PreparedBatch of
-    them; tuning: ctas per SM of the combine (None = library default)."""
+    them; tuning: see _tuning (None = library defaults)."""
     if not isinstance(items, PreparedBatch):
         items = PreparedBatch(items)
     n, arr = items.n, items.arr
-    tp = None
-    if tuning is not None:
-        t = dm_batch_tuning()
-        t.combine_ctas_per_sm = int(tuning)
-        tp = ctypes.byref(t)
-    st = load().dm_update_tf_batch(arr, n, tp, stream)
+    st = load().dm_update_tf_batch(arr, n, _tuning(tuning), stream)
     if st != DM_OK:
         detail = load().dm_last_error_string(items.first_ctx).decode() if n else ""
         raise DmError(st, "dm_update_tf_batch", detail)
+
+
+def dm_batch_workspace_bytes(n: int) -> int:
+    return int(load().dm_batch_workspace_bytes(int(n)))
+
+
+def dm_update_tf_batch_ws(items, tuning, d_workspace, workspace_bytes, stream=None):
+    """Batched update whose items may repeat a context (several TFs of one volume); the
+    active sets live in the caller's device workspace of dm_batch_workspace_bytes(n)."""
+    if not isinstance(items, PreparedBatch):
+        items = PreparedBatch(items)
+    n, arr = items.n, items.arr
+    st = load().dm_update_tf_batch_ws(arr, n, _tuning(tuning), d_workspace,
+                                      int(workspace_bytes), stream)
+    if st != DM_OK:
+        detail = load().dm_last_error_string(items.first_ctx).decode() if n else ""
+        raise DmError(st, "dm_update_tf_batch_ws", detail)
 
 
 def orbit_camera(dims, angle_rad, width, height, step=0.5, ert=0.98, elevation_rad=0.3):

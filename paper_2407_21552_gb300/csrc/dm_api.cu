@@ -429,49 +429,144 @@ dm_status dm_mark_built(dm_ctx* ctx, uint64_t hash, int32_t with_minmax, void* s
     return DM_OK;
 }
 
+static dm_status check_batch_items(const dm_batch_item* items, int32_t n, bool unique)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        dm_ctx* c = items[i].ctx;
+        if (!c || !items[i].d_tf_rgba || !items[i].d_out ||
+            (reinterpret_cast<uintptr_t>(items[i].d_tf_rgba) & 3))
+            return c ? fail(c, DM_ERR_INVALID_ARG, "batched update: item %d: null or "
+                            "misaligned buffer", i) : DM_ERR_INVALID_ARG;
+        if (!c->d_pdm || !c->d_scratch || !c->built)
+            return fail(c, DM_ERR_NOT_BOUND, "batched update: item %d: context not built", i);
+        if (unique)
+            for (int32_t j = 0; j < i; ++j)
+                if (items[j].ctx == c)
+                    return fail(c, DM_ERR_INVALID_ARG, "dm_update_tf_batch: context repeated "
+                                "(items %d and %d)", j, i);
+    }
+    return DM_OK;
+}
+
+static dmk::BatchTuning batch_tuning(const dm_batch_tuning* t)
+{
+    dmk::BatchTuning bt;
+    bt.ctas_per_sm = t ? t->combine_ctas_per_sm : 0;
+    bt.loads_per_stage = t ? t->loads_per_stage : 0;
+    return bt;
+}
+
+static void group_of(dm_ctx* c, dmk::BatchGroup& d)
+{
+    uint8_t* scratch = static_cast<uint8_t*>(c->d_scratch);
+    d.pdm = static_cast<const uint8_t*>(c->d_pdm);
+    d.plane = c->geo.plane;
+    d.G = c->geo.G;
+    d.lut = scratch + c->off_lut;
+    d.N = c->cfg.tf_size;
+    d.K = c->cfg.num_partitions;
+    d.J = c->J;
+    d.E = 0;
+}
+
 dm_status dm_update_tf_batch(const dm_batch_item* items, int32_t n, const dm_batch_tuning* tuning,
                              void* stream)
 {
     if (!items || n < 0) return DM_ERR_INVALID_ARG;
     if (n == 0) return DM_OK;
-    for (int32_t i = 0; i < n; ++i) {
-        dm_ctx* c = items[i].ctx;
-        if (!c || !items[i].d_tf_rgba || !items[i].d_out ||
-            (reinterpret_cast<uintptr_t>(items[i].d_tf_rgba) & 3))
-            return c ? fail(c, DM_ERR_INVALID_ARG, "dm_update_tf_batch: item %d: null or "
-                            "misaligned buffer", i) : DM_ERR_INVALID_ARG;
-        if (!c->d_pdm || !c->d_scratch || !c->built)
-            return fail(c, DM_ERR_NOT_BOUND, "dm_update_tf_batch: item %d: context not built", i);
-        for (int32_t j = 0; j < i; ++j)
-            if (items[j].ctx == c)
-                return fail(c, DM_ERR_INVALID_ARG, "dm_update_tf_batch: context repeated "
-                            "(items %d and %d)", j, i);
-    }
+    dm_status st = check_batch_items(items, n, true);
+    if (st != DM_OK) return st;
     dm_ctx* first = items[0].ctx;
-    dm_status st = check_sticky(first, "dm_update_tf_batch (earlier work)");
+    st = check_sticky(first, "dm_update_tf_batch (earlier work)");
     if (st != DM_OK) return st;
     cudaStream_t s = as_stream(stream);
-    const int per_sm = tuning ? tuning->combine_ctas_per_sm : 0;
-    dmk::BatchDesc desc[dmk::kMaxBatch];
+    const dmk::BatchTuning bt = batch_tuning(tuning);
+    dmk::BatchGroup desc[dmk::kMaxBatch];
     for (int32_t i0 = 0; i0 < n; i0 += dmk::kMaxBatch) {
         const int m = (n - i0) < dmk::kMaxBatch ? (n - i0) : dmk::kMaxBatch;
-        for (int k = 0; k < m; ++k) {
-            dm_ctx* c = items[i0 + k].ctx;
+        for (int k = 0; k < m; ++k) {                   // one TF per group; the plane list
+            dm_ctx* c = items[i0 + k].ctx;             // lives in the context's scratch
             uint8_t* scratch = static_cast<uint8_t*>(c->d_scratch);
-            dmk::BatchDesc& d = desc[k];
-            d.pdm = static_cast<const uint8_t*>(c->d_pdm);
-            d.plane = c->geo.plane;
-            d.G = c->geo.G;
-            d.tf = items[i0 + k].d_tf_rgba;
-            d.out = items[i0 + k].d_out;
-            d.lut = scratch + c->off_lut;
-            d.act = reinterpret_cast<uint16_t*>(scratch + c->off_act);
-            d.nact = reinterpret_cast<int32_t*>(scratch + c->off_nact);
-            d.N = c->cfg.tf_size;
-            d.K = c->cfg.num_partitions;
-            d.J = c->J;
+            dmk::BatchGroup& d = desc[k];
+            group_of(c, d);
+            d.list = reinterpret_cast<uint16_t*>(scratch + c->off_act);
+            d.emask = nullptr;
+            d.count = reinterpret_cast<int32_t*>(scratch + c->off_nact);
+            d.E = 1;
+            d.tf[0] = items[i0 + k].d_tf_rgba;
+            d.out[0] = items[i0 + k].d_out;
         }
-        cudaError_t e = dmk::launch_update_batch(desc, m, per_sm, first->num_sms, s);
+        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched update");
+    }
+    return DM_OK;
+}
+
+// Workspace slot of one group: the plane count, then the padded plane list and TF sets.
+static size_t ws_slot_bytes()
+{
+    const size_t entries = dmk::batch_list_entries(2048);
+    return align_up(16 + entries * 3, 256);
+}
+
+size_t dm_batch_workspace_bytes(int32_t n) { return n > 0 ? size_t(n) * ws_slot_bytes() : 0; }
+
+dm_status dm_update_tf_batch_ws(const dm_batch_item* items, int32_t n,
+                                const dm_batch_tuning* tuning, void* d_workspace,
+                                size_t workspace_bytes, void* stream)
+{
+    if (!items || n < 0) return DM_ERR_INVALID_ARG;
+    if (n == 0) return DM_OK;
+    dm_ctx* first = items[0].ctx;
+    if (!first) return DM_ERR_INVALID_ARG;
+    if (!d_workspace || !aligned(d_workspace, 256) || workspace_bytes < dm_batch_workspace_bytes(n))
+        return fail(first, DM_ERR_INVALID_ARG, "dm_update_tf_batch_ws: workspace null, not "
+                    "256-byte aligned or smaller than dm_batch_workspace_bytes(%d)", n);
+    dm_status st = check_batch_items(items, n, false);
+    if (st != DM_OK) return st;
+    st = check_sticky(first, "dm_update_tf_batch_ws (earlier work)");
+    if (st != DM_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    const dmk::BatchTuning bt = batch_tuning(tuning);
+    const size_t slot = ws_slot_bytes();
+    const size_t entries = dmk::batch_list_entries(2048);
+    uint8_t* ws = static_cast<uint8_t*>(d_workspace);
+    // groups: the items of one context in their order, up to kMaxGroupEdits per group
+    dmk::BatchGroup desc[dmk::kMaxBatch];
+    int m = 0, used_slots = 0;
+    bool* taken = new (std::nothrow) bool[size_t(n)]();
+    if (!taken) return fail(first, DM_ERR_INVALID_ARG, "dm_update_tf_batch_ws: out of host memory");
+    for (int32_t i = 0; i < n; ++i) {
+        if (taken[i]) continue;
+        dm_ctx* c = items[i].ctx;
+        for (int32_t j = i; j < n;) {              // fill groups of this context
+            dmk::BatchGroup& d = desc[m];
+            group_of(c, d);
+            uint8_t* sl = ws + size_t(used_slots++) * slot;
+            d.count = reinterpret_cast<int32_t*>(sl);
+            d.list = reinterpret_cast<uint16_t*>(sl + 16);
+            d.emask = sl + 16 + entries * 2;
+            for (; j < n && d.E < dmk::kMaxGroupEdits; ++j) {
+                if (taken[j] || items[j].ctx != c) continue;
+                taken[j] = true;
+                d.tf[d.E] = items[j].d_tf_rgba;
+                d.out[d.E] = items[j].d_out;
+                ++d.E;
+            }
+            if (++m == dmk::kMaxBatch) {
+                cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
+                if (e != cudaSuccess) {
+                    delete[] taken;
+                    return cuda_fail(first, e, "batched update");
+                }
+                m = 0;
+            }
+            while (j < n && (taken[j] || items[j].ctx != c)) ++j;
+        }
+    }
+    delete[] taken;
+    if (m > 0) {
+        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(first, e, "batched update");
     }
     return DM_OK;

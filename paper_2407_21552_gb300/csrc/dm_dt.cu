@@ -17,15 +17,17 @@
 // one 16-byte store writes them.  The one-map pass (full recompute) takes one masked
 // clz/ffs plus the two lookups per output, four outputs per 32-bit store.
 //
-// y / z passes: a CTA stages a tile of 16 or 32 neighbouring lines (full line length) in
-// shared memory and builds a doubling table of window minima (level j holds the min over
-// 2^j rows, 16 lines per vector with __vminu4).  h(i) <= t holds exactly when the window
-// of radius t around i holds a value <= t (monotone in t).  A thread walks a segment of
-// one line: a binary search over t gives h at the segment start; after that h changes by
-// at most 1 per step (h is 1-Lipschitz along the line), so each further output takes one
-// window query (radius h - 1) and, when h does not drop, the two rows at distance h read
-// from level 0, which stays the input.  Outputs go straight to global memory in place
-// (the tile was staged before any store).
+// y / z passes: one thread per line, a CTA per tile of kLineTile neighbouring lines (along
+// x) staged whole in shared memory.  The transform splits into the sweeps
+// F(i) = min over j <= i of max(i - j, g(j)) and, run backwards over F, h itself (the
+// backward sweep of F takes the j > i terms; j <= i ones are already folded into F).  A
+// sweep keeps its level v = F(i - 1) and T, the last position j with g(j) <= v.  A new
+// value g(i) <= v starts a new level at i; otherwise the level holds while a source of
+// value v lies within distance v (i - T <= v), and else rises by one: F(i) is then v + 1
+// and T the last position whose value is exactly v + 1, read from a per-line table of the
+// last position of every value (0..255) that the sweep fills as it goes.  Each output
+// costs O(1) work whatever the distances are.  Clamping at 255 needs no extra step: a
+// value of 255 is a source of level 255 that never expires.
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -271,51 +273,96 @@ struct LineGeom {
     int64_t s;          // element stride along the line
     int64_t os;         // stride of the outer index
     int64_t plane;      // stride between planes
-    int J;              // highest doubling-table level
-    int seg;            // rows per thread segment
-    int vec_ok;         // rows of 16 columns are 16-byte aligned and full
+    int vec_ok;         // rows of kLineTile columns are 16-byte aligned and full
 };
 
-// min of g over rows [r - t, r + t] clipped to the line, from the doubling table
-template <int TC>
-__device__ __forceinline__ int window_min(const uint8_t* __restrict__ lvl, int L, int r, int t,
-                                          int c)
+// Bytes of shared memory of a tile: the lines' values [L][TC] and the table of last
+// positions [256][TC] (uint16).
+__host__ __device__ inline size_t sweep_tile_bytes(int L, int TC)
 {
-    const int wl = max(0, r - t), wh = min(L - 1, r + t);
-    const int j = 31 - __clz(wh - wl + 1);
-    const uint8_t* Lj = lvl + j * L * TC;
-    return min(int(Lj[wl * TC + c]), int(Lj[(wh - (1 << j) + 1) * TC + c]));
+    return (size_t(L) * TC + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ uint4 vmin16(uint4 a, uint4 b)
+// One sweep over a line of the tile, rows in the order FINAL gives (forward from row 0, or
+// backward from row L-1).  Positions enter the table as `off` + the step count, so that a
+// sweep never mistakes an entry of an earlier sweep (all below its own `off`) for one of
+// its own.  FINAL: the values go to global memory (column `col` of the tile's rows);
+// otherwise back into the tile.  The values of kRun rows are read before any of them is
+// processed, and the table entry a rise to the next level would need is read one step
+// ahead (then corrected for the value the step itself enters), so that no shared-memory
+// read waits inside a step; every step is the same branch-free sequence.
+constexpr int kRun = 8;
+
+template <int TC, bool FINAL>
+__device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, uint16_t* __restrict__ tab,
+                                           int L, int off, uint8_t* __restrict__ col,
+                                           int64_t gstride)
 {
-    return make_uint4(__vminu4(a.x, b.x), __vminu4(a.y, b.y), __vminu4(a.z, b.z),
-                      __vminu4(a.w, b.w));
+    const int r0 = FINAL ? L - 1 : 0;
+    const int dir = FINAL ? -1 : 1;
+    int lv = 255;                // level of the previous row (255 before the first)
+    int T = off;                 // last position holding a value <= lv
+    int x = off;                 // the table entry of level lv + 1, read one step ahead
+    for (int k0 = 0; k0 < L; k0 += kRun) {
+        int gv[kRun];
+#pragma unroll
+        for (int i = 0; i < kRun; ++i)
+            gv[i] = k0 + i < L ? tile[(r0 + dir * (k0 + i)) * TC] : 0;
+#pragma unroll
+        for (int i = 0; i < kRun; ++i) {
+            const int k = k0 + i;
+            if (k >= L) break;
+            const int r = r0 + dir * k;
+            const int g = gv[i];
+            const int pos = off + k;
+            tab[g * TC] = uint16_t(pos);
+            const int w = lv + 1;
+            const int xw = g == w ? pos : x;                 // this step's own entry
+            const bool drop = g <= lv;
+            const bool rise = !drop && pos - T > lv;
+            T = drop ? pos : (rise ? max(T, xw) : T);
+            lv = drop ? g : (rise ? w : lv);
+            x = tab[min(lv + 1, 255) * TC];                  // for the next step
+            if (FINAL) col[int64_t(r) * gstride] = uint8_t(lv);
+            else tile[r * TC] = uint8_t(lv);
+        }
+    }
 }
 
-// One tile = TC adjacent columns x one whole line.  Level 0 of the table keeps g; every
-// output goes straight to global memory (in place: the tile was staged before any store).
+// One tile = TC adjacent columns x one whole line of every column; thread c takes column c.
+// The tile is staged before any output is written, so the pass works in place.
 template <int TC>
-__global__ void __launch_bounds__(kThreads)
-k_line_pass(uint8_t* buf, LineGeom lg)
+__global__ void __launch_bounds__(TC)
+k_line_sweep(uint8_t* buf, LineGeom lg)
 {
-    extern __shared__ __align__(16) uint8_t s_lvl[];        // [J+1][L][TC]
+    extern __shared__ uint32_t s_mem[];
     constexpr int V = TC / 16;                               // 16-byte vectors per row
+    const int L = lg.L;
+    uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_mem);     // [L][TC]
+    uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_tile + sweep_tile_bytes(L, TC));  // [256][TC]
     pdl_wait();
     const int tid = threadIdx.x;
-    const int L = lg.L;
     const int x0 = blockIdx.x * TC;
     uint8_t* base = buf + int64_t(blockIdx.z) * lg.plane + int64_t(blockIdx.y) * lg.os + x0;
     const int ncols = min(TC, lg.gx - x0);
 
-    // ---- stage level 0; note whether the tile can change at all (some value >= 2 and
-    //      not everything 255)
+    // ---- stage the tile (asynchronous copies, all in flight at once); note whether it can
+    //      change at all (some value >= 2 and not everything 255)
     int any_big = 0, any_not255 = 0;
     if (lg.vec_ok) {
-        for (int i = tid; i < L * V; i += kThreads) {
+        for (int i = tid; i < L * V; i += TC) {
             const int r = i / V, q = i - r * V;
-            const uint4 v = *reinterpret_cast<const uint4*>(base + int64_t(r) * lg.s + 16 * q);
-            reinterpret_cast<uint4*>(s_lvl)[i] = v;
+            const unsigned sa = static_cast<unsigned>(
+                __cvta_generic_to_shared(reinterpret_cast<uint4*>(s_tile) + i));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                         "l"(base + int64_t(r) * lg.s + 16 * q)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        for (int i = tid; i < L * V; i += TC) {
+            const uint4 v = reinterpret_cast<const uint4*>(s_tile)[i];
             const unsigned w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -324,86 +371,35 @@ k_line_pass(uint8_t* buf, LineGeom lg)
             }
         }
     } else {
-        for (int i = tid; i < L * TC; i += kThreads) {
+        for (int i = tid; i < L * TC; i += TC) {
             const int r = i / TC, c = i - r * TC;
             uint8_t v = 255;
             if (c < ncols) v = base[int64_t(r) * lg.s + c];
-            s_lvl[r * TC + c] = v;
+            s_tile[i] = v;
             any_not255 |= (c < ncols) && (v != 255);
             any_big |= (c < ncols) && (v >= 2);
         }
     }
+    // the table starts at position 0 everywhere: the forward sweep's T is >= 0 from its
+    // first row on, so these entries are never taken for a source
+    for (int i = tid; i < 256 * TC / 8; i += TC)
+        reinterpret_cast<uint4*>(s_tab)[i] = make_uint4(0u, 0u, 0u, 0u);
     any_big = __syncthreads_or(any_big);
     any_not255 = __syncthreads_or(any_not255);
     if (!any_big || !any_not255) return;   // all values <= 1, or all 255: h == g
-
-    // ---- doubling table of window minima, 16 columns per vector
-    uint4* lv = reinterpret_cast<uint4*>(s_lvl);
-    for (int j = 1; j <= lg.J; ++j) {
-        const uint4* prevl = lv + (j - 1) * L * V;
-        uint4* cur = lv + j * L * V;
-        const int half = 1 << (j - 1);
-        for (int i = tid; i < L * V; i += kThreads) {
-            const int r = i / V, q = i - r * V;
-            const int r2 = min(r + half, L - 1);
-            cur[i] = vmin16(prevl[i], prevl[r2 * V + q]);
-        }
-        __syncthreads();
-    }
-
-    // ---- outputs: one thread per (segment, column), rows in order.  At a segment start h
-    //      comes from a binary search; after that h moves by at most 1 per row (the
-    //      transform is 1-Lipschitz), and the window of radius h is the window of radius
-    //      h - 1 plus the two rows at distance h, read from level 0.
-    const int seg = lg.seg;
-    const int nseg = (L + seg - 1) / seg;
-    for (int item = tid; item < nseg * TC; item += kThreads) {
-        const int c = item % TC, sg = item / TC;
-        if (c >= ncols) continue;
-        const int r0 = sg * seg, r1 = min(L, r0 + seg);
-        uint8_t* col = base + c;
-        int h = 0;
-        for (int r = r0; r < r1; ++r) {
-            const int gv = s_lvl[r * TC + c];
-            if (gv <= 1) {
-                h = gv;                                      // h == g for g in {0, 1}
-            } else if (r == r0) {
-                int lo = 1, hi = gv;                         // least t with window min <= t
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (window_min<TC>(s_lvl, L, r, mid, c) <= mid) hi = mid; else lo = mid + 1;
-                }
-                h = lo;
-            } else {                                         // h(r) in {h-1, h, h+1}
-                int m;                                       // min over radius h - 1
-                if (h >= 2) {
-                    m = window_min<TC>(s_lvl, L, r, h - 1, c);
-                } else {
-                    m = h == 1 ? gv : 255;                   // radius 0, or the empty window
-                }
-                if (h >= 2 && m <= h - 1) {
-                    h = h - 1;
-                } else {
-                    if (r - h >= 0) m = min(m, int(s_lvl[(r - h) * TC + c]));
-                    if (r + h < L) m = min(m, int(s_lvl[(r + h) * TC + c]));
-                    if (m > h) h = h + 1;
-                }
-            }
-            col[int64_t(r) * lg.s] = uint8_t(h);
-        }
-    }
+    if (tid >= ncols) return;               // no barrier follows
+    uint8_t* tile = s_tile + tid;
+    uint16_t* tab = s_tab + tid;
+    sweep_line<TC, false>(tile, tab, L, 0, nullptr, 0);
+    sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
 }
 
 }  // namespace
 
-static size_t line_pass_smem_tc(int L, int TC)
+size_t line_pass_smem(int L)
 {
-    int J = 0;
-    while (J < kMaxLevels - 1 && (2 << J) <= L) ++J;
-    return size_t(J + 1) * size_t(L) * TC;
+    return sweep_tile_bytes(L, kLineTile) + size_t(256) * kLineTile * sizeof(uint16_t);
 }
-
-size_t line_pass_smem(int L) { return line_pass_smem_tc(L, kLineTile); }
 
 size_t xpass_smem(int gx, int K)
 {
@@ -478,30 +474,15 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
         lg.os = g.gx;
     }
     if (lg.L <= 1) return cudaSuccess;   // a single block per line: h == g
-    int J = 0;
-    while (J < kMaxLevels - 1 && (2 << J) <= lg.L) ++J;
-    lg.J = J;
-    // Batched passes take 32-column tiles (a warp owns one segment and stores 32 bytes
-    // per row) while the table still lets 3 CTAs share an SM; one-map passes (the full
-    // recompute, latency-bound) and long lines keep 16 columns.  Segments are sized so
-    // that columns x segments cover about one CTA of threads.
-    const bool wide = P > 1 && line_pass_smem_tc(lg.L, 2 * kLineTile) <= size_t(kLineWideSmem);
-    const int TC = wide ? 2 * kLineTile : kLineTile;
-    lg.seg = (lg.L * TC + kThreads - 1) / kThreads;
-    if (lg.seg < 4) lg.seg = 4;
+    constexpr int TC = kLineTile;
     lg.vec_ok = (g.gx % TC == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
                 (plane % 16 == 0);
-    const size_t smem = line_pass_smem_tc(lg.L, TC);
+    const size_t smem = line_pass_smem(lg.L);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
     dim3 grid((g.gx + TC - 1) / TC, lg.n_outer, P);
-    if (wide) {
-        cudaError_t e = ensure_dynamic_smem<k_line_pass<2 * kLineTile>>(int(smem));
-        if (e != cudaSuccess) return e;
-        return launch_pdl(k_line_pass<2 * kLineTile>, grid, dim3(kThreads), smem, s, buf, lg);
-    }
-    cudaError_t e = ensure_dynamic_smem<k_line_pass<kLineTile>>(int(smem));
+    cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC>>(int(smem));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_line_pass<kLineTile>, grid, dim3(kThreads), smem, s, buf, lg);
+    return launch_pdl(k_line_sweep<TC>, grid, dim3(TC), smem, s, buf, lg);
 }
 
 }  // namespace dmk

@@ -510,6 +510,466 @@ k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__
     }
 }
 
+// ------------------------------------------------------------------------------------
+// The b = 4, apron-1 footprint kernel with 16-byte voxel loads (X a multiple of 16 / sizeof(T)
+// and a 16-byte aligned volume).  A lane loads 16 bytes of a voxel row, VL = 16 / sizeof(T)
+// voxels, i.e. BL = VL / 4 whole blocks; the 32 lanes of a warp cover 32 * VL voxels of one
+// block row, the CTA's 8 warps 8 block rows, and the CTA streams a chunk of block-slices
+// along z.  Per voxel slice and warp:
+//  - each voxel's one-hot partition mask (or visibility bit) comes from a shared-memory
+//    table indexed by the clamped intensity; min / max are taken on whole 32-bit words
+//    (two 16-bit or four 8-bit voxels per operation);
+//  - the x footprint of a block is its 4 voxels plus the last voxel of the block to the left
+//    and the first of the block to the right: inside the lane directly, across lanes by a
+//    shuffle (the CTA's outermost lanes load the edge voxel themselves);
+//  - rows: a warp handles the 4 core rows of its block row.  The footprints of its first
+//    and last row go through shared memory to the warps above and below, which hold them as
+//    apron rows; warp 0 and warp 7 load the CTA's outer apron rows themselves.  One CTA
+//    barrier per slice (double-buffered);
+//  - z: a slice belongs to one or two block-slices; their running masks and min / max stay
+//    in registers, and a block is written once its last slice is in (16-byte mask stores);
+//  - the next slice's rows are copied into shared memory (cp.async) while the current one
+//    is reduced, so that the voxel reads stay in flight.
+// OR distributes over the footprint's parts and min / max likewise, so the result is the
+// footprint reduction of §3.1 whatever order the parts are combined in.
+constexpr int kVZChunk = 8;                    // block-slices per CTA
+
+template <typename T>
+struct VTraits;
+template <>
+struct VTraits<uint16_t> {
+    static constexpr int VL = 8;
+    __device__ static uint32_t vmin(uint32_t a, uint32_t b) { return min_u16x2(a, b); }
+    __device__ static uint32_t vmax(uint32_t a, uint32_t b)
+    {
+        uint32_t d;
+        asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+        return d;
+    }
+    __device__ static unsigned get(uint32_t w, int k) { return (w >> (16 * k)) & 0xFFFFu; }
+    static constexpr int PER_WORD = 2;
+    static constexpr uint32_t NEUTRAL_MIN = 0xFFFFFFFFu;
+};
+template <>
+struct VTraits<uint8_t> {
+    static constexpr int VL = 16;
+    __device__ static uint32_t vmin(uint32_t a, uint32_t b) { return __vminu4(a, b); }
+    __device__ static uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
+    __device__ static unsigned get(uint32_t w, int k) { return (w >> (8 * k)) & 0xFFu; }
+    static constexpr int PER_WORD = 4;
+    static constexpr uint32_t NEUTRAL_MIN = 0xFFFFFFFFu;
+};
+
+// Footprint masks and min / max of the BL blocks of a lane from per-voxel-position parts
+// (one row, or several rows already combined position by position): `core` = OR of each
+// block's 4 voxels, `first` / `last` = its first / last voxel, `em`, `emn`, `emx` = the edge
+// voxel of lanes 0 and 31; `wmn` / `wmx` = the 4 words of voxel minima / maxima.
+template <typename T, int NW>
+__device__ __forceinline__ void lane_footprint(const uint32_t (&core)[16 / sizeof(T) / 4][NW],
+                                               const uint32_t (&first)[16 / sizeof(T) / 4][NW],
+                                               const uint32_t (&last)[16 / sizeof(T) / 4][NW],
+                                               const uint32_t (&em)[NW], unsigned emn, unsigned emx,
+                                               const uint32_t (&wmn)[4], const uint32_t (&wmx)[4],
+                                               int lane, bool want_mm,
+                                               uint32_t (&fp)[16 / sizeof(T) / 4][NW],
+                                               unsigned (&fmn)[16 / sizeof(T) / 4],
+                                               unsigned (&fmx)[16 / sizeof(T) / 4])
+{
+    using Tr = VTraits<T>;
+    constexpr int BL = Tr::VL / 4;
+    uint32_t lft[NW], rgt[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        lft[w] = __shfl_up_sync(0xFFFFFFFFu, last[BL - 1][w], 1);
+        rgt[w] = __shfl_down_sync(0xFFFFFFFFu, first[0][w], 1);
+        if (lane == 0) lft[w] = em[w];
+        if (lane == 31) rgt[w] = em[w];
+    }
+#pragma unroll
+    for (int j = 0; j < BL; ++j)
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            fp[j][w] = core[j][w] | (j == 0 ? lft[w] : last[j - 1][w]) |
+                       (j == BL - 1 ? rgt[w] : first[j + 1][w]);
+#pragma unroll
+    for (int j = 0; j < BL; ++j) {
+        fmn[j] = 0xFFFFu;
+        fmx[j] = 0;
+    }
+    if (!want_mm) return;
+    // voxel minima / maxima of the positions next to the lane (packed min | max << 16)
+    constexpr int VB = 32 / Tr::PER_WORD;                     // bits per voxel in a word
+    const unsigned lastv = (wmn[3] >> (32 - VB)) | ((wmx[3] >> (32 - VB)) << 16);
+    const unsigned firstv = Tr::get(wmn[0], 0) | (Tr::get(wmx[0], 0) << 16);
+    unsigned lp = __shfl_up_sync(0xFFFFFFFFu, lastv, 1);
+    unsigned rp = __shfl_down_sync(0xFFFFFFFFu, firstv, 1);
+    if (lane == 0) lp = emn | (emx << 16);
+    if (lane == 31) rp = emn | (emx << 16);
+#pragma unroll
+    for (int j = 0; j < BL; ++j) {
+        unsigned mn, mx;
+        if constexpr (sizeof(T) == 2) {                       // block j: words 2j, 2j+1
+            const uint32_t a = Tr::vmin(wmn[2 * j], wmn[2 * j + 1]);
+            const uint32_t b = Tr::vmax(wmx[2 * j], wmx[2 * j + 1]);
+            mn = min(a & 0xFFFFu, a >> 16);
+            mx = max(b & 0xFFFFu, b >> 16);
+            const unsigned bef = j == 0 ? lp : (Tr::get(wmn[2 * j - 1], 1) | (Tr::get(wmx[2 * j - 1], 1) << 16));
+            const unsigned aft = j == BL - 1 ? rp : (Tr::get(wmn[2 * j + 2], 0) | (Tr::get(wmx[2 * j + 2], 0) << 16));
+            mn = min(mn, min(bef & 0xFFFFu, aft & 0xFFFFu));
+            mx = max(mx, max(bef >> 16, aft >> 16));
+        } else {                                              // block j: word j
+            const uint32_t a = min_u16x2(wmn[j] & 0x00FF00FFu, (wmn[j] >> 8) & 0x00FF00FFu);
+            const uint32_t b = VTraits<uint16_t>::vmax(wmx[j] & 0x00FF00FFu, (wmx[j] >> 8) & 0x00FF00FFu);
+            mn = min(a & 0xFFFFu, a >> 16);
+            mx = max(b & 0xFFFFu, b >> 16);
+            const unsigned bef = j == 0 ? lp : (Tr::get(wmn[j - 1], 3) | (Tr::get(wmx[j - 1], 3) << 16));
+            const unsigned aft = j == BL - 1 ? rp : (Tr::get(wmn[j + 1], 0) | (Tr::get(wmx[j + 1], 0) << 16));
+            mn = min(mn, min(bef & 0xFFFFu, aft & 0xFFFFu));
+            mx = max(mx, max(bef >> 16, aft >> 16));
+        }
+        fmn[j] = mn;
+        fmx[j] = mx;
+    }
+}
+
+// One voxel row of a lane: per-position parts from one 16-byte load `q` (already known to
+// lie in the volume when `ok`) and the edge voxel `ev` (lanes 0 / 31; 0xFFFFFFFF = none).
+template <typename T, int NW>
+__device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, uint32_t nmax2,
+                                         unsigned nmax, const uint32_t* __restrict__ s_tab,
+                                         uint32_t (&core)[16 / sizeof(T) / 4][NW],
+                                         uint32_t (&first)[16 / sizeof(T) / 4][NW],
+                                         uint32_t (&last)[16 / sizeof(T) / 4][NW],
+                                         uint32_t (&em)[NW], unsigned& emn, unsigned& emx,
+                                         uint32_t (&wv)[4])
+{
+    using Tr = VTraits<T>;
+    constexpr int BL = Tr::VL / 4;
+    constexpr int PW = Tr::PER_WORD;
+    wv[0] = q.x; wv[1] = q.y; wv[2] = q.z; wv[3] = q.w;
+#pragma unroll
+    for (int j = 0; j < BL; ++j)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) core[j][w] = first[j][w] = last[j][w] = 0;
+    if (ok) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wv[k] = Tr::vmin(wv[k], nmax2);
+#pragma unroll
+        for (int j = 0; j < BL; ++j) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int v = 4 * j + i;                       // voxel position in the lane
+                const unsigned x = Tr::get(wv[v / PW], v % PW);
+                uint32_t m[NW];
+                if constexpr (NW == 2) {
+                    const uint2 t2 = reinterpret_cast<const uint2*>(s_tab)[x];
+                    m[0] = t2.x;
+                    m[NW - 1] = t2.y;
+                } else {
+                    m[0] = s_tab[x];
+                }
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    core[j][w] |= m[w];
+                    if (i == 0) first[j][w] = m[w];
+                    if (i == 3) last[j][w] = m[w];
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wv[k] = Tr::NEUTRAL_MIN;
+    }
+    if (ev != 0xFFFFFFFFu) {
+        const unsigned x = min(ev, nmax);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) em[w] = s_tab[x * NW + w];
+        emn = x;
+        emx = x;
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) em[w] = 0;
+        emn = 0xFFFFu;
+        emx = 0;
+    }
+}
+
+template <typename T, int NW, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
+          const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+          uint8_t* __restrict__ occ, int tab_n)
+{
+    using Tr = VTraits<T>;
+    constexpr int VL = Tr::VL, BL = VL / 4;
+    constexpr int XW = BL * (NW + 1);                          // words a lane publishes per row
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);       // [tab_n][NW]
+    uint32_t* s_x = reinterpret_cast<uint32_t*>(smem + align16(size_t(tab_n) * NW * 4));
+    // s_x: [2 buffers][2 rows (first, last)][kWarps][XW][32 lanes]
+    uint4* s_rows = reinterpret_cast<uint4*>(s_x + 2 * 2 * kWarps * XW * 32);
+    // s_rows: [2 slices][kWarps][5 rows][32 lanes]: the voxel rows, copied one slice ahead
+    pdl_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < tab_n; i += kWarps * 32) {
+        if (MODE == kModePom) {
+            const unsigned c = lut[i];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) s_tab[i * NW + w] = ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
+        } else {
+            s_tab[i] = cnt[i + 1] > cnt[i] ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    const bool want_mm = MODE == kModePom && minmax != nullptr;
+    const int X = p.X, Y = p.Y;
+    const unsigned nmax = unsigned(p.N - 1);
+    const uint32_t nmax2 = sizeof(T) == 2 ? (min(nmax, 0xFFFFu) * 0x10001u)
+                                          : (min(nmax, 0xFFu) * 0x01010101u);
+    const int by = blockIdx.y * kWarps + warp;
+    const int xv0 = (blockIdx.x * 32 + lane) * VL;             // first voxel of the lane
+    const bool lane_ok = xv0 < X;
+    const int xe = lane == 0 ? int(blockIdx.x) * 32 * VL - 1 : (int(blockIdx.x) + 1) * 32 * VL;
+    const bool edge_ok = (lane == 0 || lane == 31) && xe >= 0 && xe < X;
+    const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
+    const int zs = max(0, 4 * zb0 - 1), ze = min(p.Z - 1, 4 * zb1);
+    const int y0 = by * 4;
+    const int yx = warp == 0 ? y0 - 1 : y0 + 4;                 // warps 0 / 7: outer apron row
+    const bool has_x = warp == 0 || warp == kWarps - 1;
+    const int64_t rowX = X;
+    // running footprint of two block-slices: A = z >> 2, B = the next one (started at its
+    // first apron slice)
+    uint32_t aM[BL][NW], bM[BL][NW];
+    unsigned aMn[BL], aMx[BL], bMn[BL], bMx[BL];
+#pragma unroll
+    for (int j = 0; j < BL; ++j) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) aM[j][w] = bM[j][w] = 0;
+        aMn[j] = bMn[j] = 0xFFFFu;
+        aMx[j] = bMx[j] = 0;
+    }
+    auto store_block = [&](int bz, const uint32_t (&M)[BL][NW], const unsigned (&Mn)[BL],
+                           const unsigned (&Mx)[BL]) {
+        if (bz < zb0 || bz >= zb1 || by >= p.gy || !lane_ok) return;
+        const int64_t blk0 = (int64_t(bz) * p.gy + by) * p.gx + xv0 / 4;
+        if (MODE == kModePom) {
+            uint64_t m64[BL];
+#pragma unroll
+            for (int j = 0; j < BL; ++j)
+                m64[j] = uint64_t(M[j][0]) | (NW > 1 ? (uint64_t(M[j][NW > 1 ? 1 : 0]) << 32) : 0ull);
+            uint64_t* dst = mask + blk0;                       // one mask word per block
+#pragma unroll
+            for (int j = 0; j < BL; j += 2)
+                *reinterpret_cast<uint4*>(dst + j) =
+                    make_uint4(uint32_t(m64[j]), uint32_t(m64[j] >> 32), uint32_t(m64[j + 1]),
+                               uint32_t(m64[j + 1] >> 32));
+            if (want_mm) {
+                if (sizeof(T) == 1) {
+                    uint32_t pk[BL / 2];
+#pragma unroll
+                    for (int j = 0; j < BL; j += 2)
+                        pk[j / 2] = (Mn[j] | (Mx[j] << 8)) | ((Mn[j + 1] | (Mx[j + 1] << 8)) << 16);
+                    uint16_t* mm = reinterpret_cast<uint16_t*>(minmax) + blk0;
+                    *reinterpret_cast<uint2*>(mm) = make_uint2(pk[0], pk[BL / 2 - 1]);
+                } else {
+                    uint32_t* mm = reinterpret_cast<uint32_t*>(minmax) + blk0;
+                    *reinterpret_cast<uint2*>(mm) = make_uint2(Mn[0] | (Mx[0] << 16),
+                                                               Mn[BL - 1] | (Mx[BL - 1] << 16));
+                }
+            }
+        } else {                                               // any alignment
+#pragma unroll
+            for (int j = 0; j < BL; ++j) occ[blk0 + j] = uint8_t(M[j][0] != 0);
+        }
+    };
+    // the rows of a slice: the 4 core rows and, for warps 0 / 7, the outer apron row
+    bool okr[5];
+    int64_t yoff[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int y = t < 4 ? y0 + t : yx;
+        okr[t] = (t < 4 || has_x) && y >= 0 && y < Y;             // warp-uniform
+        yoff[t] = int64_t(okr[t] ? y : 0) * rowX;
+    }
+    // copies of slice z's rows into buffer `bsel` (asynchronous, one group), and the edge
+    // voxels of lanes 0 / 31 into registers
+    auto fetch = [&](int z, int bsel, unsigned (&ev)[5]) {
+        const T* slice = vol + int64_t(z) * Y * rowX;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            if (okr[t] && lane_ok) {
+                const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
+                    s_rows + ((bsel * kWarps + warp) * 5 + t) * 32 + lane));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                             "l"(slice + yoff[t] + xv0)
+                             : "memory");
+            }
+            ev[t] = (okr[t] && edge_ok) ? unsigned(__ldg(slice + yoff[t] + xe)) : 0xFFFFFFFFu;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    unsigned ev_next[5];
+    fetch(zs, 0, ev_next);
+    for (int z = zs; z <= ze; ++z) {
+        const int bsel = (z - zs) & 1;
+        unsigned ev[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) ev[t] = ev_next[t];
+        if (z < ze) fetch(z + 1, bsel ^ 1, ev_next);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");     // this lane's rows of z
+        uint4 q[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t)
+            q[t] = (okr[t] && lane_ok) ? s_rows[((bsel * kWarps + warp) * 5 + t) * 32 + lane]
+                                       : make_uint4(0u, 0u, 0u, 0u);
+        // ---- per-row parts; rows 0 and 3 (and the apron row) keep their own footprints,
+        //      rows 1 and 2 are combined position by position first
+        uint32_t fp[3][BL][NW];                                 // row 0, row 3, rows 1-2
+        unsigned fmn[3][BL], fmx[3][BL];
+        uint32_t xfp[BL][NW];                                   // the outer apron row
+        unsigned xmn[BL], xmx[BL];
+        {
+            uint32_t core[BL][NW], first[BL][NW], last[BL][NW], em[NW], wv[4];
+            unsigned emn, emx;
+            uint32_t c12[BL][NW], f12[BL][NW], l12[BL][NW], e12[NW], mn12[4], mx12[4];
+            unsigned en12 = 0xFFFFu, ex12 = 0;
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                if (t == 4 && !has_x) break;                    // warp-uniform
+                lane_row<T, NW>(q[t], ev[t], okr[t] && lane_ok, nmax2, nmax, s_tab, core, first,
+                                last, em, emn, emx, wv);
+                if (t == 1) {
+#pragma unroll
+                    for (int j = 0; j < BL; ++j)
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) {
+                            c12[j][w] = core[j][w];
+                            f12[j][w] = first[j][w];
+                            l12[j][w] = last[j][w];
+                        }
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) e12[w] = em[w];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) { mn12[k] = wv[k]; mx12[k] = okr[t] && lane_ok ? wv[k] : 0u; }
+                    en12 = emn;
+                    ex12 = emx;
+                    continue;
+                }
+                if (t == 2) {
+#pragma unroll
+                    for (int j = 0; j < BL; ++j)
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) {
+                            c12[j][w] |= core[j][w];
+                            f12[j][w] |= first[j][w];
+                            l12[j][w] |= last[j][w];
+                        }
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) e12[w] |= em[w];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        mn12[k] = Tr::vmin(mn12[k], wv[k]);
+                        mx12[k] = Tr::vmax(mx12[k], okr[t] && lane_ok ? wv[k] : 0u);
+                    }
+                    en12 = min(en12, emn);
+                    ex12 = max(ex12, emx);
+                    lane_footprint<T, NW>(c12, f12, l12, e12, en12, ex12, mn12, mx12, lane, want_mm,
+                                          fp[2], fmn[2], fmx[2]);
+                    continue;
+                }
+                uint32_t wmx[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wmx[k] = okr[t] && lane_ok ? wv[k] : 0u;
+                if (t == 4)
+                    lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm,
+                                          xfp, xmn, xmx);
+                else
+                    lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm,
+                                          fp[t == 0 ? 0 : 1], fmn[t == 0 ? 0 : 1], fmx[t == 0 ? 0 : 1]);
+            }
+        }
+        // ---- publish rows 0 and 3 for the warps below and above
+        const int buf = z & 1;
+        uint32_t* xf = s_x + ((buf * 2 + 0) * kWarps + warp) * XW * 32 + lane;
+        uint32_t* xl = s_x + ((buf * 2 + 1) * kWarps + warp) * XW * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < BL; ++j) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                xf[(j * NW + w) * 32] = fp[0][j][w];
+                xl[(j * NW + w) * 32] = fp[1][j][w];
+            }
+            xf[(BL * NW + j) * 32] = fmn[0][j] | (fmx[0][j] << 16);
+            xl[(BL * NW + j) * 32] = fmn[1][j] | (fmx[1][j] << 16);
+        }
+        __syncthreads();
+        // ---- the slice's footprint of every block of the lane
+        uint32_t S[BL][NW];
+        unsigned Smn[BL], Smx[BL];
+        const uint32_t* up = s_x + ((buf * 2 + 1) * kWarps + (warp > 0 ? warp - 1 : 0)) * XW * 32 + lane;
+        const uint32_t* dn = s_x + ((buf * 2 + 0) * kWarps + (warp < kWarps - 1 ? warp + 1 : 0)) * XW * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < BL; ++j) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t a = warp > 0 ? up[(j * NW + w) * 32] : (okr[4] ? xfp[j][w] : 0u);
+                const uint32_t b = warp < kWarps - 1 ? dn[(j * NW + w) * 32] : (okr[4] ? xfp[j][w] : 0u);
+                S[j][w] = fp[0][j][w] | fp[1][j][w] | fp[2][j][w] | a | b;
+            }
+            unsigned mn = min(min(fmn[0][j], fmn[1][j]), fmn[2][j]);
+            unsigned mx = max(max(fmx[0][j], fmx[1][j]), fmx[2][j]);
+            const unsigned pa = warp > 0 ? up[(BL * NW + j) * 32]
+                                         : (okr[4] ? (xmn[j] | (xmx[j] << 16)) : 0xFFFFu);
+            const unsigned pb = warp < kWarps - 1 ? dn[(BL * NW + j) * 32]
+                                                  : (okr[4] ? (xmn[j] | (xmx[j] << 16)) : 0xFFFFu);
+            mn = min(mn, min(pa & 0xFFFFu, pb & 0xFFFFu));
+            mx = max(mx, max(pa >> 16, pb >> 16));
+            Smn[j] = mn;
+            Smx[j] = mx;
+        }
+        // ---- z: slice z = 4 q + t belongs to block-slice q, to q - 1 when t == 0 and to
+        //      q + 1 when t == 3
+        const int t = z & 3, qz = z >> 2;
+        if (t == 0) {
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) aM[j][w] |= S[j][w];
+                aMn[j] = min(aMn[j], Smn[j]);
+                aMx[j] = max(aMx[j], Smx[j]);
+            }
+            store_block(qz - 1, aM, aMn, aMx);
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) { aM[j][w] = bM[j][w] | S[j][w]; bM[j][w] = 0; }
+                aMn[j] = min(bMn[j], Smn[j]);
+                aMx[j] = max(bMx[j], Smx[j]);
+                bMn[j] = 0xFFFFu;
+                bMx[j] = 0;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) aM[j][w] |= S[j][w];
+                aMn[j] = min(aMn[j], Smn[j]);
+                aMx[j] = max(aMx[j], Smx[j]);
+                if (t == 3) {
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) bM[j][w] = S[j][w];
+                    bMn[j] = Smn[j];
+                    bMx[j] = Smx[j];
+                }
+            }
+        }
+    }
+    // the volume ends inside block-slice ze >> 2 (when it ends before the chunk's last apron
+    // slice): that block is complete now
+    if (ze < 4 * zb1) store_block(ze >> 2, aM, aMn, aMx);
+}
+
 size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
 template <typename T, int NW, int MODE>
@@ -529,6 +989,28 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     dim3 grid((g.gx + 31) / 32, (g.gy + kWarps - 1) / kWarps, (g.gz + p.zchunk - 1) / p.zchunk);
     const T* v = static_cast<const T*>(vol);
     cudaError_t e;
+    // 16-byte voxel loads: b = 4, apron 1, rows of whole 16-byte vectors, an aligned volume,
+    // and at most 4 mask words per lane (so that the per-lane state stays in registers)
+    constexpr int VL = 16 / int(sizeof(T));
+    constexpr bool kVecOk = sizeof(T) == 2 ? NW <= 2 : NW == 1;
+    if constexpr (kVecOk) {
+        const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
+        const size_t tab_bytes = align16(size_t(tab_n) * NW * 4);
+        if (g.b == 4 && g.a == 1 && g.X % VL == 0 &&
+            (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && tab_bytes <= kFpTabLimit) {
+            FpParams pv = p;
+            pv.zchunk = kVZChunk;
+            const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
+            const size_t rows = size_t(2) * kWarps * 5 * 32 * 16;
+            const size_t sm = tab_bytes + xb + rows;
+            dim3 gv((g.X / VL + 31) / 32, (g.gy + kWarps - 1) / kWarps,
+                    (g.gz + kVZChunk - 1) / kVZChunk);
+            e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE>>(int(sm));
+            if (e != cudaSuccess) return e;
+            return launch_pdl(k_pom_vec<T, NW, MODE>, gv, dim3(kWarps * 32), sm, s, v, pv, lut, cnt,
+                              mask, minmax, occ, tab_n);
+        }
+    }
     if (fast && g.a == 1) {
         const size_t xsm = size_t(2) * 2 * kWarps * (NW + 1) * 32 * 4;   // row exchange
         if constexpr (MODE == kModePom && NW <= 2) {

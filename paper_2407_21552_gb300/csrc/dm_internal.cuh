@@ -11,10 +11,8 @@
 namespace dmk {
 
 constexpr int kMaxPartitions = 256;
-constexpr int kLineTile = 16;         // columns per line-pass tile (bytes per row)
-constexpr int kMaxLevels = 9;         // sparse-table levels 0..8 cover windows up to 511
+constexpr int kLineTile = 32;         // lines per y / z pass tile (one thread each)
 constexpr int kLineSmemLimit = 200 * 1024;
-constexpr int kLineWideSmem = 72 * 1024;   // 32-column line tiles up to this table size
 constexpr int kXpassSmemLimit = 160 * 1024;
 
 // Partition borders as a by-value kernel parameter: v[p] is the lowest intensity of
@@ -247,23 +245,37 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
                            const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched update
-constexpr int kMaxBatch = 64;          // items per launch pair (descriptors as parameters)
+constexpr int kMaxBatch = 64;          // groups per launch pair (descriptors as parameters)
+constexpr int kMaxGroupEdits = 8;      // TFs of one volume that share their plane reads
 
-struct BatchDesc {
+// One volume and up to kMaxGroupEdits TFs for it.  list / emask / count: where the
+// active-set kernel leaves the group's planes (batch_list_entries(planes) entries each; for
+// E == 1 emask is not used).
+struct BatchGroup {
     const uint8_t* pdm;
     int64_t plane, G;
-    const float* tf;
-    uint8_t* out;
-    const uint8_t* lut;                // the item's partition table (its scratch)
-    uint16_t* act;                     // the item's active list and count (its scratch)
-    int32_t* nact;
+    const uint8_t* lut;                // the volume's partition table (its scratch)
+    uint16_t* list;
+    uint8_t* emask;
+    int32_t* count;
     int32_t N, K;
     int32_t J;                         // index levels (-1: no index)
+    int32_t E;
+    const float* tf[kMaxGroupEdits];
+    uint8_t* out[kMaxGroupEdits];
 };
 
-// Active sets of up to kMaxBatch items (one CTA each), then one combine over
-// all their work units (PDL); `ctas_per_sm` sizes the combine grid (<= 0: 24).
-cudaError_t launch_update_batch(const BatchDesc* items, int n, int ctas_per_sm, int num_sms,
-                                cudaStream_t s);
+struct BatchTuning {
+    int ctas_per_sm;                   // combine grid: CTAs per SM (<= 0: 24)
+    int loads_per_stage;               // plane loads per pipeline stage: 4 (default) or 8
+};
+
+// Entries of a group's plane list, padding included, for a buffer of `planes` planes.
+size_t batch_list_entries(int planes);
+
+// Active sets of up to kMaxBatch groups (one CTA each), then one combine over all their
+// work units (PDL).
+cudaError_t launch_update_batch(const BatchGroup* groups, int n, const BatchTuning& tune,
+                                int num_sms, cudaStream_t s);
 
 }  // namespace dmk

@@ -68,7 +68,9 @@ def cfg(**kw):
     (dict(num_partitions=4, borders=[0, 5, 5, 200, 256]), A.DM_ERR_INVALID_ARG),
     (dict(num_partitions=4, borders=[1, 5, 9, 200, 256]), A.DM_ERR_INVALID_ARG),
     (dict(num_partitions=4, borders=[0, 5, 9, 200, 255]), A.DM_ERR_INVALID_ARG),
-    (dict(dims=(4, 4, 4 * 2000)), A.DM_ERR_UNSUPPORTED),     # z lines beyond the tiling
+    (dict(dims=(4, 4, 4 * 2000)), A.DM_OK),                  # 2000-block z lines
+    (dict(dims=(4, 4, 4 * 5888)), A.DM_OK),                  # the longest line a tile holds
+    (dict(dims=(4, 4, 4 * 5889)), A.DM_ERR_UNSUPPORTED),     # z lines beyond the tiling
     (dict(dims=(1, 1, 1), block=1, apron=0, num_partitions=1, tf_size=2), A.DM_OK),
 ])
 def test_create_validation(kw, status):
@@ -228,3 +230,36 @@ def test_noalloc_wrapper_checks_the_border_count():
     for borders in ([0, 128, 256], [0, 64, 128, 192, 256, 256]):
         with pytest.raises(ValueError):
             A.dm_update_tf_noalloc(fake, 64, 64, 4, borders, 256, fake, fake, None)
+
+
+def test_workspace_batch_is_refused_on_the_host():
+    """dm_update_tf_batch_ws checks its workspace (present, 256-byte aligned, at least
+    dm_batch_workspace_bytes(n)) and then every item, before it launches; unlike
+    dm_update_tf_batch it accepts a context given twice (it fails here only because the
+    contexts were never built)."""
+    c, keep = cfg()
+    ctxs = [A.dm_create(c) for _ in range(2)]
+    lib = A.load()
+    fake = 1 << 20
+    per = A.dm_batch_workspace_bytes(1)
+    assert per > 0 and per % 256 == 0
+    assert A.dm_batch_workspace_bytes(5) == 5 * per and A.dm_batch_workspace_bytes(0) == 0
+    try:
+        for ctx in ctxs:
+            assert lib.dm_bind(ctx, ctypes.c_void_p(fake), ctypes.c_void_p(fake),
+                               ctypes.c_void_p(fake), ctypes.c_void_p(fake)) == A.DM_OK
+        items = [(ctxs[0], fake, fake + 4096), (ctxs[0], fake + 64, fake + 8192),
+                 (ctxs[1], fake + 128, fake + 12288)]
+        need = A.dm_batch_workspace_bytes(len(items))
+        for ws, size in ((None, need), (fake + 128, need), (fake, need - 1)):
+            with pytest.raises(A.DmError) as e:
+                A.dm_update_tf_batch_ws(items, None, ws, size, None)
+            assert e.value.status == A.DM_ERR_INVALID_ARG
+            assert "workspace" in str(e.value)
+        with pytest.raises(A.DmError) as e:               # repeated context: allowed
+            A.dm_update_tf_batch_ws(items, (12, 8), fake, need, None)
+        assert e.value.status == A.DM_ERR_NOT_BOUND
+        A.dm_update_tf_batch_ws([], None, None, 0, None)  # nothing to do
+    finally:
+        for ctx in ctxs:
+            A.dm_destroy(ctx)

@@ -186,3 +186,149 @@ def test_batch_rejects_repeated_context():
     out = torch.empty(eng.G, dtype=torch.uint8, device="cuda")
     with pytest.raises(A.DmError):
         A.dm_update_tf_batch([(eng.ctx, tf.data_ptr(), out.data_ptr())] * 2, None, _stream())
+
+
+def _ws(A, n):
+    nbytes = A.dm_batch_workspace_bytes(n)
+    return torch.empty(nbytes, dtype=torch.uint8, device="cuda"), nbytes
+
+
+def _oracle_pdms(items):
+    return [oracle.build_partitions(synth.as_numpy(vol), sp.get("b", 4), 1, sp["N"], sp["K"])[1]
+            for sp, vol, _ in items]
+
+
+@pytest.mark.parametrize("tuning", [None, (12, 8), (2, 4)])
+def test_batch_ws_several_edits_per_volume(tuning):
+    """dm_update_tf_batch_ws with repeated contexts: 6 volumes (one with the range index,
+    one of b = 3 so its rows take the byte paths) with 1, 2, 3, 5, 8 and 11 TF edits (11:
+    two groups of one context), interleaved in the item list, one output misaligned.  Every
+    output is the oracle's D' for its own TF and that of dm_update_tf alone."""
+    from paper_2407_21552_gb300 import _abi as A, DM_INDEX_RANGES
+    specs = _small_specs(6, 31)
+    specs[2]["index"] = DM_INDEX_RANGES
+    specs[4]["b"] = 3
+    items = _engines(specs)
+    pdms = _oracle_pdms(items)
+    counts = [1, 2, 3, 5, 8, 11]
+    order = [(v, k) for k in range(max(counts)) for v in range(6) if k < counts[v]]
+    tfs, outs, want = [], [], []
+    for j, (v, k) in enumerate(order):
+        sp, _, eng = items[v]
+        tf = T.tf_edit_sequence(900 + 13 * v + k, sp["N"], 2)[-1] if k % 4 else \
+            T.special_tfs(sp["N"], T.uniform_borders(sp["N"], sp["K"]))[k % 16]
+        tfs.append(torch.from_numpy(tf).cuda())
+        off = 1 if j == 7 else 0                          # one misaligned output
+        buf = torch.full((eng.G + 16,), 9, dtype=torch.uint8, device="cuda")
+        outs.append(buf[off: off + eng.G])
+        want.append(oracle.update_tf(pdms[v], tf)[0].reshape(-1))
+    ws, nbytes = _ws(A, len(order))
+    A.dm_update_tf_batch_ws([(items[v][2].ctx, tfs[j].data_ptr(), outs[j].data_ptr())
+                             for j, (v, _) in enumerate(order)], tuning, ws.data_ptr(), nbytes,
+                            _stream())
+    torch.cuda.synchronize()
+    for j, (v, k) in enumerate(order):
+        assert np.array_equal(outs[j].cpu().numpy(), want[j]), (v, k)
+        assert torch.equal(items[v][2].update_tf(tfs[j]), outs[j]), (v, k)
+
+
+def test_batch_graph_replay_with_new_tfs():
+    """Both batched calls captured once in a CUDA graph over fixed TF buffers, then replayed
+    with new TFs copied in: every replay gives the oracle's D' for the TFs of that replay."""
+    from paper_2407_21552_gb300 import _abi as A
+    items = _engines(_small_specs(9, 41))
+    pdms = _oracle_pdms(items)
+    NMAX = max(sp["N"] for sp, _, _ in items)
+    n = len(items)
+    tf_fixed = torch.zeros((n + 3, NMAX, 4), dtype=torch.float32, device="cuda")
+    outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in items]
+    outs_ws = [torch.empty(items[i if i < n else i - n][2].G, dtype=torch.uint8, device="cuda")
+               for i in range(n + 3)]
+    single = [(eng.ctx, tf_fixed[i].data_ptr(), outs[i].data_ptr())
+              for i, (_, _, eng) in enumerate(items)]
+    multi = single[:] + [(items[i][2].ctx, tf_fixed[n + i].data_ptr(), 0) for i in range(3)]
+    multi = [(c, t, outs_ws[i].data_ptr()) for i, (c, t, _) in enumerate(multi)]
+    ws, nbytes = _ws(A, len(multi))
+    pb1, pb2 = A.PreparedBatch(single), A.PreparedBatch(multi)
+    A.dm_update_tf_batch(pb1, None, _stream())           # warm-up outside the capture
+    A.dm_update_tf_batch_ws(pb2, None, ws.data_ptr(), nbytes, _stream())
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        A.dm_update_tf_batch(pb1, None, st)
+        A.dm_update_tf_batch_ws(pb2, None, ws.data_ptr(), nbytes, st)
+    for rep in range(3):
+        cur = []
+        for i in range(n + 3):
+            sp = items[i % n if i < n else i - n][0]
+            tf = T.tf_edit_sequence(5000 + 97 * rep + i, sp["N"], 1)[0]
+            tf_fixed[i].zero_()
+            tf_fixed[i, : sp["N"]] = torch.from_numpy(tf).cuda()
+            cur.append(tf)
+        graph.replay()
+        torch.cuda.synchronize()
+        for i in range(n):
+            want = oracle.update_tf(pdms[i], cur[i])[0].reshape(-1)
+            assert np.array_equal(outs[i].cpu().numpy(), want), (rep, i)
+        for i in range(n + 3):
+            v = i if i < n else i - n
+            want = oracle.update_tf(pdms[v], cur[i])[0].reshape(-1)
+            assert np.array_equal(outs_ws[i].cpu().numpy(), want), (rep, "ws", i)
+
+
+def test_batch_of_block_8_volumes():
+    """b = 8 (the autotuner's coarser choice) in a batch, against the oracle at b = 8."""
+    from paper_2407_21552_gb300 import _abi as A
+    specs = synth.batch_specs(seed=45, count=10, lo=20, hi=120)
+    for sp in specs:
+        sp["b"] = 8
+    items = _engines(specs)
+    pdms = _oracle_pdms(items)
+    tfs = [torch.from_numpy(T.tf_edit_sequence(60 + i, sp["N"], 2)[-1]).cuda()
+           for i, (sp, _, _) in enumerate(items)]
+    outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in items]
+    A.dm_update_tf_batch([(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr())
+                          for i, (_, _, eng) in enumerate(items)], (8, 8), _stream())
+    torch.cuda.synchronize()
+    for i in range(len(items)):
+        want = oracle.update_tf(pdms[i], tfs[i].cpu().numpy())[0].reshape(-1)
+        assert np.array_equal(outs[i].cpu().numpy(), want), i
+
+
+def test_autotuner_search_and_choice():
+    """The autotuner times every (block, CTAs per SM, loads per stage) of its search
+    space, stops at the first block size whose best schedule meets the target (b = 4 for a
+    target nothing misses), otherwise keeps the fastest schedule of all block sizes; the
+    chosen schedule's batch gives the oracle's D' at the chosen block size."""
+    from paper_2407_21552_gb300 import _abi as A
+    from paper_2407_21552_gb300.autotune import tune
+    base = synth.batch_specs(seed=47, count=6, lo=24, hi=80)
+    built = {}
+
+    def items_for(b):
+        if b not in built:
+            specs = [dict(sp, b=b) for sp in base]
+            its = _engines(specs)
+            tfs = [torch.from_numpy(T.tf_edit_sequence(70 + i, sp["N"], 1)[0]).cuda()
+                   for i, (sp, _, _) in enumerate(its)]
+            outs = [torch.empty(eng.G, dtype=torch.uint8, device="cuda") for _, _, eng in its]
+            built[b] = (its, tfs, outs)
+        its, tfs, outs = built[b]
+        return [(eng.ctx, tfs[i].data_ptr(), outs[i].data_ptr()) for i, (_, _, eng) in enumerate(its)]
+
+    cps, lps = (4, 24), (4, 8)
+    easy = tune(items_for, 1e12, reps=3, ctas_per_sm=cps, loads_per_stage=lps)
+    assert easy.block == 4 and set(easy.table) == {(4, c, k) for c in cps for k in lps}
+    hard = tune(items_for, 0.0, reps=3, ctas_per_sm=cps, loads_per_stage=lps)
+    assert set(hard.table) == {(b, c, k) for b in (4, 8) for c in cps for k in lps}
+    assert hard.p50_us == min(hard.table.values())
+    its, tfs, outs = built[hard.block]
+    for o in outs:
+        o.fill_(3)
+    A.dm_update_tf_batch(items_for(hard.block), hard.tuning, _stream())
+    torch.cuda.synchronize()
+    for i, (sp, vol, _) in enumerate(its):
+        pdm = oracle.build_partitions(synth.as_numpy(vol), hard.block, 1, sp["N"], sp["K"])[1]
+        want = oracle.update_tf(pdm, tfs[i].cpu().numpy())[0].reshape(-1)
+        assert np.array_equal(outs[i].cpu().numpy(), want), i

@@ -227,6 +227,40 @@ def test_ragged_configs(shape, b, a, N, K, dt, borders):
     eng.close()
 
 
+# b = 4, apron 1 with rows of whole 16-byte vectors: the footprint kernel with 16-byte
+# voxel loads (8 uint16 or 16 uint8 voxels, 2 or 4 blocks per lane).  Its edges: CTAs with
+# few active lanes, block rows and z chunks that the grid ends inside, volumes ending 0, 1,
+# 2 or 3 slices into their last block, one and two mask words, TF tables up to 64 KiB,
+# voxels above the TF domain (clamped on both sides), explicit borders.
+VEC_CASES = [
+    # shape (Z, Y, X), N, K, dtype, borders
+    ((23, 37, 72), 4096, 64, np.uint16, None),      # 9 lanes; 10 block rows; gz = 6
+    ((36, 64, 264), 4096, 48, np.uint16, None),     # 33 lanes: 2 CTAs in x; 2 z chunks
+    ((34, 30, 8), 1000, 20, np.uint16, None),       # one lane per CTA; Z ends at slice 1
+    ((33, 70, 48), 256, 32, np.uint8, None),        # 3 lanes of 16 voxels; Z ends at slice 0
+    ((17, 9, 32), 200, 16, np.uint8, None),         # N < 256: uint8 voxels clamped
+    ((8, 8, 16), 16, 4, np.uint16, None),           # tiny N: most voxels clamped
+    ((19, 41, 80), 8192, 64, np.uint16, None),      # the largest table (64 KiB)
+    ((21, 26, 96), 4096, 41, np.uint16,
+     [0, 1] + [int(v) for v in np.linspace(90, 4000, 39).astype(int)] + [4096]),
+]
+
+
+@pytest.mark.parametrize("shape,N,K,dt,borders", VEC_CASES)
+def test_vector_footprint_edges(shape, N, K, dt, borders):
+    rng = np.random.default_rng(sum(shape) * 11 + K)
+    vol = rand_volume(rng, shape, N, dt)
+    top = 0xFFFF if dt == np.uint16 else 0xFF
+    if N - 1 < top:
+        vol.reshape(-1)[::53] = min(top, N + 7)      # above the TF domain: treated as N - 1
+        vol.reshape(-1)[::211] = top
+    eng, vd, ref = check_build(vol, 4, 1, N, K, borders)
+    bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
+    tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 4) + T.special_tfs(N, bd)[:6]
+    check_updates(eng, vd, vol, ref, tfs, 4, 1, borders, exact_every=2)
+    eng.close()
+
+
 @pytest.mark.parametrize("shape", [(4 * 600, 8, 8), (8, 4 * 300, 8), (8, 8, 4 * 700)])
 def test_long_lines_clamp_at_255(shape):
     """One occupied corner; lines of 300-700 blocks need the 255 clamp on every axis."""
