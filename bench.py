@@ -791,13 +791,56 @@ def multi_edit_leg(engs, edits, specs, tr, flush, stream, n_edits, reps):
 
 
 # -------------------------------------------------------------------- serving workload
+def _open_loop(sch, n_sess, rate, n_req, tfs, rng):
+    """Poisson arrivals at `rate` edits/s over the sessions, uniformly chosen; returns the
+    wall time until every edit completed."""
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    sess = rng.integers(0, n_sess, size=n_req)
+    t0 = time.perf_counter()
+    k = 0
+    while k < n_req or sch.has_work():
+        now = time.perf_counter() - t0
+        while k < n_req and arrive[k] <= now:
+            sch.submit(int(sess[k]), tfs[k % len(tfs)], t_arrival=t0 + arrive[k])
+            k += 1
+        sch.poll()
+    return time.perf_counter() - t0
+
+
+def _serve_stats(sch, wall, rate):
+    lat = np.array(sch.stats.latencies) * 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
+            "offered_edits_per_s": rate, "batches": sch.stats.batches,
+            "mean_batch": float(np.mean(sch.stats.batch_sizes)),
+            "max_batch": int(np.max(sch.stats.batch_sizes))}
+
+
+def _knee(rows):
+    """The highest offered rate the server sustains (within 5 %) with p99 at most 4x the
+    p99 of the lowest rate; the rows after it have queues that grow."""
+    base = rows[0]["p99_ms"]
+    knee = rows[0]
+    for r in rows:
+        if r["sustained_edits_per_s"] >= 0.95 * r["offered_edits_per_s"] and r["p99_ms"] <= 4 * base:
+            knee = r
+    return {"offered_edits_per_s": knee["offered_edits_per_s"], "p50_ms": knee["p50_ms"],
+            "p99_ms": knee["p99_ms"], "sustained_edits_per_s": knee["sustained_edits_per_s"],
+            "mean_batch": knee["mean_batch"]}
+
+
 def run_serving(args, ws, rank, local):
     """32 sessions (12-bit volumes with sides U[256, 1024], K in {16, 32, 64}) admitted
     under a 150 GB HBM budget; TF edits arrive as a Poisson process over the sessions at
-    200, 1000 and 5000 edits/s.  The partitioned server batches them continuously onto 3
-    streams; the comparison server runs a full recompute per edit in the same loop.  A last
-    run serves 1000 edits/s under a budget of 40 % of the sessions' bytes, evicting idle
-    sessions to host memory and readmitting them for their next edit."""
+    200 .. 100000 edits/s.  Three servers in the same loop on 3 streams: the partitioned
+    one batching one edit per session per batch, the partitioned one batching up to 4 edits
+    per session (dm_update_tf_batch_ws: a session's edits share their plane reads), and a
+    full recompute per edit.  The knee of each (the highest rate it sustains with a p99
+    near its low-load p99) is reported.  Then: 1000 edits/s under a budget of 40 % of the
+    sessions' bytes, evicting idle sessions to host memory and readmitting them; and a
+    churn run where 48 sessions of b = 2 maps with K in {128, 256} (about 270 GB in all)
+    open over time under the 150 GB budget, their maps built at admission, each sending
+    20 edits and leaving once they completed, so that sessions wait for admission."""
     import torch
     import synth
     from paper_2407_21552_gb300 import DM_U16
@@ -822,36 +865,28 @@ def run_serving(args, ws, rank, local):
         engines.append(eng)
         s = eng.sizes
         specs.append(SessionSpec(sid, int(s.pdm_bytes + s.minmax_bytes + s.scratch_bytes
-                                          + 3 * s.out_bytes), dict(engine=eng)))
+                                          + 3 * 4 * s.out_bytes), dict(engine=eng)))
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     tfs = [torch.from_numpy(t).pin_memory() for t in synth.tf_edit_sequence(6, 4096, 256)]
-    results = {}
-    for rate in (200, 1000, 5000):
-        for mode in ("partitioned", "full"):
-            ex = DeviceExecutor(slots=3, mode=mode, device=dev)
-            sch = Scheduler(ex, budget, slots=3)
+    rates = (200, 1000, 5000, 20000, 50000, 100000)
+    servers = {"partitioned": ("partitioned", 1), "partitioned_4_per_session": ("partitioned", 4),
+               "full_recompute": ("full", 1)}
+    results, knees = {}, {}
+    for name, (mode, E) in servers.items():
+        rows = []
+        for rate in rates:
+            ex = DeviceExecutor(slots=3, mode=mode, device=dev, edits_per_session=E)
+            sch = Scheduler(ex, budget, slots=3, edits_per_session=E)
             for sp in specs:
                 sch.open_session(sp)
-            n_req = max(50, int(rate * args.serve_seconds))
-            gaps = rng.exponential(1.0 / rate, size=n_req)
-            arrive = np.cumsum(gaps)
-            sess = rng.integers(0, n_sess, size=n_req)
-            t0 = time.perf_counter()
-            k = 0
-            while k < n_req or sch.has_work():
-                now = time.perf_counter() - t0
-                while k < n_req and arrive[k] <= now:
-                    sch.submit(int(sess[k]), tfs[k % len(tfs)], t_arrival=t0 + arrive[k])
-                    k += 1
-                sch.poll()
-            wall = time.perf_counter() - t0
-            lat = np.array(sch.stats.latencies) * 1e3
-            results[f"{mode}@{rate}"] = {
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
-                "offered_edits_per_s": rate, "batches": sch.stats.batches,
-                "mean_batch": float(np.mean(sch.stats.batch_sizes))}
+            n_req = int(min(max(50, rate * args.serve_seconds), 20000))
+            wall = _open_loop(sch, n_sess, rate, n_req, tfs, rng)
+            rows.append(_serve_stats(sch, wall, rate))
+            for sp in specs:
+                sch.close_session(sp.sid)
+        results[name] = rows
+        knees[name] = _knee(rows)
     # eviction: a budget of 40 % of the sessions' device bytes; idle sessions' maps move
     # to pinned host memory and come back (no recompute) for their next edit
     ev_budget = int(0.4 * sum(sp.device_bytes for sp in specs))
@@ -860,42 +895,113 @@ def run_serving(args, ws, rank, local):
     sch = Scheduler(ex, ev_budget, slots=3, evict_idle=True)
     for sp in specs:
         sch.open_session(sp)
-    n_req = max(50, int(rate * args.serve_seconds))
-    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-    sess = rng.integers(0, n_sess, size=n_req)
     ev0, re0 = sch.stats.evictions, sch.stats.readmissions
-    t0 = time.perf_counter()
-    k = 0
-    while k < n_req or sch.has_work():
-        now = time.perf_counter() - t0
-        while k < n_req and arrive[k] <= now:
-            sch.submit(int(sess[k]), tfs[k % len(tfs)], t_arrival=t0 + arrive[k])
-            k += 1
-        sch.poll()
-    wall = time.perf_counter() - t0
-    lat = np.array(sch.stats.latencies) * 1e3
-    results[f"partitioned+evict@{rate}"] = {
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "edits": int(len(lat)), "sustained_edits_per_s": len(lat) / wall,
-        "offered_edits_per_s": rate, "batches": sch.stats.batches,
-        "mean_batch": float(np.mean(sch.stats.batch_sizes)),
-        "budget_gb": ev_budget / 1e9,
-        "evictions": sch.stats.evictions - ev0, "readmissions": sch.stats.readmissions - re0,
-        "evictions_at_open": ev0}
+    wall = _open_loop(sch, n_sess, rate, max(50, int(rate * args.serve_seconds)), tfs, rng)
+    evict = _serve_stats(sch, wall, rate)
+    evict.update({"budget_gb": ev_budget / 1e9, "evictions": sch.stats.evictions - ev0,
+                  "readmissions": sch.stats.readmissions - re0, "evictions_at_open": ev0})
     for e in engines:                             # every session resident again
         e.reload()
+    churn = serving_churn(dev, budget, rng, tfs)
     if rank != 0:
         return
     sides = [e.grid[0] * 4 for e in engines]
     res = {"metric": "serving: TF-update latency p50/p99 (ms) and sustained edits/s",
-           "value": results["partitioned@1000"]["p50_ms"], "unit": "ms", "n_gpus": ws,
+           "value": knees["partitioned"]["p50_ms"], "unit": "ms", "n_gpus": ws,
            "higher_is_better": False, "data": "synthetic",
            "config": {"workload": f"serving: {n_sess} sessions, 12-bit volumes with sides "
                                   f"{min(sides)}..{max(sides)}, K in {{16,32,64}}, 150 GB "
                                   f"budget, Poisson arrivals, 3 streams",
                       "resident_gb": sum(sp.device_bytes for sp in specs) / 1e9},
-           "servers": results}
+           "knee": knees, "servers": results, "eviction_at_40pct_budget": evict,
+           "churn_150gb_budget": churn}
     print(json.dumps(res))
+
+
+def serving_churn(dev, budget, rng, tfs, n_sess=48, edits=20, session_rate=20.0,
+                  edit_rate=200.0):
+    """Sessions that come and go under the HBM budget: `n_sess` sessions open as a Poisson
+    process (`session_rate` per s), each with b = 2 maps (K 128 or 256) of one of three
+    12-bit volumes (sides 384, 576 and 768 voxels), built at admission on a side stream;
+    each sends `edits` TF edits at `edit_rate` per s from its opening on (queued while it
+    waits for admission) and leaves once they all completed.  Reports admission waits and
+    edit latencies."""
+    import torch
+    import synth
+    from paper_2407_21552_gb300 import DM_U16, _abi as A
+    from paper_2407_21552_gb300.maps import PartitionedDistanceMaps
+    from paper_2407_21552_gb300.serving import DeviceExecutor, Scheduler, SessionSpec
+    sides = (384, 576, 768)
+
+    def session_bytes(side, K):
+        """Device bytes of a session as the library sizes them (no allocation)."""
+        cfg, keep = A.make_config((side, side, side), DM_U16, 2, 1, K, 4096)
+        ctx = A.dm_create(cfg)
+        sz = A.dm_query_sizes(ctx)
+        A.dm_destroy(ctx)
+        return int(sz.pdm_bytes + sz.minmax_bytes + sz.scratch_bytes + 3 * sz.out_bytes)
+    base = {s: synth.volume_of("u16", (s, s, s), 3000 + s, device=dev) for s in sides}
+    torch.cuda.synchronize(dev)
+    ex = DeviceExecutor(slots=3, mode="partitioned", device=dev)
+    sch = Scheduler(ex, budget, slots=3)
+    plan = []
+    t_open = np.cumsum(rng.exponential(1.0 / session_rate, size=n_sess))
+    for sid in range(n_sess):
+        side = int(rng.choice(sides))
+        K = int(rng.choice([128, 256]))
+        nbytes = session_bytes(side, K)
+
+        def build(stream, side=side, K=K):
+            with torch.cuda.stream(stream):
+                eng = PartitionedDistanceMaps((side, side, side), DM_U16, 2, 1, K, 4096,
+                                              device=dev)
+                eng.build_partitions(base[side], stream=stream)
+                eng.release_mask()
+            return eng, None
+        spec = SessionSpec(100 + sid, int(nbytes), dict(build=build))
+        times = t_open[sid] + np.arange(edits) / edit_rate
+        plan.append((spec, times))
+    events = sorted((t, i, k) for i, (_, times) in enumerate(plan) for k, t in enumerate(times))
+    opened, finished = set(), 0
+    fin = {}                                              # sid -> completed edits
+    seen = 0
+    t0 = time.perf_counter()
+    e = 0
+    while e < len(events) or sch.has_work() or finished < n_sess:
+        now = time.perf_counter() - t0
+        while e < len(events) and events[e][0] <= now:
+            t, i, k = events[e]
+            spec = plan[i][0]
+            if i not in opened:
+                sch.open_session(spec)
+                opened.add(i)
+            sch.submit(spec.sid, tfs[(7 * i + k) % len(tfs)], t_arrival=t0 + t)
+            e += 1
+        sch.poll()
+        for r in sch.completed[seen:]:                    # sessions done with their edits
+            fin[r.session] = fin.get(r.session, 0) + 1    # leave
+            if fin[r.session] == edits:
+                sch.close_session(r.session)
+                finished += 1
+        seen = len(sch.completed)
+    wall = time.perf_counter() - t0
+    del base
+    torch.cuda.empty_cache()
+    lat = np.array(sch.stats.latencies) * 1e3
+    waits = np.array(sch.stats.admission_waits) * 1e3
+    total = sum(sp.device_bytes for sp, _ in plan)
+    return {"sessions": n_sess, "edits": int(len(lat)), "wall_s": wall,
+            "budget_gb": budget / 1e9, "demand_gb": total / 1e9,
+            "max_resident_gb": sch.stats.max_used / 1e9,
+            "sessions_that_waited": int(sch.stats.rejected_waits),
+            "admission_wait_ms": {"p50": float(np.percentile(waits, 50)),
+                                  "p99": float(np.percentile(waits, 99)),
+                                  "max": float(waits.max())},
+            "edit_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                "p99": float(np.percentile(lat, 99))},
+            "sustained_edits_per_s": len(lat) / wall,
+            "maps": "b = 2, K in {128, 256}, volumes 384^3 / 576^3 / 768^3 12-bit, built "
+                    "at admission"}
 
 
 # ---------------------------------------------------------------- partition-count sweep

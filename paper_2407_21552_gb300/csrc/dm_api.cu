@@ -219,8 +219,13 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     uint8_t* pdm = static_cast<uint8_t*>(ctx->d_pdm);
     cudaError_t e = dmk::launch_partition_lut(lut, N, K, ctx->borders, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition table");
+    // uniform partitions of a power-of-two width: partition of intensity i = i >> shift
+    int shift = -1;
+    if (ctx->uniform_borders && N % K == 0 && ((N / K) & (N / K - 1)) == 0)
+        for (shift = 0; (1 << shift) < N / K; ++shift) {
+        }
     e = dmk::launch_pom_build(d_volume, ctx->geo, N, K, lut, static_cast<uint64_t*>(ctx->d_mask),
-                              ctx->d_minmax, 200 * 1024, s);
+                              ctx->d_minmax, shift, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "POM build");
     e = dmk::launch_xpass_mask(static_cast<const uint64_t*>(ctx->d_mask), K, ctx->geo, pdm, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM x pass");
@@ -365,7 +370,7 @@ dm_status dm_full_recompute(dm_ctx* ctx, const void* d_volume, const float* d_tf
                                           nullptr, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "visibility prefix");
     if (exact) {
-        e = dmk::launch_occ_exact(d_volume, ctx->geo, N, cnt, d_out, 200 * 1024, s);
+        e = dmk::launch_occ_exact(d_volume, ctx->geo, N, cnt, d_out, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "exact occupancy");
         e = dmk::launch_xpass_occ(d_out, ctx->geo, s);
     } else {

@@ -293,8 +293,8 @@ __host__ __device__ inline size_t sweep_tile_bytes(int L, int TC)
 // read waits inside a step; every step is the same branch-free sequence.
 constexpr int kRun = 8;
 
-template <int TC, bool FINAL>
-__device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, uint16_t* __restrict__ tab,
+template <int TC, bool FINAL, typename P>
+__device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __restrict__ tab,
                                            int L, int off, uint8_t* __restrict__ col,
                                            int64_t gstride)
 {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, uint16_t*
             const int r = r0 + dir * k;
             const int g = gv[i];
             const int pos = off + k;
-            tab[g * TC] = uint16_t(pos);
+            tab[g * TC] = P(pos);
             const int w = lv + 1;
             const int xw = g == w ? pos : x;                 // this step's own entry
             const bool drop = g <= lv;
@@ -330,16 +330,20 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, uint16_t*
 }
 
 // One tile = TC adjacent columns x one whole line of every column; thread c takes column c.
-// The tile is staged before any output is written, so the pass works in place.
-template <int TC>
+// The tile is staged before any output is written, so the pass works in place.  P, the
+// type of the table's positions: uint8_t for lines of at most 256 blocks (each sweep then
+// numbers its rows 0..L-1 from a cleared table), else uint16_t (the backward sweep's
+// positions follow the forward sweep's, so one clearing serves both).
+template <int TC, typename P>
 __global__ void __launch_bounds__(TC)
 k_line_sweep(uint8_t* buf, LineGeom lg)
 {
     extern __shared__ uint32_t s_mem[];
     constexpr int V = TC / 16;                               // 16-byte vectors per row
+    constexpr bool kShort = sizeof(P) == 1;
     const int L = lg.L;
     uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_mem);     // [L][TC]
-    uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_tile + sweep_tile_bytes(L, TC));  // [256][TC]
+    P* s_tab = reinterpret_cast<P*>(s_tile + sweep_tile_bytes(L, TC));   // [256][TC]
     pdl_wait();
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TC;
@@ -380,25 +384,32 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
             any_big |= (c < ncols) && (v >= 2);
         }
     }
-    // the table starts at position 0 everywhere: the forward sweep's T is >= 0 from its
-    // first row on, so these entries are never taken for a source
-    for (int i = tid; i < 256 * TC / 8; i += TC)
+    // the table starts at position 0 everywhere: a sweep's T is >= 0 from its first row on,
+    // so these entries are never taken for a source
+    constexpr int kTabVec = 256 * TC * int(sizeof(P)) / 16;
+    for (int i = tid; i < kTabVec; i += TC)
         reinterpret_cast<uint4*>(s_tab)[i] = make_uint4(0u, 0u, 0u, 0u);
     any_big = __syncthreads_or(any_big);
     any_not255 = __syncthreads_or(any_not255);
     if (!any_big || !any_not255) return;   // all values <= 1, or all 255: h == g
     if (tid >= ncols) return;               // no barrier follows
     uint8_t* tile = s_tile + tid;
-    uint16_t* tab = s_tab + tid;
+    P* tab = s_tab + tid;
     sweep_line<TC, false>(tile, tab, L, 0, nullptr, 0);
-    sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
+    if (kShort) {                           // clear this column's table again
+        for (int v = 0; v < 256; ++v) tab[v * TC] = P(0);
+        sweep_line<TC, true>(tile, tab, L, 0, base + tid, lg.s);
+    } else {
+        sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
+    }
 }
 
 }  // namespace
 
 size_t line_pass_smem(int L)
 {
-    return sweep_tile_bytes(L, kLineTile) + size_t(256) * kLineTile * sizeof(uint16_t);
+    const size_t pos_bytes = L <= 256 ? 1 : 2;
+    return sweep_tile_bytes(L, kLineTile) + size_t(256) * kLineTile * pos_bytes;
 }
 
 size_t xpass_smem(int gx, int K)
@@ -480,9 +491,14 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
     const size_t smem = line_pass_smem(lg.L);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
     dim3 grid((g.gx + TC - 1) / TC, lg.n_outer, P);
-    cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC>>(int(smem));
+    if (lg.L <= 256) {
+        cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC, uint8_t>>(int(smem));
+        if (e != cudaSuccess) return e;
+        return launch_pdl(k_line_sweep<TC, uint8_t>, grid, dim3(TC), smem, s, buf, lg);
+    }
+    cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC, uint16_t>>(int(smem));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_line_sweep<TC>, grid, dim3(TC), smem, s, buf, lg);
+    return launch_pdl(k_line_sweep<TC, uint16_t>, grid, dim3(TC), smem, s, buf, lg);
 }
 
 }  // namespace dmk

@@ -52,6 +52,7 @@ struct FpParams {
     int gx, gy, gz;
     int b, a, N, W64;
     int zchunk;                                // block-slices per CTA
+    int sh;                                    // uniform partitions of 2^sh intensities (else -1)
 };
 
 enum { kModePom = 0, kModeVis = 1 };
@@ -632,11 +633,39 @@ __device__ __forceinline__ void lane_footprint(const uint32_t (&core)[16 / sizeo
     }
 }
 
-// One voxel row of a lane: per-position parts from one 16-byte load `q` (already known to
-// lie in the volume when `ok`) and the edge voxel `ev` (lanes 0 / 31; 0xFFFFFFFF = none).
-template <typename T, int NW>
+// Shift by a register amount; amounts above 31 give 0 (PTX shl clamps the amount).
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t v, uint32_t n)
+{
+    uint32_t d;
+    asm("shl.b32 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(n));
+    return d;
+}
+
+// One voxel row of a lane: per-position parts from one 16-byte vector `q` (meaningful
+// when `ok`) and the edge voxel `ev` (lanes 0 / 31; 0xFFFFFFFF = none).  SHIFT: uniform
+// partitions of 2^sh intensities, the partition is the clamped intensity >> sh; otherwise
+// the one-hot mask (or visibility bit) comes from the shared-memory table.
+template <typename T, int NW, bool SHIFT>
+__device__ __forceinline__ void onehot_of(unsigned x, unsigned sh, const uint32_t* __restrict__ s_tab,
+                                          uint32_t (&m)[NW])
+{
+    if (SHIFT) {
+        const unsigned c = x >> sh;
+        m[0] = shl_clamped(1u, c);
+        if (NW > 1) m[NW - 1] = shl_clamped(1u, c - 32u);
+    } else if (NW == 2) {
+        const uint2 t2 = reinterpret_cast<const uint2*>(s_tab)[x];
+        m[0] = t2.x;
+        m[NW - 1] = t2.y;
+    } else {
+        m[0] = s_tab[x];
+    }
+}
+
+template <typename T, int NW, bool SHIFT>
 __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, uint32_t nmax2,
-                                         unsigned nmax, const uint32_t* __restrict__ s_tab,
+                                         unsigned nmax, unsigned sh,
+                                         const uint32_t* __restrict__ s_tab,
                                          uint32_t (&core)[16 / sizeof(T) / 4][NW],
                                          uint32_t (&first)[16 / sizeof(T) / 4][NW],
                                          uint32_t (&last)[16 / sizeof(T) / 4][NW],
@@ -659,15 +688,8 @@ __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, u
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int v = 4 * j + i;                       // voxel position in the lane
-                const unsigned x = Tr::get(wv[v / PW], v % PW);
                 uint32_t m[NW];
-                if constexpr (NW == 2) {
-                    const uint2 t2 = reinterpret_cast<const uint2*>(s_tab)[x];
-                    m[0] = t2.x;
-                    m[NW - 1] = t2.y;
-                } else {
-                    m[0] = s_tab[x];
-                }
+                onehot_of<T, NW, SHIFT>(Tr::get(wv[v / PW], v % PW), sh, s_tab, m);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
                     core[j][w] |= m[w];
@@ -682,8 +704,7 @@ __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, u
     }
     if (ev != 0xFFFFFFFFu) {
         const unsigned x = min(ev, nmax);
-#pragma unroll
-        for (int w = 0; w < NW; ++w) em[w] = s_tab[x * NW + w];
+        onehot_of<T, NW, SHIFT>(x, sh, s_tab, em);
         emn = x;
         emx = x;
     } else {
@@ -694,33 +715,38 @@ __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, u
     }
 }
 
-template <typename T, int NW, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+template <typename T, int NW, int MODE, bool SHIFT>
+__global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
 k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
           const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
-          uint8_t* __restrict__ occ, int tab_n)
+          uint8_t* __restrict__ occ, int tab_n, int sh)
 {
     using Tr = VTraits<T>;
     constexpr int VL = Tr::VL, BL = VL / 4;
     constexpr int XW = BL * (NW + 1);                          // words a lane publishes per row
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);       // [tab_n][NW]
+    uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);       // [tab_n][NW] (not SHIFT)
     uint32_t* s_x = reinterpret_cast<uint32_t*>(smem + align16(size_t(tab_n) * NW * 4));
     // s_x: [2 buffers][2 rows (first, last)][kWarps][XW][32 lanes]
     uint4* s_rows = reinterpret_cast<uint4*>(s_x + 2 * 2 * kWarps * XW * 32);
     // s_rows: [2 slices][kWarps][5 rows][32 lanes]: the voxel rows, copied one slice ahead
+    uint4* s_edge = s_rows + 2 * kWarps * 5 * 32;
+    // s_edge: [2 slices][kWarps][5 rows][2]: the 16-byte vectors holding the CTA's edge
+    // voxels (left of lane 0, right of lane 31), copied with the rows
     pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < tab_n; i += kWarps * 32) {
-        if (MODE == kModePom) {
-            const unsigned c = lut[i];
+    if (!SHIFT) {
+        for (int i = tid; i < tab_n; i += kWarps * 32) {
+            if (MODE == kModePom) {
+                const unsigned c = lut[i];
 #pragma unroll
-            for (int w = 0; w < NW; ++w) s_tab[i * NW + w] = ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
-        } else {
-            s_tab[i] = cnt[i + 1] > cnt[i] ? 1u : 0u;
+                for (int w = 0; w < NW; ++w) s_tab[i * NW + w] = ((c >> 5) == unsigned(w)) ? (1u << (c & 31)) : 0u;
+            } else {
+                s_tab[i] = cnt[i + 1] > cnt[i] ? 1u : 0u;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     const bool want_mm = MODE == kModePom && minmax != nullptr;
     const int X = p.X, Y = p.Y;
     const unsigned nmax = unsigned(p.N - 1);
@@ -783,150 +809,173 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
         }
     };
     // the rows of a slice: the 4 core rows and, for warps 0 / 7, the outer apron row
-    bool okr[5];
-    int64_t yoff[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        const int y = t < 4 ? y0 + t : yx;
-        okr[t] = (t < 4 || has_x) && y >= 0 && y < Y;             // warp-uniform
-        yoff[t] = int64_t(okr[t] ? y : 0) * rowX;
-    }
-    // copies of slice z's rows into buffer `bsel` (asynchronous, one group), and the edge
-    // voxels of lanes 0 / 31 into registers
-    auto fetch = [&](int z, int bsel, unsigned (&ev)[5]) {
+    auto row_y = [&](int t) { return t < 4 ? y0 + t : yx; };
+    auto row_ok = [&](int t) {                                 // warp-uniform
+        const int y = row_y(t);
+        return (t < 4 || has_x) && y >= 0 && y < Y;
+    };
+    // the 16-byte vector that holds the edge voxel of lane 0 (its last voxel) or lane 31
+    // (its first voxel): aligned, since rows are whole vectors
+    const int xev = lane == 0 ? xe - (VL - 1) : xe;
+    const int eslot = lane == 0 ? 0 : 1;
+    // copies of slice z's rows (and edge vectors) into buffer `bsel`, asynchronous, one group
+    auto fetch = [&](int z, int bsel) {
         const T* slice = vol + int64_t(z) * Y * rowX;
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-            if (okr[t] && lane_ok) {
+            const bool ok = row_ok(t);
+            const T* row = slice + int64_t(ok ? row_y(t) : 0) * rowX;
+            if (ok && lane_ok) {
                 const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
                     s_rows + ((bsel * kWarps + warp) * 5 + t) * 32 + lane));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
-                             "l"(slice + yoff[t] + xv0)
+                             "l"(row + xv0)
                              : "memory");
             }
-            ev[t] = (okr[t] && edge_ok) ? unsigned(__ldg(slice + yoff[t] + xe)) : 0xFFFFFFFFu;
+            if (ok && edge_ok) {
+                const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
+                    s_edge + ((bsel * kWarps + warp) * 5 + t) * 2 + eslot));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                             "l"(row + xev)
+                             : "memory");
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    unsigned ev_next[5];
-    fetch(zs, 0, ev_next);
+    fetch(zs, 0);
     for (int z = zs; z <= ze; ++z) {
         const int bsel = (z - zs) & 1;
-        unsigned ev[5];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) ev[t] = ev_next[t];
-        if (z < ze) fetch(z + 1, bsel ^ 1, ev_next);
+        if (z < ze) fetch(z + 1, bsel ^ 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");     // this lane's rows of z
-        uint4 q[5];
+        asm volatile("cp.async.wait_group 1;" ::: "memory");     // this lane's copies of z
+        const uint4* rows = s_rows + (bsel * kWarps + warp) * 5 * 32 + lane;
+        const uint4* edges = s_edge + (bsel * kWarps + warp) * 5 * 2 + eslot;
+        // the edge voxel of row t (lanes 0 / 31), else none
+        auto edge_of = [&](int t) -> unsigned {
+            if (!(row_ok(t) && edge_ok)) return 0xFFFFFFFFu;
+            const uint4 q = edges[t * 2];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+            return lane == 0 ? VTraits<T>::get(w[3], VTraits<T>::PER_WORD - 1)
+                             : VTraits<T>::get(w[0], 0);
+        };
+        // ---- the slice's footprint of every block of the lane, S: rows 0 and 3 (published
+        //      for the warps above and below), rows 1 and 2 combined position by position
+        //      first, the warp's own outer apron row, then the neighbours' rows
+        uint32_t S[BL][NW];
+        unsigned Smn[BL], Smx[BL];
 #pragma unroll
-        for (int t = 0; t < 5; ++t)
-            q[t] = (okr[t] && lane_ok) ? s_rows[((bsel * kWarps + warp) * 5 + t) * 32 + lane]
-                                       : make_uint4(0u, 0u, 0u, 0u);
-        // ---- per-row parts; rows 0 and 3 (and the apron row) keep their own footprints,
-        //      rows 1 and 2 are combined position by position first
-        uint32_t fp[3][BL][NW];                                 // row 0, row 3, rows 1-2
-        unsigned fmn[3][BL], fmx[3][BL];
-        uint32_t xfp[BL][NW];                                   // the outer apron row
-        unsigned xmn[BL], xmx[BL];
-        {
-            uint32_t core[BL][NW], first[BL][NW], last[BL][NW], em[NW], wv[4];
-            unsigned emn, emx;
-            uint32_t c12[BL][NW], f12[BL][NW], l12[BL][NW], e12[NW], mn12[4], mx12[4];
-            unsigned en12 = 0xFFFFu, ex12 = 0;
+        for (int j = 0; j < BL; ++j) {
 #pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                if (t == 4 && !has_x) break;                    // warp-uniform
-                lane_row<T, NW>(q[t], ev[t], okr[t] && lane_ok, nmax2, nmax, s_tab, core, first,
-                                last, em, emn, emx, wv);
-                if (t == 1) {
-#pragma unroll
-                    for (int j = 0; j < BL; ++j)
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) {
-                            c12[j][w] = core[j][w];
-                            f12[j][w] = first[j][w];
-                            l12[j][w] = last[j][w];
-                        }
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) e12[w] = em[w];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) { mn12[k] = wv[k]; mx12[k] = okr[t] && lane_ok ? wv[k] : 0u; }
-                    en12 = emn;
-                    ex12 = emx;
-                    continue;
-                }
-                if (t == 2) {
-#pragma unroll
-                    for (int j = 0; j < BL; ++j)
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) {
-                            c12[j][w] |= core[j][w];
-                            f12[j][w] |= first[j][w];
-                            l12[j][w] |= last[j][w];
-                        }
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) e12[w] |= em[w];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        mn12[k] = Tr::vmin(mn12[k], wv[k]);
-                        mx12[k] = Tr::vmax(mx12[k], okr[t] && lane_ok ? wv[k] : 0u);
-                    }
-                    en12 = min(en12, emn);
-                    ex12 = max(ex12, emx);
-                    lane_footprint<T, NW>(c12, f12, l12, e12, en12, ex12, mn12, mx12, lane, want_mm,
-                                          fp[2], fmn[2], fmx[2]);
-                    continue;
-                }
-                uint32_t wmx[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) wmx[k] = okr[t] && lane_ok ? wv[k] : 0u;
-                if (t == 4)
-                    lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm,
-                                          xfp, xmn, xmx);
-                else
-                    lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm,
-                                          fp[t == 0 ? 0 : 1], fmn[t == 0 ? 0 : 1], fmx[t == 0 ? 0 : 1]);
-            }
+            for (int w = 0; w < NW; ++w) S[j][w] = 0;
+            Smn[j] = 0xFFFFu;
+            Smx[j] = 0;
         }
-        // ---- publish rows 0 and 3 for the warps below and above
         const int buf = z & 1;
         uint32_t* xf = s_x + ((buf * 2 + 0) * kWarps + warp) * XW * 32 + lane;
         uint32_t* xl = s_x + ((buf * 2 + 1) * kWarps + warp) * XW * 32 + lane;
+        auto fold = [&](const uint32_t (&fp)[BL][NW], const unsigned (&fmn)[BL],
+                        const unsigned (&fmx)[BL]) {
 #pragma unroll
-        for (int j = 0; j < BL; ++j) {
+            for (int j = 0; j < BL; ++j) {
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                xf[(j * NW + w) * 32] = fp[0][j][w];
-                xl[(j * NW + w) * 32] = fp[1][j][w];
+                for (int w = 0; w < NW; ++w) S[j][w] |= fp[j][w];
+                Smn[j] = min(Smn[j], fmn[j]);
+                Smx[j] = max(Smx[j], fmx[j]);
             }
-            xf[(BL * NW + j) * 32] = fmn[0][j] | (fmx[0][j] << 16);
-            xl[(BL * NW + j) * 32] = fmn[1][j] | (fmx[1][j] << 16);
+        };
+        auto publish = [&](uint32_t* dst, const uint32_t (&fp)[BL][NW], const unsigned (&fmn)[BL],
+                           const unsigned (&fmx)[BL]) {
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) dst[(j * NW + w) * 32] = fp[j][w];
+                dst[(BL * NW + j) * 32] = fmn[j] | (fmx[j] << 16);
+            }
+        };
+        {
+            uint32_t core[BL][NW], first[BL][NW], last[BL][NW], em[NW], wv[4], wmx[4];
+            uint32_t fp[BL][NW];
+            unsigned emn, emx, fmn[BL], fmx[BL];
+            const unsigned sh = unsigned(p.sh);
+            // one row on its own: rows 0, 3 and the apron row
+            auto single = [&](int t) {
+                const bool ok = row_ok(t) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[t * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(t), ok,
+                                       nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wmx[k] = ok ? wv[k] : 0u;
+                lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm, fp,
+                                      fmn, fmx);
+            };
+            single(0);
+            publish(xf, fp, fmn, fmx);
+            fold(fp, fmn, fmx);
+            single(3);
+            publish(xl, fp, fmn, fmx);
+            fold(fp, fmn, fmx);
+            if (has_x) {                                        // warp-uniform
+                single(4);
+                fold(fp, fmn, fmx);
+            }
+            // rows 1 and 2, combined position by position before the footprint
+            uint32_t c12[BL][NW], f12[BL][NW], l12[BL][NW], e12[NW], mn12[4], mx12[4];
+            unsigned en12, ex12;
+            {
+                const bool ok = row_ok(1) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[1 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(1), ok,
+                                       nmax2, nmax, sh, s_tab, c12, f12, l12, e12, en12, ex12, mn12);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mx12[k] = ok ? mn12[k] : 0u;
+            }
+            {
+                const bool ok = row_ok(2) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[2 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(2), ok,
+                                       nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
+#pragma unroll
+                for (int j = 0; j < BL; ++j)
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        c12[j][w] |= core[j][w];
+                        f12[j][w] |= first[j][w];
+                        l12[j][w] |= last[j][w];
+                    }
+#pragma unroll
+                for (int w = 0; w < NW; ++w) e12[w] |= em[w];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    mn12[k] = Tr::vmin(mn12[k], wv[k]);
+                    mx12[k] = Tr::vmax(mx12[k], ok ? wv[k] : 0u);
+                }
+                en12 = min(en12, emn);
+                ex12 = max(ex12, emx);
+            }
+            lane_footprint<T, NW>(c12, f12, l12, e12, en12, ex12, mn12, mx12, lane, want_mm, fp,
+                                  fmn, fmx);
+            fold(fp, fmn, fmx);
         }
         __syncthreads();
-        // ---- the slice's footprint of every block of the lane
-        uint32_t S[BL][NW];
-        unsigned Smn[BL], Smx[BL];
-        const uint32_t* up = s_x + ((buf * 2 + 1) * kWarps + (warp > 0 ? warp - 1 : 0)) * XW * 32 + lane;
-        const uint32_t* dn = s_x + ((buf * 2 + 0) * kWarps + (warp < kWarps - 1 ? warp + 1 : 0)) * XW * 32 + lane;
+        // ---- the neighbours' rows: the last row of the warp above, the first of the one below
+        if (warp > 0) {
+            const uint32_t* up = s_x + ((buf * 2 + 1) * kWarps + warp - 1) * XW * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < BL; ++j) {
+            for (int j = 0; j < BL; ++j) {
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t a = warp > 0 ? up[(j * NW + w) * 32] : (okr[4] ? xfp[j][w] : 0u);
-                const uint32_t b = warp < kWarps - 1 ? dn[(j * NW + w) * 32] : (okr[4] ? xfp[j][w] : 0u);
-                S[j][w] = fp[0][j][w] | fp[1][j][w] | fp[2][j][w] | a | b;
+                for (int w = 0; w < NW; ++w) S[j][w] |= up[(j * NW + w) * 32];
+                const unsigned pa = up[(BL * NW + j) * 32];
+                Smn[j] = min(Smn[j], pa & 0xFFFFu);
+                Smx[j] = max(Smx[j], pa >> 16);
             }
-            unsigned mn = min(min(fmn[0][j], fmn[1][j]), fmn[2][j]);
-            unsigned mx = max(max(fmx[0][j], fmx[1][j]), fmx[2][j]);
-            const unsigned pa = warp > 0 ? up[(BL * NW + j) * 32]
-                                         : (okr[4] ? (xmn[j] | (xmx[j] << 16)) : 0xFFFFu);
-            const unsigned pb = warp < kWarps - 1 ? dn[(BL * NW + j) * 32]
-                                                  : (okr[4] ? (xmn[j] | (xmx[j] << 16)) : 0xFFFFu);
-            mn = min(mn, min(pa & 0xFFFFu, pb & 0xFFFFu));
-            mx = max(mx, max(pa >> 16, pb >> 16));
-            Smn[j] = mn;
-            Smx[j] = mx;
+        }
+        if (warp < kWarps - 1) {
+            const uint32_t* dn = s_x + ((buf * 2 + 0) * kWarps + warp + 1) * XW * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) S[j][w] |= dn[(j * NW + w) * 32];
+                const unsigned pb = dn[(BL * NW + j) * 32];
+                Smn[j] = min(Smn[j], pb & 0xFFFFu);
+                Smx[j] = max(Smx[j], pb >> 16);
+            }
         }
         // ---- z: slice z = 4 q + t belongs to block-slice q, to q - 1 when t == 0 and to
         //      q + 1 when t == 3
@@ -972,10 +1021,27 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
 
 size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
+template <typename T, int NW, int MODE, bool SHIFT>
+cudaError_t launch_pom_vec(const T* v, const FpParams& p, int tab_n, const uint8_t* lut,
+                           const int32_t* cnt, uint64_t* mask, void* minmax, uint8_t* occ,
+                           cudaStream_t s)
+{
+    constexpr int VL = 16 / int(sizeof(T));
+    const size_t tab_bytes = SHIFT ? 0 : align16(size_t(tab_n) * NW * 4);
+    const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
+    const size_t rows = size_t(2) * kWarps * 5 * (32 + 2) * 16;
+    const size_t sm = tab_bytes + xb + rows;
+    dim3 gv((p.X / VL + 31) / 32, (p.gy + kWarps - 1) / kWarps, (p.gz + p.zchunk - 1) / p.zchunk);
+    cudaError_t e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE, SHIFT>>(int(sm));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_pom_vec<T, NW, MODE, SHIFT>, gv, dim3(kWarps * 32), sm, s, v, p, lut, cnt,
+                      mask, minmax, occ, SHIFT ? 0 : tab_n, p.sh);
+}
+
 template <typename T, int NW, int MODE>
 cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const uint8_t* lut,
                         const int32_t* cnt, uint64_t* mask, void* minmax, uint8_t* occ,
-                        cudaStream_t s)
+                        int shift, cudaStream_t s)
 {
     FpParams p;
     p.X = g.X; p.Y = g.Y; p.Z = g.Z;
@@ -983,6 +1049,7 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     p.b = g.b; p.a = g.a; p.N = N;
     p.W64 = (K + 63) / 64;
     p.zchunk = 4;
+    p.sh = shift;
     const size_t smem = fp_smem(N, NW);
     const bool fast = g.b == 4 && ((reinterpret_cast<uintptr_t>(vol) & (4 * sizeof(T) - 1)) == 0) &&
                       ((int64_t(g.X) * sizeof(T)) % (4 * sizeof(T)) == 0) && (g.X % 4 == 0);
@@ -996,19 +1063,16 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     if constexpr (kVecOk) {
         const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
         const size_t tab_bytes = align16(size_t(tab_n) * NW * 4);
+        const bool shift_ok = MODE == kModePom && shift >= 0;
         if (g.b == 4 && g.a == 1 && g.X % VL == 0 &&
-            (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && tab_bytes <= kFpTabLimit) {
+            (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && (shift_ok || tab_bytes <= kFpTabLimit)) {
             FpParams pv = p;
             pv.zchunk = kVZChunk;
-            const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
-            const size_t rows = size_t(2) * kWarps * 5 * 32 * 16;
-            const size_t sm = tab_bytes + xb + rows;
-            dim3 gv((g.X / VL + 31) / 32, (g.gy + kWarps - 1) / kWarps,
-                    (g.gz + kVZChunk - 1) / kVZChunk);
-            e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE>>(int(sm));
-            if (e != cudaSuccess) return e;
-            return launch_pdl(k_pom_vec<T, NW, MODE>, gv, dim3(kWarps * 32), sm, s, v, pv, lut, cnt,
-                              mask, minmax, occ, tab_n);
+            if constexpr (MODE == kModePom)
+                if (shift_ok)
+                    return launch_pom_vec<T, NW, MODE, true>(v, pv, tab_n, lut, cnt, mask, minmax,
+                                                             occ, s);
+            return launch_pom_vec<T, NW, MODE, false>(v, pv, tab_n, lut, cnt, mask, minmax, occ, s);
         }
     }
     if (fast && g.a == 1) {
@@ -1042,15 +1106,15 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
 
 template <typename T>
 cudaError_t launch_pom_t(const void* vol, const Geometry& g, int N, int K, const uint8_t* lut,
-                         uint64_t* mask, void* minmax, cudaStream_t s)
+                         uint64_t* mask, void* minmax, int shift, cudaStream_t s)
 {
     if (K <= 32)
-        return launch_fp_t<T, 1, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+        return launch_fp_t<T, 1, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, shift, s);
     if (K <= 64)
-        return launch_fp_t<T, 2, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+        return launch_fp_t<T, 2, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, shift, s);
     if (K <= 128)
-        return launch_fp_t<T, 4, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
-    return launch_fp_t<T, 8, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, s);
+        return launch_fp_t<T, 4, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, shift, s);
+    return launch_fp_t<T, 8, kModePom>(vol, g, N, K, lut, nullptr, mask, minmax, nullptr, shift, s);
 }
 
 }  // namespace
@@ -1062,21 +1126,21 @@ cudaError_t launch_partition_lut(uint8_t* lut, int N, int K, const Borders& bd, 
 }
 
 cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
-                             const uint8_t* lut, uint64_t* mask, void* minmax,
-                             size_t smem_limit, cudaStream_t s)
+                             const uint8_t* lut, uint64_t* mask, void* minmax, int shift,
+                             cudaStream_t s)
 {
-    (void)smem_limit;
-    if (g.bpv == 1) return launch_pom_t<uint8_t>(vol, g, N, K, lut, mask, minmax, s);
-    return launch_pom_t<uint16_t>(vol, g, N, K, lut, mask, minmax, s);
+    if (g.bpv == 1) return launch_pom_t<uint8_t>(vol, g, N, K, lut, mask, minmax, shift, s);
+    return launch_pom_t<uint16_t>(vol, g, N, K, lut, mask, minmax, shift, s);
 }
 
 cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const int32_t* cnt,
-                             uint8_t* occ, size_t smem_limit, cudaStream_t s)
+                             uint8_t* occ, cudaStream_t s)
 {
-    (void)smem_limit;
     if (g.bpv == 1)
-        return launch_fp_t<uint8_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ, s);
-    return launch_fp_t<uint16_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ, s);
+        return launch_fp_t<uint8_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ,
+                                                 -1, s);
+    return launch_fp_t<uint16_t, 1, kModeVis>(vol, g, N, 1, nullptr, cnt, nullptr, nullptr, occ,
+                                              -1, s);
 }
 
 }  // namespace dmk

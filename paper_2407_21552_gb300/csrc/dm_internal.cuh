@@ -192,14 +192,16 @@ cudaError_t launch_partition_lut(uint8_t* lut, int N, int K, const Borders& bd,
                                  cudaStream_t s);
 
 // POM bit masks [G][W] (+ block footprint min/max pairs when minmax != nullptr).
+// shift >= 0: the partitions are uniform with 2^shift intensities each (partition of
+// intensity i = i >> shift), which the kernels may use instead of the table; else -1.
 cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
-                             const uint8_t* lut, uint64_t* mask, void* minmax,
-                             size_t smem_limit, cudaStream_t s);
+                             const uint8_t* lut, uint64_t* mask, void* minmax, int shift,
+                             cudaStream_t s);
 
 // Exact TF occupancy per block (1 byte, 0/1) from a per-voxel visibility test over the
 // footprint; visibility of intensity i is cnt[i+1] > cnt[i].
 cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const int32_t* cnt,
-                             uint8_t* occ, size_t smem_limit, cudaStream_t s);
+                             uint8_t* occ, cudaStream_t s);
 
 // ---------------------------------------------------------------- distance transform
 // x pass: 1D distance along x to the nearest occupied block, saturating at 255.

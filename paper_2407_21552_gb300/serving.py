@@ -17,10 +17,19 @@ on the device): their maps move to host memory and their budget is freed.  An ev
 session stays open; its next edit queues it for readmission, which copies the maps back
 without recomputing them (the PDMs depend on the volume only, §3.1).
 
+Edits may be submitted to a session still waiting for admission; they run once it is
+admitted, and the time each session waited for admission is recorded.  With
+`edits_per_session` > 1 a batch takes up to that many of a session's oldest edits at once
+(the executor then combines them reading each map plane once); a session still has at
+most one batch on the device.  A session's maps can also be built at admission (the
+executor's payload gives a builder): the build is queued on a side stream and the
+session's first batch waits for it on the device.
+
 The scheduler (`Scheduler`) holds no GPU state and is tested with a fake executor; the
 executor for the GPU (`DeviceExecutor`) does every step through libdm: the host TFs are
 copied to each session's device TF buffer on the slot's stream, then one
-dm_update_tf_batch (or, for the comparison server, one dm_full_recompute per edit).
+dm_update_tf_batch, or dm_update_tf_batch_ws when a session has several edits in the batch
+(or, for the comparison server, one dm_full_recompute per edit).
 """
 from __future__ import annotations
 
@@ -65,21 +74,26 @@ class Stats:
     cancelled: int = 0
     evictions: int = 0
     readmissions: int = 0
+    admission_waits: list = field(default_factory=list)   # open -> admitted, per session
+    max_used: int = 0
 
 
 class Scheduler:
-    """Admission by budget, per-session FIFO, at most one edit of a session on the device
-    at a time, a fixed number of batches in flight.  `executor` provides admit(spec), release(sid),
+    """Admission by budget, per-session FIFO, at most one batch of a session on the device
+    at a time (holding up to `edits_per_session` of its edits), a fixed number of batches
+    in flight.  `executor` provides admit(spec), release(sid),
     launch(slot, requests) -> handle, done(handle) -> bool, and clock() -> seconds; with
     `evict_idle`, also evict(sid) and readmit(spec)."""
 
     def __init__(self, executor, budget_bytes: int, slots: int = 2, max_batch: int = 64,
-                 evict_idle: bool = False):
+                 evict_idle: bool = False, edits_per_session: int = 1):
         self.ex = executor
         self.budget = int(budget_bytes)
         self.slots = int(slots)
         self.max_batch = int(max_batch)
         self.evict_idle = bool(evict_idle)
+        self.edits_per_session = max(1, int(edits_per_session))
+        self.t_open = {}                       # sid -> clock at open (until admitted)
         self.used = 0
         self.sessions = {}                     # sid -> spec (admitted)
         self.evicted = {}                      # sid -> spec (open, maps on the host)
@@ -100,6 +114,7 @@ class Scheduler:
         it; returns whether admitted."""
         if spec.device_bytes > self.budget:
             raise ValueError(f"session {spec.sid} needs more than the whole budget")
+        self.t_open[spec.sid] = self.ex.clock()
         if not self.waiting and self._room_for(spec.device_bytes):
             self._admit(spec)
             return True
@@ -115,8 +130,12 @@ class Scheduler:
         else:
             self.ex.admit(spec)
             self.stats.admitted.append(spec.sid)
+            t0 = self.t_open.pop(spec.sid, None)
+            if t0 is not None:
+                self.stats.admission_waits.append(self.ex.clock() - t0)
         self.sessions[spec.sid] = spec
         self.used += spec.device_bytes
+        self.stats.max_used = max(self.stats.max_used, self.used)
         self.last_use[spec.sid] = self._uses
 
     def _idle(self, sid) -> bool:
@@ -157,6 +176,11 @@ class Scheduler:
             raise RuntimeError("session has edits in flight")
         self.pending.pop(sid, None)
         self.last_use.pop(sid, None)
+        if sid not in self.sessions and sid not in self.evicted:
+            if not self.withdraw_waiting(sid):  # never admitted: just leave the queue
+                raise KeyError(f"session {sid} is not open")
+            self.t_open.pop(sid, None)
+            return
         if sid in self.evicted:                 # maps on the host: nothing on the device
             self.evicted.pop(sid)
             self.waiting = collections.deque(sp for sp in self.waiting if sp.sid != sid)
@@ -169,10 +193,11 @@ class Scheduler:
 
     # ------------------------------------------------------------------ requests
     def submit(self, sid: int, tf, t_arrival: float | None = None) -> Request:
-        """Queue an edit of an admitted session, or of an evicted one (which then waits
-        for readmission)."""
-        if sid not in self.sessions and sid not in self.evicted:
-            raise KeyError(f"session {sid} is not admitted")
+        """Queue an edit of an admitted session, of one still waiting for admission, or of
+        an evicted one (which then waits for readmission)."""
+        if sid not in self.sessions and sid not in self.evicted and \
+                all(sp.sid != sid for sp in self.waiting):
+            raise KeyError(f"session {sid} is not open")
         if sid in self.evicted and all(sp.sid != sid for sp in self.waiting):
             self.waiting.append(self.evicted[sid])
         r = Request(session=sid, tf=tf,
@@ -242,7 +267,9 @@ class Scheduler:
             reqs = []
             for sid, q in self.pending.items():
                 if q and sid not in self.busy and sid in self.sessions:
-                    reqs.append(q.popleft())
+                    for _ in range(min(len(q), self.edits_per_session,
+                                       self.max_batch - len(reqs))):
+                        reqs.append(q.popleft())
                     if len(reqs) == self.max_batch:
                         break
             if not reqs:
@@ -261,8 +288,8 @@ class Scheduler:
             self.stats.batches += 1
             self.stats.batch_sizes.append(len(reqs))
             # rotate so that sessions with many pending edits do not starve the others
-            for r in reqs:
-                self.pending.move_to_end(r.session)
+            for sid in dict.fromkeys(r.session for r in reqs):
+                self.pending.move_to_end(sid)
 
     def drain(self, timeout_s: float = 60.0):
         t0 = time.perf_counter()
@@ -274,13 +301,17 @@ class Scheduler:
 
 class DeviceExecutor:
     """Runs batches through libdm on one device.  payload of a SessionSpec: dict with
-    'engine' (maps.PartitionedDistanceMaps, built) and optionally 'volume'."""
+    'engine' (maps.PartitionedDistanceMaps, built) and optionally 'volume'; or, for maps
+    built at admission, 'build': a callable(stream) that creates the engine, queues its
+    precompute on `stream` and returns (engine, volume or None)."""
 
-    def __init__(self, slots: int = 2, mode: str = "partitioned", device="cuda"):
+    def __init__(self, slots: int = 2, mode: str = "partitioned", device="cuda",
+                 edits_per_session: int = 1, max_batch: int = 64):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.mode = mode                      # "partitioned" or "full"
+        self.edits_per_session = max(1, int(edits_per_session))
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         # one completion event per slot: a slot takes a new batch only after its last one
         # completed, so the event is free to record again
@@ -290,22 +321,41 @@ class DeviceExecutor:
         self.side = torch.cuda.Stream(device=self.device)   # eviction / readmission copies
         self.results = {}                     # rid -> device D' (kept if keep_results)
         self.keep_results = False
+        self.ws = None                        # per-slot workspaces of the several-edit batch
+        if self.edits_per_session > 1 and mode == "partitioned":
+            from . import _abi as A
+            self.ws_bytes = A.dm_batch_workspace_bytes(max_batch)
+            self.ws = [torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+                       for _ in range(slots)]
 
     def clock(self):
         return time.perf_counter()
 
     def admit(self, spec):
-        eng = spec.payload["engine"]
         torch = self.torch
-        tf_dev = torch.empty((eng.N, 4), dtype=torch.float32, device=self.device)
-        outs = [torch.empty(eng.G, dtype=torch.uint8, device=self.device)
-                for _ in range(len(self.streams))]
-        self.sessions[spec.sid] = dict(engine=eng, tf=[tf_dev.clone() for _ in self.streams],
-                                       out=outs, volume=spec.payload.get("volume"))
-
+        volume = spec.payload.get("volume")
+        if "build" in spec.payload:           # maps built now, on the side stream
+            eng, volume = spec.payload["build"](self.side)
+            ready = torch.cuda.Event()
+            ready.record(self.side)
+            eng.ready_event = ready
+            spec.payload["engine"] = eng
+        eng = spec.payload["engine"]
+        E = self.edits_per_session
+        self.sessions[spec.sid] = dict(
+            engine=eng, volume=volume, spec=spec,
+            tf=[[torch.empty((eng.N, 4), dtype=torch.float32, device=self.device)
+                 for _ in range(E)] for _ in self.streams],
+            out=[[torch.empty(eng.G, dtype=torch.uint8, device=self.device) for _ in range(E)]
+                 for _ in self.streams])
     def release(self, sid):
-        self.sessions.pop(sid, None)
+        """The session left (nothing of it pending or on the device): maps built at
+        admission are dropped, so their device memory goes back to torch's allocator."""
+        s = self.sessions.pop(sid, None)
         self.evicted.pop(sid, None)
+        if s is not None and "build" in s["spec"].payload:
+            s["spec"].payload.pop("engine", None)
+            s["engine"].close()
 
     def evict(self, sid):
         """Maps to pinned host memory, device buffers freed once the copy has run (the
@@ -326,27 +376,35 @@ class DeviceExecutor:
         from . import _abi as A
         torch = self.torch
         st = self.streams[slot]
-        items = []
+        items, outs, used = [], [], {}
         with torch.cuda.stream(st):
             for r in requests:
                 s = self.sessions[r.session]
                 eng = s["engine"]
-                if eng.ready_event is not None:       # readmitted: its maps are in transit
+                if eng.ready_event is not None:       # built or readmitted: maps in transit
                     st.wait_event(eng.ready_event)
                     if eng.ready_event.query():
                         eng.ready_event = None
-                s["tf"][slot].copy_(r.tf, non_blocking=True)
-                items.append((s["engine"].ctx, s["tf"][slot].data_ptr(), s["out"][slot].data_ptr()))
+                e = used.get(r.session, 0)            # the request's place in its session
+                used[r.session] = e + 1
+                tf, out = s["tf"][slot][e], s["out"][slot][e]
+                tf.copy_(r.tf, non_blocking=True)
+                items.append((eng.ctx, tf.data_ptr(), out.data_ptr()))
+                outs.append(out)
             sh = ctypes.c_void_p(st.cuda_stream)
             if self.mode == "partitioned":
-                A.dm_update_tf_batch(items, None, sh)
+                if any(v > 1 for v in used.values()):
+                    A.dm_update_tf_batch_ws(items, None, self.ws[slot].data_ptr(),
+                                            self.ws_bytes, sh)
+                else:
+                    A.dm_update_tf_batch(items, None, sh)
             else:
                 for r, (ctx, tfp, outp) in zip(requests, items):
                     v = self.sessions[r.session]["volume"]
                     A.dm_full_recompute(ctx, v.data_ptr() if v is not None else None, tfp, outp, sh)
             if self.keep_results:
-                for r in requests:
-                    self.results[r.rid] = self.sessions[r.session]["out"][slot].clone()
+                for r, out in zip(requests, outs):
+                    self.results[r.rid] = out.clone()
             ev = self.events[slot]
             ev.record(st)
         return ev

@@ -348,3 +348,59 @@ def test_random_workload_with_eviction_keeps_invariants(seed):
         order = [tf for h in ex.launched for s, tf in h["reqs"] if s == sid]
         assert order == [r.tf for r in ran]
     assert sch.stats.evictions > 0 and sch.stats.readmissions > 0
+
+
+def test_edits_of_a_waiting_session_run_after_admission():
+    """Edits may be submitted to a session that waits for admission: they stay queued,
+    none reaches the device, and once a session leaves and frees budget the waiting one is
+    admitted and its edits run in order; the admission wait is recorded."""
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=2)
+    assert s.open_session(SessionSpec(0, 8))
+    ex.t = 1.0
+    assert not s.open_session(SessionSpec(1, 5))        # waits
+    s.submit(1, "w0")
+    s.submit(1, "w1")
+    s.poll()
+    assert ex.launched == [] and s.has_work()
+    ex.t = 4.0
+    s.close_session(0)                                  # frees the budget: 1 is admitted
+    assert ex.admitted == [0, 1] and s.stats.admission_waits == [0.0, 3.0]
+    s.poll()
+    assert [h["reqs"] for h in ex.launched] == [[(1, "w0")]]
+    with pytest.raises(KeyError):
+        s.submit(7, "x")                                # never opened
+
+
+def test_several_edits_per_session_in_one_batch():
+    """With edits_per_session = 3 a batch takes up to three of a session's oldest edits,
+    in order, and the session stays out of further batches until it completes."""
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=2, max_batch=5, edits_per_session=3)
+    for sid in range(2):
+        s.open_session(SessionSpec(sid, 1))
+    for k in range(5):
+        s.submit(0, f"a{k}")
+    s.submit(1, "b0")
+    s.submit(1, "b1")
+    s.poll()
+    assert ex.launched[0]["reqs"] == [(0, "a0"), (0, "a1"), (0, "a2"), (1, "b0"), (1, "b1")]
+    assert len(ex.launched) == 1                        # both sessions on the device
+    ex.launched[0]["done"] = True
+    s.poll()
+    assert ex.launched[1]["reqs"] == [(0, "a3"), (0, "a4")]
+    ex.launched[1]["done"] = True
+    s.drain()
+    assert [r.tf for r in s.completed] == ["a0", "a1", "a2", "b0", "b1", "a3", "a4"]
+
+
+def test_closing_a_session_that_never_was_admitted():
+    ex = FakeExec()
+    s = Scheduler(ex, budget_bytes=10, slots=1)
+    s.open_session(SessionSpec(0, 10))
+    s.open_session(SessionSpec(1, 4))
+    s.submit(1, "x")
+    s.close_session(1)                                  # leaves the queue, edits dropped
+    assert not s.waiting and not s.has_work() and ex.admitted == [0]
+    with pytest.raises(KeyError):
+        s.close_session(1)
