@@ -11,7 +11,8 @@
 // x pass: a row's occupancy becomes one bit line per partition in shared memory (the
 // K-map pass transposes each warp's 32 blocks x 32 partitions bit matrix with shuffles;
 // the one-map pass takes one ballot per 32 blocks); for every 32-bit word the nearest set
-// bit left of it and right of it are precomputed.  The K-map pass gives each thread 16
+// bit left of it and right of it are precomputed (in the K-map pass by segmented warp
+// scans, one lane per word, for rows of up to 32 words).  The K-map pass gives each thread 16
 // consecutive blocks of one bit line: their left and right neighbours' nearest bits come
 // from the rest of the word or those tables, two 16-step scans give the 16 distances, and
 // one 16-byte store writes them.  The one-map pass (full recompute) takes one masked
@@ -146,8 +147,37 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
             }
         }
         __syncthreads();
-        for (int q = tid; q < np; q += kThreads)
-            nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
+        if (nw <= 32) {
+            // all warps: lines of gw lanes (one word each, gw = nw rounded up to a power of
+            // two), the nearest set bit left / right of each word by a max / min scan
+            int gw = 1;
+            while (gw < nw) gw <<= 1;
+            const int lpw = 32 / gw;                         // lines per warp and step
+            for (int q0 = warp * lpw; q0 < np; q0 += (kThreads / 32) * lpw) {
+                const int q = q0 + lane / gw, wd = lane % gw;
+                const bool valid = q < np && wd < nw;
+                const uint32_t b = valid ? s_bits[q * nw + wd] : 0u;
+                int lb = b ? wd * 32 + 31 - __clz(b) : kNone;  // last set bit of the word
+                int fb = b ? wd * 32 + __ffs(b) - 1 : kFar;    // first set bit of the word
+                for (int d = 1; d < gw; d <<= 1) {
+                    const int u = __shfl_up_sync(0xFFFFFFFFu, lb, d, gw);
+                    const int v = __shfl_down_sync(0xFFFFFFFFu, fb, d, gw);
+                    if (wd >= d) lb = max(lb, u);
+                    if (wd + d < gw) fb = min(fb, v);
+                }
+                int pv = __shfl_up_sync(0xFFFFFFFFu, lb, 1, gw);
+                int nx = __shfl_down_sync(0xFFFFFFFFu, fb, 1, gw);
+                if (wd == 0) pv = kNone;
+                if (wd == gw - 1) nx = kFar;
+                if (valid) {
+                    s_prev[q * nw + wd] = int16_t(pv);
+                    s_next[q * nw + wd] = int16_t(nx);
+                }
+            }
+        } else {
+            for (int q = tid; q < np; q += kThreads)
+                nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
+        }
         __syncthreads();
         for (int it = tid; it < np * nh; it += kThreads) {
             const int q = it / nh, hw = it - q * nh;
@@ -276,8 +306,8 @@ struct LineGeom {
     int vec_ok;         // rows of kLineTile columns are 16-byte aligned and full
 };
 
-// Bytes of shared memory of a tile: the lines' values [L][TC] and the table of last
-// positions [256][TC] (uint16).
+// Bytes of shared memory of a tile's values [L][TC]; the table of last positions
+// [257][TC] follows.
 __host__ __device__ inline size_t sweep_tile_bytes(int L, int TC)
 {
     return (size_t(L) * TC + 15) / 16 * 16;
@@ -322,7 +352,7 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __rest
             const bool rise = !drop && pos - T > lv;
             T = drop ? pos : (rise ? max(T, xw) : T);
             lv = drop ? g : (rise ? w : lv);
-            x = tab[min(lv + 1, 255) * TC];                  // for the next step
+            x = tab[(lv + 1) * TC];                          // for the next step
             if (FINAL) col[int64_t(r) * gstride] = uint8_t(lv);
             else tile[r * TC] = uint8_t(lv);
         }
@@ -343,7 +373,7 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
     constexpr bool kShort = sizeof(P) == 1;
     const int L = lg.L;
     uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_mem);     // [L][TC]
-    P* s_tab = reinterpret_cast<P*>(s_tile + sweep_tile_bytes(L, TC));   // [256][TC]
+    P* s_tab = reinterpret_cast<P*>(s_tile + sweep_tile_bytes(L, TC));   // [257][TC]
     pdl_wait();
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TC;
@@ -385,8 +415,9 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
         }
     }
     // the table starts at position 0 everywhere: a sweep's T is >= 0 from its first row on,
-    // so these entries are never taken for a source
-    constexpr int kTabVec = 256 * TC * int(sizeof(P)) / 16;
+    // so these entries are never taken for a source.  Entry 256 (level 255 + 1) is read but
+    // never written.
+    constexpr int kTabVec = 257 * TC * int(sizeof(P)) / 16;
     for (int i = tid; i < kTabVec; i += TC)
         reinterpret_cast<uint4*>(s_tab)[i] = make_uint4(0u, 0u, 0u, 0u);
     any_big = __syncthreads_or(any_big);
@@ -409,7 +440,7 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
 size_t line_pass_smem(int L)
 {
     const size_t pos_bytes = L <= 256 ? 1 : 2;
-    return sweep_tile_bytes(L, kLineTile) + size_t(256) * kLineTile * pos_bytes;
+    return sweep_tile_bytes(L, kLineTile) + size_t(257) * kLineTile * pos_bytes;
 }
 
 size_t xpass_smem(int gx, int K)
