@@ -11,8 +11,7 @@
 // x pass: a row's occupancy becomes one bit line per partition in shared memory (the
 // K-map pass transposes each warp's 32 blocks x 32 partitions bit matrix with shuffles;
 // the one-map pass takes one ballot per 32 blocks); for every 32-bit word the nearest set
-// bit left of it and right of it are precomputed (in the K-map pass by segmented warp
-// scans, one lane per word, for rows of up to 32 words).  The K-map pass gives each thread 16
+// bit left of it and right of it are precomputed.  The K-map pass gives each thread 16
 // consecutive blocks of one bit line: their left and right neighbours' nearest bits come
 // from the rest of the word or those tables, two 16-step scans give the 16 distances, and
 // one 16-byte store writes them.  The one-map pass (full recompute) takes one masked
@@ -147,37 +146,8 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
             }
         }
         __syncthreads();
-        if (nw <= 32) {
-            // all warps: lines of gw lanes (one word each, gw = nw rounded up to a power of
-            // two), the nearest set bit left / right of each word by a max / min scan
-            int gw = 1;
-            while (gw < nw) gw <<= 1;
-            const int lpw = 32 / gw;                         // lines per warp and step
-            for (int q0 = warp * lpw; q0 < np; q0 += (kThreads / 32) * lpw) {
-                const int q = q0 + lane / gw, wd = lane % gw;
-                const bool valid = q < np && wd < nw;
-                const uint32_t b = valid ? s_bits[q * nw + wd] : 0u;
-                int lb = b ? wd * 32 + 31 - __clz(b) : kNone;  // last set bit of the word
-                int fb = b ? wd * 32 + __ffs(b) - 1 : kFar;    // first set bit of the word
-                for (int d = 1; d < gw; d <<= 1) {
-                    const int u = __shfl_up_sync(0xFFFFFFFFu, lb, d, gw);
-                    const int v = __shfl_down_sync(0xFFFFFFFFu, fb, d, gw);
-                    if (wd >= d) lb = max(lb, u);
-                    if (wd + d < gw) fb = min(fb, v);
-                }
-                int pv = __shfl_up_sync(0xFFFFFFFFu, lb, 1, gw);
-                int nx = __shfl_down_sync(0xFFFFFFFFu, fb, 1, gw);
-                if (wd == 0) pv = kNone;
-                if (wd == gw - 1) nx = kFar;
-                if (valid) {
-                    s_prev[q * nw + wd] = int16_t(pv);
-                    s_next[q * nw + wd] = int16_t(nx);
-                }
-            }
-        } else {
-            for (int q = tid; q < np; q += kThreads)
-                nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
-        }
+        for (int q = tid; q < np; q += kThreads)
+            nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
         __syncthreads();
         for (int it = tid; it < np * nh; it += kThreads) {
             const int q = it / nh, hw = it - q * nh;

@@ -523,9 +523,10 @@ k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__
 //  - the x footprint of a block is its 4 voxels plus the last voxel of the block to the left
 //    and the first of the block to the right: inside the lane directly, across lanes by a
 //    shuffle (the CTA's outermost lanes load the edge voxel themselves);
-//  - rows: a warp takes the 6 footprint rows of its block row (4 core rows and the apron
-//    row on each side, the apron rows also being its neighbours' core rows), combines them
-//    position by position, and forms the x footprint once per slice; no CTA barrier;
+//  - rows: a warp handles the 4 core rows of its block row.  The footprints of its first
+//    and last row go through shared memory to the warps above and below, which hold them as
+//    apron rows; warp 0 and warp 7 load the CTA's outer apron rows themselves.  One CTA
+//    barrier per slice (double-buffered);
 //  - z: a slice belongs to one or two block-slices; their running masks and min / max stay
 //    in registers, and a block is written once its last slice is in (16-byte mask stores);
 //  - the next slice's rows are copied into shared memory (cp.async) while the current one
@@ -722,13 +723,15 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
 {
     using Tr = VTraits<T>;
     constexpr int VL = Tr::VL, BL = VL / 4;
-    constexpr int R = 6;                                       // footprint rows: 4 + apron 2
+    constexpr int XW = BL * (NW + 1);                          // words a lane publishes per row
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);       // [tab_n][NW] (not SHIFT)
-    uint4* s_rows = reinterpret_cast<uint4*>(smem + align16(size_t(tab_n) * NW * 4));
-    // s_rows: [2 slices][kWarps][R rows][32 lanes]: the voxel rows, copied one slice ahead
-    uint4* s_edge = s_rows + 2 * kWarps * R * 32;
-    // s_edge: [2 slices][kWarps][R rows][2]: the 16-byte vectors holding the CTA's edge
+    uint32_t* s_x = reinterpret_cast<uint32_t*>(smem + align16(size_t(tab_n) * NW * 4));
+    // s_x: [2 buffers][2 rows (first, last)][kWarps][XW][32 lanes]
+    uint4* s_rows = reinterpret_cast<uint4*>(s_x + 2 * 2 * kWarps * XW * 32);
+    // s_rows: [2 slices][kWarps][5 rows][32 lanes]: the voxel rows, copied one slice ahead
+    uint4* s_edge = s_rows + 2 * kWarps * 5 * 32;
+    // s_edge: [2 slices][kWarps][5 rows][2]: the 16-byte vectors holding the CTA's edge
     // voxels (left of lane 0, right of lane 31), copied with the rows
     pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -749,21 +752,17 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
     const unsigned nmax = unsigned(p.N - 1);
     const uint32_t nmax2 = sizeof(T) == 2 ? (min(nmax, 0xFFFFu) * 0x10001u)
                                           : (min(nmax, 0xFFu) * 0x01010101u);
-    const unsigned shv = unsigned(sh);
     const int by = blockIdx.y * kWarps + warp;
     const int xv0 = (blockIdx.x * 32 + lane) * VL;             // first voxel of the lane
     const bool lane_ok = xv0 < X;
     const int xe = lane == 0 ? int(blockIdx.x) * 32 * VL - 1 : (int(blockIdx.x) + 1) * 32 * VL;
     const bool edge_ok = (lane == 0 || lane == 31) && xe >= 0 && xe < X;
-    // the 16-byte vector that holds the edge voxel of lane 0 (its last voxel) or lane 31
-    // (its first voxel): aligned, since rows are whole vectors
-    const int xev = lane == 0 ? xe - (VL - 1) : xe;
-    const int eslot = lane == 0 ? 0 : 1;
     const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
     const int zs = max(0, 4 * zb0 - 1), ze = min(p.Z - 1, 4 * zb1);
-    const int ya = by * 4 - 1;                                  // first footprint row
+    const int y0 = by * 4;
+    const int yx = warp == 0 ? y0 - 1 : y0 + 4;                 // warps 0 / 7: outer apron row
+    const bool has_x = warp == 0 || warp == kWarps - 1;
     const int64_t rowX = X;
-    auto row_ok = [&](int t) { return ya + t >= 0 && ya + t < Y; };   // warp-uniform
     // running footprint of two block-slices: A = z >> 2, B = the next one (started at its
     // first apron slice)
     uint32_t aM[BL][NW], bM[BL][NW];
@@ -809,23 +808,33 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
             for (int j = 0; j < BL; ++j) occ[blk0 + j] = uint8_t(M[j][0] != 0);
         }
     };
-    // copies of slice z's R rows (and edge vectors) into buffer `bsel`, asynchronous
+    // the rows of a slice: the 4 core rows and, for warps 0 / 7, the outer apron row
+    auto row_y = [&](int t) { return t < 4 ? y0 + t : yx; };
+    auto row_ok = [&](int t) {                                 // warp-uniform
+        const int y = row_y(t);
+        return (t < 4 || has_x) && y >= 0 && y < Y;
+    };
+    // the 16-byte vector that holds the edge voxel of lane 0 (its last voxel) or lane 31
+    // (its first voxel): aligned, since rows are whole vectors
+    const int xev = lane == 0 ? xe - (VL - 1) : xe;
+    const int eslot = lane == 0 ? 0 : 1;
+    // copies of slice z's rows (and edge vectors) into buffer `bsel`, asynchronous, one group
     auto fetch = [&](int z, int bsel) {
         const T* slice = vol + int64_t(z) * Y * rowX;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-            if (!row_ok(t)) continue;
-            const T* row = slice + int64_t(ya + t) * rowX;
-            if (lane_ok) {
+        for (int t = 0; t < 5; ++t) {
+            const bool ok = row_ok(t);
+            const T* row = slice + int64_t(ok ? row_y(t) : 0) * rowX;
+            if (ok && lane_ok) {
                 const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
-                    s_rows + ((bsel * kWarps + warp) * R + t) * 32 + lane));
+                    s_rows + ((bsel * kWarps + warp) * 5 + t) * 32 + lane));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
                              "l"(row + xv0)
                              : "memory");
             }
-            if (edge_ok) {
+            if (ok && edge_ok) {
                 const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
-                    s_edge + ((bsel * kWarps + warp) * R + t) * 2 + eslot));
+                    s_edge + ((bsel * kWarps + warp) * 5 + t) * 2 + eslot));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
                              "l"(row + xev)
                              : "memory");
@@ -839,57 +848,135 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
         if (z < ze) fetch(z + 1, bsel ^ 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");     // this lane's copies of z
-        const uint4* rows = s_rows + (bsel * kWarps + warp) * R * 32 + lane;
-        const uint4* edges = s_edge + (bsel * kWarps + warp) * R * 2 + eslot;
-        // ---- the warp's R footprint rows, combined position by position, then the x
-        //      footprint of every block of the lane once per slice
-        uint32_t c6[BL][NW], f6[BL][NW], l6[BL][NW], e6[NW], mn6[4], mx6[4];
-        unsigned en6 = 0xFFFFu, ex6 = 0;
-#pragma unroll
-        for (int j = 0; j < BL; ++j)
-#pragma unroll
-            for (int w = 0; w < NW; ++w) c6[j][w] = f6[j][w] = l6[j][w] = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) e6[w] = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { mn6[k] = Tr::NEUTRAL_MIN; mx6[k] = 0; }
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            if (!row_ok(t)) continue;                           // warp-uniform
-            unsigned ev = 0xFFFFFFFFu;
-            if (edge_ok) {
-                const uint4 q = edges[t * 2];
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-                ev = lane == 0 ? Tr::get(w4[3], Tr::PER_WORD - 1) : Tr::get(w4[0], 0);
-            }
-            uint32_t core[BL][NW], first[BL][NW], last[BL][NW], em[NW], wv[4];
-            unsigned emn, emx;
-            lane_row<T, NW, SHIFT>(lane_ok ? rows[t * 32] : make_uint4(0u, 0u, 0u, 0u), ev,
-                                   lane_ok, nmax2, nmax, shv, s_tab, core, first, last, em, emn,
-                                   emx, wv);
-#pragma unroll
-            for (int j = 0; j < BL; ++j)
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    c6[j][w] |= core[j][w];
-                    f6[j][w] |= first[j][w];
-                    l6[j][w] |= last[j][w];
-                }
-#pragma unroll
-            for (int w = 0; w < NW; ++w) e6[w] |= em[w];
-            if (want_mm) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    mn6[k] = Tr::vmin(mn6[k], wv[k]);
-                    mx6[k] = Tr::vmax(mx6[k], lane_ok ? wv[k] : 0u);
-                }
-                en6 = min(en6, emn);
-                ex6 = max(ex6, emx);
-            }
-        }
+        const uint4* rows = s_rows + (bsel * kWarps + warp) * 5 * 32 + lane;
+        const uint4* edges = s_edge + (bsel * kWarps + warp) * 5 * 2 + eslot;
+        // the edge voxel of row t (lanes 0 / 31), else none
+        auto edge_of = [&](int t) -> unsigned {
+            if (!(row_ok(t) && edge_ok)) return 0xFFFFFFFFu;
+            const uint4 q = edges[t * 2];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+            return lane == 0 ? VTraits<T>::get(w[3], VTraits<T>::PER_WORD - 1)
+                             : VTraits<T>::get(w[0], 0);
+        };
+        // ---- the slice's footprint of every block of the lane, S: rows 0 and 3 (published
+        //      for the warps above and below), rows 1 and 2 combined position by position
+        //      first, the warp's own outer apron row, then the neighbours' rows
         uint32_t S[BL][NW];
         unsigned Smn[BL], Smx[BL];
-        lane_footprint<T, NW>(c6, f6, l6, e6, en6, ex6, mn6, mx6, lane, want_mm, S, Smn, Smx);
+#pragma unroll
+        for (int j = 0; j < BL; ++j) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) S[j][w] = 0;
+            Smn[j] = 0xFFFFu;
+            Smx[j] = 0;
+        }
+        const int buf = z & 1;
+        uint32_t* xf = s_x + ((buf * 2 + 0) * kWarps + warp) * XW * 32 + lane;
+        uint32_t* xl = s_x + ((buf * 2 + 1) * kWarps + warp) * XW * 32 + lane;
+        auto fold = [&](const uint32_t (&fp)[BL][NW], const unsigned (&fmn)[BL],
+                        const unsigned (&fmx)[BL]) {
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) S[j][w] |= fp[j][w];
+                Smn[j] = min(Smn[j], fmn[j]);
+                Smx[j] = max(Smx[j], fmx[j]);
+            }
+        };
+        auto publish = [&](uint32_t* dst, const uint32_t (&fp)[BL][NW], const unsigned (&fmn)[BL],
+                           const unsigned (&fmx)[BL]) {
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) dst[(j * NW + w) * 32] = fp[j][w];
+                dst[(BL * NW + j) * 32] = fmn[j] | (fmx[j] << 16);
+            }
+        };
+        {
+            uint32_t core[BL][NW], first[BL][NW], last[BL][NW], em[NW], wv[4], wmx[4];
+            uint32_t fp[BL][NW];
+            unsigned emn, emx, fmn[BL], fmx[BL];
+            const unsigned sh = unsigned(p.sh);
+            // one row on its own: rows 0, 3 and the apron row
+            auto single = [&](int t) {
+                const bool ok = row_ok(t) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[t * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(t), ok,
+                                       nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) wmx[k] = ok ? wv[k] : 0u;
+                lane_footprint<T, NW>(core, first, last, em, emn, emx, wv, wmx, lane, want_mm, fp,
+                                      fmn, fmx);
+            };
+            single(0);
+            publish(xf, fp, fmn, fmx);
+            fold(fp, fmn, fmx);
+            single(3);
+            publish(xl, fp, fmn, fmx);
+            fold(fp, fmn, fmx);
+            if (has_x) {                                        // warp-uniform
+                single(4);
+                fold(fp, fmn, fmx);
+            }
+            // rows 1 and 2, combined position by position before the footprint
+            uint32_t c12[BL][NW], f12[BL][NW], l12[BL][NW], e12[NW], mn12[4], mx12[4];
+            unsigned en12, ex12;
+            {
+                const bool ok = row_ok(1) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[1 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(1), ok,
+                                       nmax2, nmax, sh, s_tab, c12, f12, l12, e12, en12, ex12, mn12);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mx12[k] = ok ? mn12[k] : 0u;
+            }
+            {
+                const bool ok = row_ok(2) && lane_ok;
+                lane_row<T, NW, SHIFT>(ok ? rows[2 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(2), ok,
+                                       nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
+#pragma unroll
+                for (int j = 0; j < BL; ++j)
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        c12[j][w] |= core[j][w];
+                        f12[j][w] |= first[j][w];
+                        l12[j][w] |= last[j][w];
+                    }
+#pragma unroll
+                for (int w = 0; w < NW; ++w) e12[w] |= em[w];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    mn12[k] = Tr::vmin(mn12[k], wv[k]);
+                    mx12[k] = Tr::vmax(mx12[k], ok ? wv[k] : 0u);
+                }
+                en12 = min(en12, emn);
+                ex12 = max(ex12, emx);
+            }
+            lane_footprint<T, NW>(c12, f12, l12, e12, en12, ex12, mn12, mx12, lane, want_mm, fp,
+                                  fmn, fmx);
+            fold(fp, fmn, fmx);
+        }
+        __syncthreads();
+        // ---- the neighbours' rows: the last row of the warp above, the first of the one below
+        if (warp > 0) {
+            const uint32_t* up = s_x + ((buf * 2 + 1) * kWarps + warp - 1) * XW * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) S[j][w] |= up[(j * NW + w) * 32];
+                const unsigned pa = up[(BL * NW + j) * 32];
+                Smn[j] = min(Smn[j], pa & 0xFFFFu);
+                Smx[j] = max(Smx[j], pa >> 16);
+            }
+        }
+        if (warp < kWarps - 1) {
+            const uint32_t* dn = s_x + ((buf * 2 + 0) * kWarps + warp + 1) * XW * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) S[j][w] |= dn[(j * NW + w) * 32];
+                const unsigned pb = dn[(BL * NW + j) * 32];
+                Smn[j] = min(Smn[j], pb & 0xFFFFu);
+                Smx[j] = max(Smx[j], pb >> 16);
+            }
+        }
         // ---- z: slice z = 4 q + t belongs to block-slice q, to q - 1 when t == 0 and to
         //      q + 1 when t == 3
         const int t = z & 3, qz = z >> 2;
@@ -941,8 +1028,9 @@ cudaError_t launch_pom_vec(const T* v, const FpParams& p, int tab_n, const uint8
 {
     constexpr int VL = 16 / int(sizeof(T));
     const size_t tab_bytes = SHIFT ? 0 : align16(size_t(tab_n) * NW * 4);
-    const size_t rows = size_t(2) * kWarps * 6 * (32 + 2) * 16;
-    const size_t sm = tab_bytes + rows;
+    const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
+    const size_t rows = size_t(2) * kWarps * 5 * (32 + 2) * 16;
+    const size_t sm = tab_bytes + xb + rows;
     dim3 gv((p.X / VL + 31) / 32, (p.gy + kWarps - 1) / kWarps, (p.gz + p.zchunk - 1) / p.zchunk);
     cudaError_t e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE, SHIFT>>(int(sm));
     if (e != cudaSuccess) return e;

@@ -26,8 +26,10 @@ executor's payload gives a builder): the build is queued on a side stream and th
 session's first batch waits for it on the device.
 
 The scheduler (`Scheduler`) holds no GPU state and is tested with a fake executor; the
-executor for the GPU (`DeviceExecutor`) does every step through libdm: the host TFs are
-copied to each session's device TF buffer on the slot's stream, then one
+executor for the GPU (`DeviceExecutor`) does every step through libdm: pinned host TFs
+are handed to the kernels as they are (the active-set step reads their alpha channel once
+per edit over the CPU-GPU link), other TFs are copied to the session's device TF buffer on
+the slot's stream; then one
 dm_update_tf_batch, or dm_update_tf_batch_ws when a session has several edits in the batch
 (or, for the comparison server, one dm_full_recompute per edit).
 """
@@ -306,11 +308,14 @@ class DeviceExecutor:
     precompute on `stream` and returns (engine, volume or None)."""
 
     def __init__(self, slots: int = 2, mode: str = "partitioned", device="cuda",
-                 edits_per_session: int = 1, max_batch: int = 64):
+                 edits_per_session: int = 1, max_batch: int = 64, tf_from_host: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.mode = mode                      # "partitioned" or "full"
+        # pinned host TFs are read by the kernels in place (one CTA per edit reads its
+        # alpha channel over the CPU-GPU link) instead of being copied first
+        self.tf_from_host = bool(tf_from_host)
         self.edits_per_session = max(1, int(edits_per_session))
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         # one completion event per slot: a slot takes a new batch only after its last one
@@ -387,9 +392,14 @@ class DeviceExecutor:
                         eng.ready_event = None
                 e = used.get(r.session, 0)            # the request's place in its session
                 used[r.session] = e + 1
-                tf, out = s["tf"][slot][e], s["out"][slot][e]
-                tf.copy_(r.tf, non_blocking=True)
-                items.append((eng.ctx, tf.data_ptr(), out.data_ptr()))
+                out = s["out"][slot][e]
+                if self.tf_from_host and not r.tf.is_cuda and r.tf.is_pinned():
+                    tfp = r.tf.data_ptr()             # read in place; the request keeps it alive
+                else:
+                    tf = s["tf"][slot][e]
+                    tf.copy_(r.tf, non_blocking=True)
+                    tfp = tf.data_ptr()
+                items.append((eng.ctx, tfp, out.data_ptr()))
                 outs.append(out)
             sh = ctypes.c_void_p(st.cuda_stream)
             if self.mode == "partitioned":

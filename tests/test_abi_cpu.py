@@ -69,8 +69,8 @@ def cfg(**kw):
     (dict(num_partitions=4, borders=[1, 5, 9, 200, 256]), A.DM_ERR_INVALID_ARG),
     (dict(num_partitions=4, borders=[0, 5, 9, 200, 255]), A.DM_ERR_INVALID_ARG),
     (dict(dims=(4, 4, 4 * 2000)), A.DM_OK),                  # 2000-block z lines
-    (dict(dims=(4, 4, 4 * 5888)), A.DM_OK),                  # the longest line a tile holds
-    (dict(dims=(4, 4, 4 * 5889)), A.DM_ERR_UNSUPPORTED),     # z lines beyond the tiling
+    (dict(dims=(4, 4, 4 * 5886)), A.DM_OK),                  # the longest line a tile holds
+    (dict(dims=(4, 4, 4 * 5887)), A.DM_ERR_UNSUPPORTED),     # z lines beyond the tiling
     (dict(dims=(1, 1, 1), block=1, apron=0, num_partitions=1, tf_size=2), A.DM_OK),
 ])
 def test_create_validation(kw, status):
