@@ -128,6 +128,30 @@ dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *
 dm_status dm_build_partitions(dm_ctx *ctx, const void *d_volume, void *stream);
 
 /*
+ * The same one-time precompute (§3.1, §3.2) for n volumes in one call: ctxs[i] is built
+ * from d_volumes[i] exactly as dm_build_partitions(ctxs[i], d_volumes[i], stream) would
+ * build it.  Contexts may differ in size, voxel type, block, K and N.  Each step of the
+ * precompute (partition tables, POM masks, x pass, y pass, z pass) runs as one launch per
+ * kernel variant over the CTAs of all the volumes, DM_BUILD_BATCH_MAX_ITEMS volumes at a
+ * time.  POM builds go to the 16-byte vector kernel where it takes the volume (b = 4,
+ * apron 1, rows of whole 16-byte vectors, a 16-byte aligned volume, K <= 32 for uint8 and
+ * K <= 64 for uint16), else to the general kernel (K <= 64); a volume with K > 64 gets its
+ * own POM launch within the batch.  The range-index levels (DM_INDEX_RANGES) are built
+ * per volume after the z pass.  Asynchronous on `stream`.  The call first clears the
+ * message of every listed context.  Errors, all found on the host before anything is
+ * enqueued: DM_ERR_INVALID_ARG
+ * (null arrays or n < 0, a null context, a null or misaligned volume, a context listed
+ * twice, two contexts bound to the same mask, pdm, min/max or scratch buffer) and
+ * DM_ERR_NOT_BOUND (mask, pdm or scratch not bound), reported in the context concerned
+ * (dm_last_error_string), else in ctxs[0].  The buffers of different contexts must not
+ * overlap.  A launch failure returns DM_ERR_CUDA; the volumes of the failing group of
+ * DM_BUILD_BATCH_MAX_ITEMS are then unbuilt and those of later groups untouched.
+ */
+#define DM_BUILD_BATCH_MAX_ITEMS 64
+dm_status dm_build_partitions_batch(dm_ctx *const *ctxs, const void *const *d_volumes,
+                                    int32_t n, void *stream);
+
+/*
  * Per-TF update (§3.1 steps 1 and 2, Eq. 1).  d_tf_rgba: device float32 [N][4] (RGBA);
  * a partition is active when one of its intensities has alpha > 0.0f (NaN is not).
  * d_out: device uint8 [G], D' = min over active p of PDM_p, 255 where no partition is

@@ -28,9 +28,11 @@ DM_NOALLOC_MAX_TF_SIZE = 16384
 DM_NOALLOC_SCRATCH_BYTES = 4096
 DM_BATCH_MAX_ITEMS = 64
 DM_BATCH_MAX_EDITS_PER_GROUP = 8
+DM_BUILD_BATCH_MAX_ITEMS = 64
 
 #: every function declared in include/dm.h
-EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
+EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions",
+            "dm_build_partitions_batch", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
             "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_batch_workspace_bytes",
             "dm_update_tf_batch_ws", "dm_render", "dm_config_hash",
@@ -95,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.dm_query_sizes.argtypes = [P, ctypes.POINTER(dm_sizes)]
     lib.dm_bind.argtypes = [P, P, P, P, P]
     lib.dm_build_partitions.argtypes = [P, P, P]
+    lib.dm_build_partitions_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), S, P]
     lib.dm_update_tf.argtypes = [P, P, P, P, P]
     lib.dm_update_tf_host.argtypes = [P, P, P, P]
     lib.dm_full_recompute.argtypes = [P, P, P, P, P]
@@ -117,7 +120,8 @@ def load(path: str = LIB_PATH):
     lib.dm_status_string.argtypes = [S]
     lib.dm_status_string.restype = ctypes.c_char_p
     lib.dm_version.argtypes = []
-    for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions", "dm_update_tf",
+    for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions",
+              "dm_build_partitions_batch", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
               "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_update_tf_batch_ws",
               "dm_render", "dm_config_hash", "dm_mark_built", "dm_sync", "dm_version"):
@@ -186,6 +190,26 @@ def dm_bind(ctx, d_mask, d_pdm, d_minmax, d_scratch):
 
 def dm_build_partitions(ctx, d_volume, stream):
     _check(ctx, load().dm_build_partitions(ctx, d_volume, stream), "dm_build_partitions")
+
+
+def dm_build_partitions_batch(ctxs, d_volumes, stream=None):
+    """The precompute of several contexts in one call: ctxs[i] from the device volume
+    pointer d_volumes[i]."""
+    n = len(ctxs)
+    if len(d_volumes) != n:
+        raise ValueError(f"{n} contexts but {len(d_volumes)} volumes")
+    carr = (ctypes.c_void_p * max(1, n))(*ctxs)
+    varr = (ctypes.c_void_p * max(1, n))(*d_volumes)
+    st = load().dm_build_partitions_batch(carr, varr, n, stream)
+    if st != DM_OK:
+        # the library reports in the context concerned: the first one with a message
+        detail = ""
+        for c in ctxs:
+            if c:
+                detail = load().dm_last_error_string(c).decode()
+                if detail:
+                    break
+        raise DmError(st, "dm_build_partitions_batch", detail)
 
 
 def dm_update_tf(ctx, d_tf_rgba, d_out, d_active_mask_out, stream):

@@ -4,12 +4,14 @@
 // method runs in the kernels of dm_footprint.cu, dm_dt.cu and dm_update.cu; this file only
 // checks arguments, lays out the caller's scratch buffer and enqueues work on the caller's
 // stream.  No device memory is allocated here.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 
 #include "../../include/dm.h"
+#include "dm_build_batch.cuh"
 #include "dm_internal.cuh"
 
 struct dm_ctx {
@@ -203,6 +205,17 @@ dm_status dm_bind(dm_ctx* ctx, void* d_mask, void* d_pdm, void* d_minmax, void* 
     return DM_OK;
 }
 
+// Uniform partitions of a power-of-two width: the partition of intensity i is i >> shift.
+// Else -1.
+static int pom_shift(const dm_ctx* c)
+{
+    const int K = c->cfg.num_partitions, N = c->cfg.tf_size;
+    if (!c->uniform_borders || N % K != 0 || ((N / K) & (N / K - 1)) != 0) return -1;
+    int shift = 0;
+    while ((1 << shift) < N / K) ++shift;
+    return shift;
+}
+
 dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
 {
     if (!ctx) return DM_ERR_INVALID_ARG;
@@ -219,11 +232,7 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     uint8_t* pdm = static_cast<uint8_t*>(ctx->d_pdm);
     cudaError_t e = dmk::launch_partition_lut(lut, N, K, ctx->borders, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition table");
-    // uniform partitions of a power-of-two width: partition of intensity i = i >> shift
-    int shift = -1;
-    if (ctx->uniform_borders && N % K == 0 && ((N / K) & (N / K - 1)) == 0)
-        for (shift = 0; (1 << shift) < N / K; ++shift) {
-        }
+    const int shift = pom_shift(ctx);
     e = dmk::launch_pom_build(d_volume, ctx->geo, N, K, lut, static_cast<uint64_t*>(ctx->d_mask),
                               ctx->d_minmax, shift, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "POM build");
@@ -240,6 +249,109 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     ctx->built = true;
     ctx->minmax_built = ctx->d_minmax != nullptr;
     ctx->err[0] = 0;
+    return DM_OK;
+}
+
+// Host checks of a batched precompute: every context bound, every volume aligned, no
+// context twice and no buffer bound to two contexts (by sorting the buffer addresses).
+static dm_status check_build_batch(dm_ctx* const* ctxs, const void* const* vols, int32_t n)
+{
+    for (int32_t i = 0; i < n; ++i)        // a refusal leaves its message in one context only
+        if (ctxs[i]) ctxs[i]->err[0] = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        dm_ctx* c = ctxs[i];
+        if (!c)
+            return ctxs[0] ? fail(ctxs[0], DM_ERR_INVALID_ARG, "dm_build_partitions_batch: item "
+                                  "%d: null context", i) : DM_ERR_INVALID_ARG;
+        if (!vols[i] || !aligned(vols[i], size_t(c->geo.bpv)))
+            return fail(c, DM_ERR_INVALID_ARG, "dm_build_partitions_batch: item %d: null or "
+                        "misaligned volume", i);
+        if (!c->d_mask || !c->d_pdm || !c->d_scratch)
+            return fail(c, DM_ERR_NOT_BOUND, "dm_build_partitions_batch: item %d: mask, pdm and "
+                        "scratch must be bound", i);
+    }
+    struct Buf {
+        uintptr_t p;
+        int32_t item;
+    };
+    Buf* bufs = new (std::nothrow) Buf[size_t(n) * 5];
+    if (!bufs)
+        return fail(ctxs[0], DM_ERR_INVALID_ARG, "dm_build_partitions_batch: out of host memory");
+    size_t nb = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const dm_ctx* c = ctxs[i];
+        // the context itself counts as a buffer, so that a context listed twice is caught
+        const void* own[5] = {c, c->d_mask, c->d_pdm, c->d_scratch, c->d_minmax};
+        for (const void* p : own)
+            if (p) bufs[nb++] = Buf{reinterpret_cast<uintptr_t>(p), i};
+    }
+    std::sort(bufs, bufs + nb, [](const Buf& a, const Buf& b) {
+        return a.p < b.p || (a.p == b.p && a.item < b.item);
+    });
+    dm_status st = DM_OK;
+    for (size_t k = 1; k < nb && st == DM_OK; ++k)
+        if (bufs[k].p == bufs[k - 1].p && bufs[k].item != bufs[k - 1].item)
+            st = fail(ctxs[bufs[k].item], DM_ERR_INVALID_ARG, "dm_build_partitions_batch: items "
+                      "%d and %d share a context or a buffer", bufs[k - 1].item, bufs[k].item);
+    delete[] bufs;
+    return st;
+}
+
+dm_status dm_build_partitions_batch(dm_ctx* const* ctxs, const void* const* d_volumes, int32_t n,
+                                    void* stream)
+{
+    if (!ctxs || !d_volumes || n < 0) return DM_ERR_INVALID_ARG;
+    if (n == 0) return DM_OK;
+    dm_status st = check_build_batch(ctxs, d_volumes, n);
+    if (st != DM_OK) return st;
+    st = check_sticky(ctxs[0], "dm_build_partitions_batch (earlier work)");
+    if (st != DM_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    dmk::BuildItem items[dmk::kMaxBuildBatch];
+    for (int32_t i0 = 0; i0 < n; i0 += dmk::kMaxBuildBatch) {
+        const int m = (n - i0) < dmk::kMaxBuildBatch ? (n - i0) : dmk::kMaxBuildBatch;
+        for (int k = 0; k < m; ++k) {
+            dm_ctx* c = ctxs[i0 + k];
+            dmk::BuildItem& b = items[k];
+            b.vol = d_volumes[i0 + k];
+            b.g = c->geo;
+            b.N = c->cfg.tf_size;
+            b.K = c->cfg.num_partitions;
+            b.shift = pom_shift(c);
+            b.borders = &c->borders;
+            b.lut = static_cast<uint8_t*>(c->d_scratch) + c->off_lut;
+            b.mask = static_cast<uint64_t*>(c->d_mask);
+            b.minmax = c->d_minmax;
+            b.pdm = static_cast<uint8_t*>(c->d_pdm);
+            c->built = false;
+            c->minmax_built = false;
+        }
+        dm_ctx* first = ctxs[i0];
+        cudaError_t e = dmk::launch_partition_lut_batch(items, m, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: partition tables");
+        e = dmk::launch_pom_build_batch(items, m, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: POM build");
+        e = dmk::launch_xpass_mask_batch(items, m, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: x pass");
+        e = dmk::launch_line_pass_batch(items, m, 1, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: y pass");
+        e = dmk::launch_line_pass_batch(items, m, 2, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: z pass");
+        for (int k = 0; k < m; ++k) {
+            dm_ctx* c = ctxs[i0 + k];
+            if (c->J > 0) {
+                e = dmk::launch_build_index(items[k].pdm, c->geo.plane, c->geo.G,
+                                            c->cfg.num_partitions, s);
+                if (e != cudaSuccess) return cuda_fail(c, e, "batched precompute: range index");
+            }
+        }
+        for (int k = 0; k < m; ++k) {
+            dm_ctx* c = ctxs[i0 + k];
+            c->built = true;
+            c->minmax_built = c->d_minmax != nullptr;
+            c->err[0] = 0;
+        }
+    }
     return DM_OK;
 }
 

@@ -1,0 +1,46 @@
+// dm_build_batch.cuh -- the batched one-time precompute: launchers shared between the
+// C-ABI layer and the kernel files.  Internal to libdm.
+#pragma once
+
+#include "dm_internal.cuh"
+
+namespace dmk {
+
+// ---------------------------------------------------------------- batched precompute
+constexpr int kMaxBuildBatch = 64;     // volumes per batched launch (descriptors as parameters)
+
+// One volume of a batched precompute: the buffers of its one-volume build.
+struct BuildItem {
+    const void* vol;
+    Geometry g;
+    int N, K;
+    int shift;                         // as in launch_pom_build
+    const Borders* borders;            // host memory, read while the launches are set up
+    uint8_t* lut;
+    uint64_t* mask;
+    void* minmax;                      // may be null
+    uint8_t* pdm;                      // K planes, g.plane bytes apart
+};
+
+// The CTA of a grid that concatenates several volumes' grids: the last i < n with
+// start[i] <= cta (start ascending from start[0] = 0, no volume without CTAs).
+__device__ __forceinline__ int batch_item_of(const int* start, int n, int cta)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= cta) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Each step of the precompute of up to kMaxBuildBatch volumes as one launch per kernel
+// variant over all their CTAs.  Partition tables; POM build (volumes that the 16-byte
+// vector kernel does not take run their one-volume kernels); x pass; y pass; z pass.
+cudaError_t launch_partition_lut_batch(const BuildItem* items, int n, cudaStream_t s);
+cudaError_t launch_pom_build_batch(const BuildItem* items, int n, cudaStream_t s);
+cudaError_t launch_xpass_mask_batch(const BuildItem* items, int n, cudaStream_t s);
+cudaError_t launch_line_pass_batch(const BuildItem* items, int n, int axis, cudaStream_t s);
+
+}  // namespace dmk

@@ -28,6 +28,9 @@
 // last position of every value (0..255) that the sweep fills as it goes.  Each output
 // costs O(1) work whatever the distances are.  Clamping at 255 needs no extra step: a
 // value of 255 is a source of level 255 that never expires.
+#include <algorithm>
+
+#include "dm_build_batch.cuh"
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -114,17 +117,16 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t r, int lane)
 // right of its 16 blocks comes from the rest of the word or the prev / next tables, then
 // two 16-step scans give every distance, stored as one 16-byte vector.
 template <int W>
-__global__ void __launch_bounds__(kThreads)
-k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
+__device__ __forceinline__ void xpass_mask_row(const uint64_t* __restrict__ mask, int K,
+                                               const XGeom& xg, uint8_t* __restrict__ out,
+                                               int row)
 {
     extern __shared__ uint32_t s_mem[];
-    pdl_wait();
     const int nw = xg.nw;
     const int cap = min(64, K);                              // partitions per chunk
     uint32_t* s_bits = s_mem;
     int16_t* s_prev = reinterpret_cast<int16_t*>(s_mem + cap * nw);
     int16_t* s_next = s_prev + cap * nw;
-    const int row = blockIdx.x;                              // z * gy + y
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rbase = int64_t(row) * xg.gx;
     const int nh = 2 * nw;                                   // 16-block items per bit line
@@ -185,6 +187,33 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
             }
         }
     }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
+{
+    pdl_wait();
+    xpass_mask_row<W>(mask, K, xg, out, blockIdx.x);         // row = z * gy + y
+}
+
+// Several volumes' x passes in one grid: one CTA per block row, volume after volume.
+struct XBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first row (CTA) of each volume
+    const uint64_t* mask[kMaxBuildBatch];
+    uint8_t* out[kMaxBuildBatch];
+    int K[kMaxBuildBatch];
+    XGeom xg[kMaxBuildBatch];
+};
+
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+k_xpass_mask_batch(const __grid_constant__ XBatch B)
+{
+    const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    pdl_wait();
+    xpass_mask_row<W>(B.mask[i], B.K[i], B.xg[i], B.out[i], int(blockIdx.x) - B.start[i]);
 }
 
 template <typename Src>
@@ -335,8 +364,8 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __rest
 // numbers its rows 0..L-1 from a cleared table), else uint16_t (the backward sweep's
 // positions follow the forward sweep's, so one clearing serves both).
 template <int TC, typename P>
-__global__ void __launch_bounds__(TC)
-k_line_sweep(uint8_t* buf, LineGeom lg)
+__device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg, int cx,
+                                                int cy, int cz)
 {
     extern __shared__ uint32_t s_mem[];
     constexpr int V = TC / 16;                               // 16-byte vectors per row
@@ -344,10 +373,9 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
     const int L = lg.L;
     uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_mem);     // [L][TC]
     P* s_tab = reinterpret_cast<P*>(s_tile + sweep_tile_bytes(L, TC));   // [257][TC]
-    pdl_wait();
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TC;
-    uint8_t* base = buf + int64_t(blockIdx.z) * lg.plane + int64_t(blockIdx.y) * lg.os + x0;
+    const int x0 = cx * TC;
+    uint8_t* base = buf + int64_t(cz) * lg.plane + int64_t(cy) * lg.os + x0;
     const int ncols = min(TC, lg.gx - x0);
 
     // ---- stage the tile (asynchronous copies, all in flight at once); note whether it can
@@ -403,6 +431,36 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
     } else {
         sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
     }
+}
+
+template <int TC, typename P>
+__global__ void __launch_bounds__(TC)
+k_line_sweep(uint8_t* buf, LineGeom lg)
+{
+    pdl_wait();
+    line_sweep_tile<TC, P>(buf, lg, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several volumes' y (or z) passes in one grid; each volume keeps its one-volume grid
+// (tiles along x fastest, then the outer index, then the plane).
+struct LineBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first CTA of each volume
+    uint8_t* buf[kMaxBuildBatch];
+    LineGeom lg[kMaxBuildBatch];
+    int gdx[kMaxBuildBatch];                   // tiles along x
+};
+
+template <int TC, typename P>
+__global__ void __launch_bounds__(TC)
+k_line_sweep_batch(const __grid_constant__ LineBatch B)
+{
+    const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const int local = int(blockIdx.x) - B.start[i];
+    const int gdx = B.gdx[i], n_outer = B.lg[i].n_outer;
+    const int cx = local % gdx, rest = local / gdx;
+    pdl_wait();
+    line_sweep_tile<TC, P>(B.buf[i], B.lg[i], cx, rest % n_outer, rest / n_outer);
 }
 
 }  // namespace
@@ -468,8 +526,7 @@ cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t
     return launch_single(SrcOcc{occ_inout}, g, occ_inout, s);
 }
 
-cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
-                             cudaStream_t s)
+static LineGeom line_geom(uint8_t* buf, int64_t plane, const Geometry& g, int axis)
 {
     LineGeom lg;
     lg.gx = g.gx;
@@ -485,10 +542,17 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
         lg.n_outer = g.gy;
         lg.os = g.gx;
     }
+    lg.vec_ok = (g.gx % kLineTile == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
+                (plane % 16 == 0);
+    return lg;
+}
+
+cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry& g, int axis,
+                             cudaStream_t s)
+{
+    const LineGeom lg = line_geom(buf, plane, g, axis);
     if (lg.L <= 1) return cudaSuccess;   // a single block per line: h == g
     constexpr int TC = kLineTile;
-    lg.vec_ok = (g.gx % TC == 0) && ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) &&
-                (plane % 16 == 0);
     const size_t smem = line_pass_smem(lg.L);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
     dim3 grid((g.gx + TC - 1) / TC, lg.n_outer, P);
@@ -500,6 +564,92 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
     cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC, uint16_t>>(int(smem));
     if (e != cudaSuccess) return e;
     return launch_pdl(k_line_sweep<TC, uint16_t>, grid, dim3(TC), smem, s, buf, lg);
+}
+
+template <int W>
+static cudaError_t launch_xpass_group(const BuildItem* const* its, int m, cudaStream_t s)
+{
+    XBatch B;
+    B.n = m;
+    int64_t rows = 0;
+    size_t smem = 0;
+    for (int k = 0; k < m; ++k) {
+        const BuildItem& b = *its[k];
+        B.mask[k] = b.mask;
+        B.out[k] = b.pdm;
+        B.K[k] = b.K;
+        B.xg[k] = xgeom(b.g, b.g.plane, b.pdm);
+        B.start[k] = int(rows);
+        rows += B.xg[k].rows;
+        if (rows > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+        smem = std::max(smem, size_t(b.K < 64 ? b.K : 64) * B.xg[k].nw * 8);
+    }
+    B.start[m] = int(rows);
+    cudaError_t e = ensure_dynamic_smem<k_xpass_mask_batch<W>>(int(smem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_xpass_mask_batch<W>, dim3(unsigned(rows)), dim3(kThreads), smem, s, B);
+}
+
+cudaError_t launch_xpass_mask_batch(const BuildItem* items, int n, cudaStream_t s)
+{
+    const BuildItem* by_w[4][kMaxBuildBatch];
+    int count[4] = {0, 0, 0, 0};
+    for (int i = 0; i < n && i < kMaxBuildBatch; ++i) {
+        const int w = (items[i].K + 63) / 64 - 1;
+        if (w < 0 || w > 3) return cudaErrorInvalidValue;
+        by_w[w][count[w]++] = &items[i];
+    }
+    cudaError_t e = cudaSuccess;
+    if (count[0]) e = launch_xpass_group<1>(by_w[0], count[0], s);
+    if (e == cudaSuccess && count[1]) e = launch_xpass_group<2>(by_w[1], count[1], s);
+    if (e == cudaSuccess && count[2]) e = launch_xpass_group<3>(by_w[2], count[2], s);
+    if (e == cudaSuccess && count[3]) e = launch_xpass_group<4>(by_w[3], count[3], s);
+    return e;
+}
+
+template <typename P>
+static cudaError_t launch_line_group(const BuildItem* const* its, const LineGeom* lgs, int m,
+                                     cudaStream_t s)
+{
+    constexpr int TC = kLineTile;
+    LineBatch B;
+    B.n = m;
+    int64_t ctas = 0;
+    size_t smem = 0;
+    for (int k = 0; k < m; ++k) {
+        B.buf[k] = its[k]->pdm;
+        B.lg[k] = lgs[k];
+        B.gdx[k] = (lgs[k].gx + TC - 1) / TC;
+        B.start[k] = int(ctas);
+        ctas += int64_t(B.gdx[k]) * lgs[k].n_outer * its[k]->K;
+        if (ctas > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+        smem = std::max(smem, line_pass_smem(lgs[k].L));
+    }
+    B.start[m] = int(ctas);
+    if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_dynamic_smem<k_line_sweep_batch<TC, P>>(int(smem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_line_sweep_batch<TC, P>, dim3(unsigned(ctas)), dim3(TC), smem, s, B);
+}
+
+cudaError_t launch_line_pass_batch(const BuildItem* items, int n, int axis, cudaStream_t s)
+{
+    // lines of at most 256 blocks take 8-bit table positions, longer ones 16-bit
+    const BuildItem* its[2][kMaxBuildBatch];
+    LineGeom lgs[2][kMaxBuildBatch];
+    int count[2] = {0, 0};
+    for (int i = 0; i < n && i < kMaxBuildBatch; ++i) {
+        const BuildItem& b = items[i];
+        const LineGeom lg = line_geom(b.pdm, b.g.plane, b.g, axis);
+        if (lg.L <= 1) continue;         // a single block per line: h == g
+        const int c = lg.L <= 256 ? 0 : 1;
+        its[c][count[c]] = &b;
+        lgs[c][count[c]++] = lg;
+    }
+    cudaError_t e = cudaSuccess;
+    if (count[0]) e = launch_line_group<uint8_t>(its[0], lgs[0], count[0], s);
+    if (e == cudaSuccess && count[1]) e = launch_line_group<uint16_t>(its[1], lgs[1], count[1], s);
+    return e;
 }
 
 }  // namespace dmk

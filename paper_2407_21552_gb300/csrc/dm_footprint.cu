@@ -13,6 +13,9 @@
 // once per footprint row it lies in; the b = 4 / apron-1 kernel classifies each voxel row
 // about once and trades apron rows between warps in shared memory.  The x apron reaches
 // the neighbouring block through a warp shuffle.
+#include <algorithm>
+
+#include "dm_build_batch.cuh"
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -29,6 +32,31 @@ __global__ void k_partition_lut(uint8_t* __restrict__ lut, int N, int K, Borders
         if (bd.v[mid] <= i) lo = mid; else hi = mid - 1;
     }
     lut[i] = static_cast<uint8_t>(lo);
+}
+
+// Several partition tables in one grid, 256 entries a CTA; the borders of all tables are
+// packed into the parameters (K + 1 each).
+constexpr int kLutBorderCap = 4096;
+struct LutBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first CTA of each table
+    uint8_t* lut[kMaxBuildBatch];
+    int N[kMaxBuildBatch], K[kMaxBuildBatch], boff[kMaxBuildBatch];
+    int32_t bv[kLutBorderCap];
+};
+
+__global__ void k_partition_lut_batch(const __grid_constant__ LutBatch B)
+{
+    const int t = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const int i = (int(blockIdx.x) - B.start[t]) * int(blockDim.x) + int(threadIdx.x);
+    if (i >= B.N[t]) return;
+    const int32_t* v = B.bv + B.boff[t];
+    int lo = 0, hi = B.K[t] - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (v[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    B.lut[t][i] = static_cast<uint8_t>(lo);
 }
 
 template <typename T>
@@ -88,13 +116,12 @@ __device__ __forceinline__ void classify(unsigned v, int N, const uint8_t* s_cls
 // when a <= b: a ring of per-thread accumulators in shared memory); a block is written
 // when its last slice has been added.
 template <typename T, int NW, int MODE, bool FAST>
-__global__ void __launch_bounds__(kWarps * 32)
-k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
-            const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
-            uint8_t* __restrict__ occ)
+__device__ __forceinline__ void
+footprint_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restrict__ lut,
+              const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+              uint8_t* __restrict__ occ, int cx, int cy, int cz)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint8_t* s_cls = smem;
     uint32_t* s_ring = reinterpret_cast<uint32_t*>(smem + align16(size_t(p.N)));  // [3][NW][256]
@@ -102,11 +129,11 @@ k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ l
     for (int i = tid; i < p.N; i += kWarps * 32)
         s_cls[i] = MODE == kModePom ? lut[i] : uint8_t(cnt[i + 1] > cnt[i]);
     __syncthreads();
-    const int bx = blockIdx.x * 32 + lane, by = blockIdx.y * kWarps + warp;
+    const int bx = cx * 32 + lane, by = cy * kWarps + warp;
     if (by >= p.gy) return;                                   // warp-uniform; no CTA barrier follows
     const int b = p.b, a = p.a, X = p.X, N = p.N;
     const bool col_ok = bx < p.gx;
-    const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
+    const int zb0 = cz * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
     const int zs = max(0, zb0 * b - a), ze = min(p.Z - 1, (zb1 - 1) * b + b - 1 + a);
     const int y0 = max(0, by * b - a), y1 = min(p.Y - 1, by * b + b - 1 + a);
     const int nrows = y1 - y0 + 1;
@@ -261,6 +288,47 @@ k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ l
             }
         }
     }
+}
+
+template <typename T, int NW, int MODE, bool FAST>
+__global__ void __launch_bounds__(kWarps * 32)
+k_footprint(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
+            const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+            uint8_t* __restrict__ occ)
+{
+    pdl_wait();
+    footprint_cta<T, NW, MODE, FAST>(vol, p, lut, cnt, mask, minmax, occ, blockIdx.x, blockIdx.y,
+                                     blockIdx.z);
+}
+
+// Several volumes' POM builds with the general kernel (any b and apron) in one grid, laid
+// out as for the vector kernel's batch.
+struct FpBatchItem {
+    const void* vol;
+    FpParams p;
+    const uint8_t* lut;
+    uint64_t* mask;
+    void* minmax;
+    int gdx, gdy;                              // the volume's grid in x and y
+};
+struct FpBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first CTA of each volume
+    FpBatchItem it[kMaxBuildBatch];
+};
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(kWarps * 32)
+k_footprint_batch(const __grid_constant__ FpBatch B)
+{
+    const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const FpBatchItem& it = B.it[i];
+    const int local = int(blockIdx.x) - B.start[i];
+    const int cx = local % it.gdx, rest = local / it.gdx;
+    pdl_wait();
+    footprint_cta<T, NW, kModePom, false>(static_cast<const T*>(it.vol), it.p, it.lut, nullptr,
+                                          it.mask, it.minmax, nullptr, cx, rest % it.gdy,
+                                          rest / it.gdy);
 }
 
 // Onehot partition / visibility bit of one (already clamped) intensity.
@@ -715,11 +783,13 @@ __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, u
     }
 }
 
+// The CTA (cx, cy, cz) of the vector kernel's grid over one volume; the caller has waited
+// for the previous kernel (pdl_wait).
 template <typename T, int NW, int MODE, bool SHIFT>
-__global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
-k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
-          const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
-          uint8_t* __restrict__ occ, int tab_n, int sh)
+__device__ __forceinline__ void
+pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restrict__ lut,
+            const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+            uint8_t* __restrict__ occ, int tab_n, int sh, int cx, int cy, int cz)
 {
     using Tr = VTraits<T>;
     constexpr int VL = Tr::VL, BL = VL / 4;
@@ -733,7 +803,6 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
     uint4* s_edge = s_rows + 2 * kWarps * 5 * 32;
     // s_edge: [2 slices][kWarps][5 rows][2]: the 16-byte vectors holding the CTA's edge
     // voxels (left of lane 0, right of lane 31), copied with the rows
-    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (!SHIFT) {
         for (int i = tid; i < tab_n; i += kWarps * 32) {
@@ -752,12 +821,12 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
     const unsigned nmax = unsigned(p.N - 1);
     const uint32_t nmax2 = sizeof(T) == 2 ? (min(nmax, 0xFFFFu) * 0x10001u)
                                           : (min(nmax, 0xFFu) * 0x01010101u);
-    const int by = blockIdx.y * kWarps + warp;
-    const int xv0 = (blockIdx.x * 32 + lane) * VL;             // first voxel of the lane
+    const int by = cy * kWarps + warp;
+    const int xv0 = (cx * 32 + lane) * VL;                     // first voxel of the lane
     const bool lane_ok = xv0 < X;
-    const int xe = lane == 0 ? int(blockIdx.x) * 32 * VL - 1 : (int(blockIdx.x) + 1) * 32 * VL;
+    const int xe = lane == 0 ? cx * 32 * VL - 1 : (cx + 1) * 32 * VL;
     const bool edge_ok = (lane == 0 || lane == 31) && xe >= 0 && xe < X;
-    const int zb0 = blockIdx.z * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
+    const int zb0 = cz * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
     const int zs = max(0, 4 * zb0 - 1), ze = min(p.Z - 1, 4 * zb1);
     const int y0 = by * 4;
     const int yx = warp == 0 ? y0 - 1 : y0 + 4;                 // warps 0 / 7: outer apron row
@@ -1019,6 +1088,48 @@ k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut
     if (ze < 4 * zb1) store_block(ze >> 2, aM, aMn, aMx);
 }
 
+template <typename T, int NW, int MODE, bool SHIFT>
+__global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
+k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
+          const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
+          uint8_t* __restrict__ occ, int tab_n, int sh)
+{
+    pdl_wait();
+    pom_vec_cta<T, NW, MODE, SHIFT>(vol, p, lut, cnt, mask, minmax, occ, tab_n, sh, blockIdx.x,
+                                    blockIdx.y, blockIdx.z);
+}
+
+// Several volumes' POM builds in one grid: the CTAs of volume i follow those of volume
+// i - 1, each volume keeping its own one-volume grid (cx fastest, then cy, cz).
+struct PomBatchItem {
+    const void* vol;
+    FpParams p;
+    const uint8_t* lut;
+    uint64_t* mask;
+    void* minmax;
+    int tab_n;
+    int gdx, gdy;                              // the volume's grid in x and y
+};
+struct PomBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first CTA of each volume
+    PomBatchItem it[kMaxBuildBatch];
+};
+
+template <typename T, int NW, bool SHIFT>
+__global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
+k_pom_vec_batch(const __grid_constant__ PomBatch B)
+{
+    const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const PomBatchItem& it = B.it[i];
+    const int local = int(blockIdx.x) - B.start[i];
+    const int cx = local % it.gdx, rest = local / it.gdx;
+    pdl_wait();
+    pom_vec_cta<T, NW, kModePom, SHIFT>(static_cast<const T*>(it.vol), it.p, it.lut, nullptr,
+                                        it.mask, it.minmax, nullptr, it.tab_n, it.p.sh, cx,
+                                        rest % it.gdy, rest / it.gdy);
+}
+
 size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
 template <typename T, int NW, int MODE, bool SHIFT>
@@ -1036,6 +1147,21 @@ cudaError_t launch_pom_vec(const T* v, const FpParams& p, int tab_n, const uint8
     if (e != cudaSuccess) return e;
     return launch_pdl(k_pom_vec<T, NW, MODE, SHIFT>, gv, dim3(kWarps * 32), sm, s, v, p, lut, cnt,
                       mask, minmax, occ, SHIFT ? 0 : tab_n, p.sh);
+}
+
+// The 16-byte vector kernel takes the volume: b = 4, apron 1, rows of whole 16-byte
+// vectors, an aligned volume, at most 4 mask words per lane (so that the per-lane state
+// stays in registers), and partitions by shift or a mask table that fits shared memory.
+template <typename T, int NW>
+bool pom_vec_ok(const void* vol, const Geometry& g, int N, bool shift_ok)
+{
+    constexpr int VL = 16 / int(sizeof(T));
+    constexpr bool kVecOk = sizeof(T) == 2 ? NW <= 2 : NW == 1;
+    if (!kVecOk) return false;
+    const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
+    const size_t tab_bytes = align16(size_t(tab_n) * NW * 4);
+    return g.b == 4 && g.a == 1 && g.X % VL == 0 && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 &&
+           (shift_ok || tab_bytes <= kFpTabLimit);
 }
 
 template <typename T, int NW, int MODE>
@@ -1056,16 +1182,11 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     dim3 grid((g.gx + 31) / 32, (g.gy + kWarps - 1) / kWarps, (g.gz + p.zchunk - 1) / p.zchunk);
     const T* v = static_cast<const T*>(vol);
     cudaError_t e;
-    // 16-byte voxel loads: b = 4, apron 1, rows of whole 16-byte vectors, an aligned volume,
-    // and at most 4 mask words per lane (so that the per-lane state stays in registers)
-    constexpr int VL = 16 / int(sizeof(T));
     constexpr bool kVecOk = sizeof(T) == 2 ? NW <= 2 : NW == 1;
     if constexpr (kVecOk) {
         const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
-        const size_t tab_bytes = align16(size_t(tab_n) * NW * 4);
         const bool shift_ok = MODE == kModePom && shift >= 0;
-        if (g.b == 4 && g.a == 1 && g.X % VL == 0 &&
-            (reinterpret_cast<uintptr_t>(vol) & 15) == 0 && (shift_ok || tab_bytes <= kFpTabLimit)) {
+        if (pom_vec_ok<T, NW>(vol, g, N, shift_ok)) {
             FpParams pv = p;
             pv.zchunk = kVZChunk;
             if constexpr (MODE == kModePom)
@@ -1131,6 +1252,167 @@ cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
 {
     if (g.bpv == 1) return launch_pom_t<uint8_t>(vol, g, N, K, lut, mask, minmax, shift, s);
     return launch_pom_t<uint16_t>(vol, g, N, K, lut, mask, minmax, shift, s);
+}
+
+namespace {
+
+template <typename T, int NW, bool SHIFT>
+cudaError_t launch_pom_vec_batch(const BuildItem* const* its, int m, cudaStream_t s)
+{
+    constexpr int VL = 16 / int(sizeof(T));
+    PomBatch B;
+    B.n = m;
+    int64_t total = 0;
+    size_t tab_bytes = 0;
+    for (int k = 0; k < m; ++k) {
+        const BuildItem& b = *its[k];
+        PomBatchItem& it = B.it[k];
+        FpParams& p = it.p;
+        p.X = b.g.X; p.Y = b.g.Y; p.Z = b.g.Z;
+        p.gx = b.g.gx; p.gy = b.g.gy; p.gz = b.g.gz;
+        p.b = b.g.b; p.a = b.g.a; p.N = b.N;
+        p.W64 = (b.K + 63) / 64;
+        p.zchunk = kVZChunk;
+        p.sh = b.shift;
+        it.vol = b.vol;
+        it.lut = b.lut;
+        it.mask = b.mask;
+        it.minmax = b.minmax;
+        it.tab_n = SHIFT ? 0 : (sizeof(T) == 1 ? (b.N < 256 ? b.N : 256) : b.N);
+        if (!SHIFT) tab_bytes = std::max(tab_bytes, align16(size_t(it.tab_n) * NW * 4));
+        it.gdx = (p.X / VL + 31) / 32;
+        it.gdy = (p.gy + kWarps - 1) / kWarps;
+        B.start[k] = int(total);
+        total += int64_t(it.gdx) * it.gdy * ((p.gz + p.zchunk - 1) / p.zchunk);
+        if (total > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+    }
+    B.start[m] = int(total);
+    const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
+    const size_t rows = size_t(2) * kWarps * 5 * (32 + 2) * 16;
+    const size_t sm = tab_bytes + xb + rows;
+    cudaError_t e = ensure_dynamic_smem<k_pom_vec_batch<T, NW, SHIFT>>(int(sm));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_pom_vec_batch<T, NW, SHIFT>, dim3(unsigned(total)), dim3(kWarps * 32), sm,
+                      s, B);
+}
+
+template <typename T, int NW>
+cudaError_t launch_fp_batch(const BuildItem* const* its, int m, cudaStream_t s)
+{
+    FpBatch B;
+    B.n = m;
+    int64_t total = 0;
+    size_t sm = 0;
+    for (int k = 0; k < m; ++k) {
+        const BuildItem& b = *its[k];
+        FpBatchItem& it = B.it[k];
+        FpParams& p = it.p;
+        p.X = b.g.X; p.Y = b.g.Y; p.Z = b.g.Z;
+        p.gx = b.g.gx; p.gy = b.g.gy; p.gz = b.g.gz;
+        p.b = b.g.b; p.a = b.g.a; p.N = b.N;
+        p.W64 = (b.K + 63) / 64;
+        p.zchunk = 4;
+        p.sh = b.shift;
+        it.vol = b.vol;
+        it.lut = b.lut;
+        it.mask = b.mask;
+        it.minmax = b.minmax;
+        it.gdx = (p.gx + 31) / 32;
+        it.gdy = (p.gy + kWarps - 1) / kWarps;
+        B.start[k] = int(total);
+        total += int64_t(it.gdx) * it.gdy * ((p.gz + p.zchunk - 1) / p.zchunk);
+        if (total > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+        sm = std::max(sm, fp_smem(b.N, NW));
+    }
+    B.start[m] = int(total);
+    cudaError_t e = ensure_dynamic_smem<k_footprint_batch<T, NW>>(int(sm));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_footprint_batch<T, NW>, dim3(unsigned(total)), dim3(kWarps * 32), sm, s,
+                      B);
+}
+
+// The batched POM kernel of a volume: variants 0..5 are the vector kernel (T, mask words,
+// shift), 6..9 the general kernel (T, mask words: any b and apron, K <= 64); -1 when
+// neither takes the volume (K > 64), which then runs its one-volume kernel.
+constexpr int kPomVariants = 10;
+int pom_batch_variant(const BuildItem& b)
+{
+    const bool sh = b.shift >= 0;
+    if (b.g.bpv == 1) {
+        if (b.K <= 32 && pom_vec_ok<uint8_t, 1>(b.vol, b.g, b.N, sh)) return sh ? 1 : 0;
+        return b.K <= 32 ? 6 : (b.K <= 64 ? 7 : -1);
+    }
+    if (b.K <= 32 && pom_vec_ok<uint16_t, 1>(b.vol, b.g, b.N, sh)) return sh ? 3 : 2;
+    if (b.K <= 32) return 8;
+    if (b.K <= 64 && pom_vec_ok<uint16_t, 2>(b.vol, b.g, b.N, sh)) return sh ? 5 : 4;
+    return b.K <= 64 ? 9 : -1;
+}
+
+}  // namespace
+
+cudaError_t launch_partition_lut_batch(const BuildItem* items, int n, cudaStream_t s)
+{
+    LutBatch B;
+    int m = 0, used = 0, ctas = 0;
+    auto flush = [&]() -> cudaError_t {
+        if (m == 0) return cudaSuccess;
+        B.n = m;
+        B.start[m] = ctas;
+        k_partition_lut_batch<<<ctas, 256, 0, s>>>(B);
+        m = used = ctas = 0;
+        return cudaGetLastError();
+    };
+    for (int i = 0; i < n; ++i) {
+        const BuildItem& b = items[i];
+        if (m == kMaxBuildBatch || used + b.K + 1 > kLutBorderCap) {
+            cudaError_t e = flush();
+            if (e != cudaSuccess) return e;
+        }
+        B.lut[m] = b.lut;
+        B.N[m] = b.N;
+        B.K[m] = b.K;
+        B.boff[m] = used;
+        for (int p = 0; p <= b.K; ++p) B.bv[used + p] = b.borders->v[p];
+        used += b.K + 1;
+        B.start[m] = ctas;
+        ctas += (b.N + 255) / 256;
+        ++m;
+    }
+    return flush();
+}
+
+cudaError_t launch_pom_build_batch(const BuildItem* items, int n, cudaStream_t s)
+{
+    const BuildItem* by_variant[kPomVariants][kMaxBuildBatch];
+    int count[kPomVariants] = {};
+    for (int i = 0; i < n && i < kMaxBuildBatch; ++i) {
+        const BuildItem& b = items[i];
+        const int v = pom_batch_variant(b);
+        if (v < 0) {                                   // a one-volume kernel
+            cudaError_t e = launch_pom_build(b.vol, b.g, b.N, b.K, b.lut, b.mask, b.minmax,
+                                             b.shift, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        by_variant[v][count[v]++] = &b;
+    }
+    cudaError_t e = cudaSuccess;
+    if (count[0]) e = launch_pom_vec_batch<uint8_t, 1, false>(by_variant[0], count[0], s);
+    if (e == cudaSuccess && count[1])
+        e = launch_pom_vec_batch<uint8_t, 1, true>(by_variant[1], count[1], s);
+    if (e == cudaSuccess && count[2])
+        e = launch_pom_vec_batch<uint16_t, 1, false>(by_variant[2], count[2], s);
+    if (e == cudaSuccess && count[3])
+        e = launch_pom_vec_batch<uint16_t, 1, true>(by_variant[3], count[3], s);
+    if (e == cudaSuccess && count[4])
+        e = launch_pom_vec_batch<uint16_t, 2, false>(by_variant[4], count[4], s);
+    if (e == cudaSuccess && count[5])
+        e = launch_pom_vec_batch<uint16_t, 2, true>(by_variant[5], count[5], s);
+    if (e == cudaSuccess && count[6]) e = launch_fp_batch<uint8_t, 1>(by_variant[6], count[6], s);
+    if (e == cudaSuccess && count[7]) e = launch_fp_batch<uint8_t, 2>(by_variant[7], count[7], s);
+    if (e == cudaSuccess && count[8]) e = launch_fp_batch<uint16_t, 1>(by_variant[8], count[8], s);
+    if (e == cudaSuccess && count[9]) e = launch_fp_batch<uint16_t, 2>(by_variant[9], count[9], s);
+    return e;
 }
 
 cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const int32_t* cnt,

@@ -73,6 +73,11 @@ class PartitionedDistanceMaps:
 
     # ------------------------------------------------------------------ the three calls
     def build_partitions(self, volume: torch.Tensor, stream=None):
+        self._prepare_build(volume)
+        A.dm_build_partitions(self.ctx, volume.data_ptr(), _stream_handle(stream))
+        self._host_valid = False
+
+    def _prepare_build(self, volume: torch.Tensor):
         assert volume.is_cuda and volume.is_contiguous()
         assert _dtype_code(volume) == self.cfg.dtype
         if self._mask is None or self._pdm is None:    # released or offloaded before
@@ -87,8 +92,6 @@ class PartitionedDistanceMaps:
                     self._minmax = torch.empty(max(16, s.minmax_bytes), **alloc)
                 self._host = None
             self._bind()
-        A.dm_build_partitions(self.ctx, volume.data_ptr(), _stream_handle(stream))
-        self._host_valid = False
 
     def update_tf(self, tf: torch.Tensor, out: torch.Tensor | None = None,
                   active_mask: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -263,3 +266,17 @@ class PartitionedDistanceMaps:
             self.close()
         except Exception:
             pass
+
+
+def build_partitions_batch(maps, volumes, stream=None):
+    """The precompute of several volumes in one libdm call (dm_build_partitions_batch):
+    maps[i] is built from volumes[i] exactly as maps[i].build_partitions(volumes[i])."""
+    maps, volumes = list(maps), list(volumes)
+    if len(maps) != len(volumes):
+        raise ValueError(f"{len(maps)} maps but {len(volumes)} volumes")
+    for m, v in zip(maps, volumes):
+        m._prepare_build(v)
+    A.dm_build_partitions_batch([m.ctx for m in maps], [v.data_ptr() for v in volumes],
+                                _stream_handle(stream))
+    for m in maps:
+        m._host_valid = False

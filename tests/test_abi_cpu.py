@@ -263,3 +263,49 @@ def test_workspace_batch_is_refused_on_the_host():
     finally:
         for ctx in ctxs:
             A.dm_destroy(ctx)
+
+
+def test_batched_precompute_is_refused_on_the_host():
+    """dm_build_partitions_batch checks every item before it launches: a null context, a
+    null or misaligned volume, an unbound context, a context listed twice and two contexts
+    sharing a buffer are refused, each reported in the context concerned."""
+    c8, keep8 = cfg()
+    c16, keep16 = cfg(dtype=A.DM_U16, tf_size=4096)
+    ctxs = [A.dm_create(c8), A.dm_create(c16), A.dm_create(c8)]
+    lib = A.load()
+    base = 1 << 20
+
+    def bind(ctx, k, shared_pdm=None):
+        b = base + k * (1 << 16)
+        pdm = shared_pdm if shared_pdm is not None else b + 4096
+        assert lib.dm_bind(ctx, ctypes.c_void_p(b), ctypes.c_void_p(pdm),
+                           ctypes.c_void_p(b + 8192), ctypes.c_void_p(b + 12288)) == A.DM_OK
+
+    def refused(cs, vols, status, text):
+        with pytest.raises(A.DmError) as e:
+            A.dm_build_partitions_batch(cs, vols, None)
+        assert e.value.status == status, str(e.value)
+        assert text in str(e.value), str(e.value)
+
+    try:
+        A.dm_build_partitions_batch([], [], None)            # nothing to do
+        with pytest.raises(ValueError):
+            A.dm_build_partitions_batch(ctxs, [base], None)
+        vols = [base, base + 64, base + 128]
+        bind(ctxs[0], 0)
+        refused(ctxs, vols, A.DM_ERR_NOT_BOUND, "item 1")     # ctxs[1] unbound
+        bind(ctxs[1], 1)
+        bind(ctxs[2], 2)
+        refused(ctxs, [base, None, base], A.DM_ERR_INVALID_ARG, "item 1: null")
+        refused(ctxs, [base, base + 65, base], A.DM_ERR_INVALID_ARG, "misaligned")  # u16
+        assert lib.dm_build_partitions_batch(None, None, 1, None) == A.DM_ERR_INVALID_ARG
+        assert lib.dm_build_partitions_batch(
+            (ctypes.c_void_p * 1)(ctxs[0]), (ctypes.c_void_p * 1)(base), -1, None) == \
+            A.DM_ERR_INVALID_ARG
+        refused([ctxs[0], None], [base, base], A.DM_ERR_INVALID_ARG, "null context")
+        refused([ctxs[0], ctxs[1], ctxs[0]], vols, A.DM_ERR_INVALID_ARG, "items 0 and 2")
+        bind(ctxs[2], 2, shared_pdm=base + (1 << 16) + 4096)  # ctxs[1]'s pdm
+        refused(ctxs, vols, A.DM_ERR_INVALID_ARG, "items 1 and 2 share")
+    finally:
+        for ctx in ctxs:
+            A.dm_destroy(ctx)
