@@ -14,9 +14,11 @@ from . import _abi  # noqa: F401
 from ._abi import (DM_OK, DM_ERR_INVALID_ARG, DM_ERR_UNSUPPORTED, DM_ERR_CUDA,  # noqa: F401
                    DM_ERR_NOT_BOUND, DM_U8, DM_U16, DM_OCC_MINMAX, DM_OCC_EXACT, DM_INDEX_NONE,
                    DM_INDEX_RANGES, DmError,
-                   dm_create, dm_query_sizes, dm_bind, dm_build_partitions, dm_update_tf,
-                   dm_update_tf_host, dm_full_recompute, dm_set_profile_events,
-                   dm_update_tf_batch, dm_update_tf_noalloc, dm_render,
+                   dm_create, dm_query_sizes, dm_bind, dm_build_partitions,
+                   dm_build_partitions_batch, dm_update_tf, dm_update_tf_host,
+                   dm_full_recompute, dm_set_profile_events, dm_update_tf_batch,
+                   dm_batch_workspace_bytes, dm_update_tf_batch_ws, dm_update_tf_noalloc,
+                   dm_render,
                    dm_sync, dm_destroy,
                    dm_last_error_string, dm_status_string, dm_version, make_config)
 

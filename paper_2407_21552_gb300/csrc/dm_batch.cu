@@ -21,6 +21,7 @@ constexpr int kActThreads = 1024;
 constexpr int kThreads = 256;                  // combine CTA; one work unit = 256 x 16 B
 constexpr int kMaxPlanes = 2048;               // planes of a PDM buffer with the range index
 constexpr int kPad = 8;                        // list padding: covers the largest load group
+static_assert(kMaxPartitions + kPad >= kThreads, "a list buffer covers one entry per thread");
 
 struct Group {
     const uint8_t* pdm;
@@ -237,9 +238,17 @@ k_combine_group(const __grid_constant__ Params P)
         const Group& g = P.g[gi];
         if (gi != loaded) {                                   // this group's planes
             if (loaded >= 0) __syncthreads();                 // the last group's offsets are read
-            n = *g.count;                                     // issued with the list loads
+            // the count and the first kThreads list entries in one round trip: every list
+            // buffer holds at least kMaxPartitions + kPad >= kThreads entries
+            const unsigned l0 = g.list[tid];
+            const unsigned e0 = EMAX > 1 ? unsigned(g.emask[tid]) : 0u;
+            n = *g.count;
             const int cap = min(n + kPad, kList);
-            for (int j = tid; j < cap; j += kThreads) {
+            if (tid < cap) {
+                s_off[tid] = int64_t(l0) * g.plane;
+                if (EMAX > 1) s_emk[tid] = uint8_t(e0);
+            }
+            for (int j = tid + kThreads; j < cap; j += kThreads) {
                 s_off[j] = int64_t(g.list[j]) * g.plane;
                 if (EMAX > 1) s_emk[j] = g.emask[j];
             }

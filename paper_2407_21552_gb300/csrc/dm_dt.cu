@@ -47,6 +47,7 @@ struct XGeom {
     int64_t plane;
     int vec4;           // rows are 4-byte aligned: store 4 outputs as one word
     int vec16;          // rows are 16-byte aligned: store 16 outputs as one vector
+    int rpc;            // block rows per CTA of the K-map pass (short rows share a CTA)
 };
 
 struct SrcMinMax8 {     // min/max occupancy: one visible intensity in [min, max]
@@ -111,6 +112,47 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t r, int lane)
     return r;
 }
 
+// 16 outputs of a bit line: blocks xb = 32 wi + 16 half .. xb + 15 of the row at `row`.
+// The nearest set bit left and right of the 16 blocks comes from the rest of their word or
+// the prev / next tables, then two 16-step scans give every distance, stored as one
+// 16-byte vector where the row allows.
+__device__ __forceinline__ void emit16(const uint32_t* __restrict__ bits,
+                                       const int16_t* __restrict__ prev,
+                                       const int16_t* __restrict__ next, int wi, int half,
+                                       const XGeom& xg, uint8_t* __restrict__ row)
+{
+    const int xb = wi * 32 + half * 16;                      // first block of the item
+    const uint32_t b = bits[wi];
+    const unsigned below = half ? (b & 0xFFFFu) : 0u;        // bits left of the 16 blocks
+    const unsigned above = half ? 0u : (b >> 16);            // bits right of them
+    int last = below ? (wi * 32 + 31 - __clz(below)) : int(prev[wi]);
+    int nxt = above ? (wi * 32 + 16 + __ffs(above) - 1) : int(next[wi]);
+    const unsigned hb = (b >> (16 * half)) & 0xFFFFu;
+    int dl[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if ((hb >> i) & 1u) last = xb + i;
+        dl[i] = xb + i - last;
+    }
+    unsigned pk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 15; i >= 0; --i) {
+        if ((hb >> i) & 1u) nxt = xb + i;
+        const int d = min(min(dl[i], nxt - (xb + i)), 255);
+        pk[i >> 2] |= unsigned(d) << (8 * (i & 3));
+    }
+    uint8_t* dst = row + xb;
+    if (xg.vec16 && xb + 16 <= xg.gx) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else if (xg.vec4 && xb + 16 <= xg.gx) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) reinterpret_cast<uint32_t*>(dst)[k] = pk[k];
+    } else {
+        for (int i = 0; i < 16 && xb + i < xg.gx; ++i)
+            dst[i] = uint8_t(pk[i >> 2] >> (8 * (i & 3)));
+    }
+}
+
 // K planes from the POM masks; one CTA per block row, 64 partitions (one mask word) at a
 // time.  Shared memory: bits [cap][nw] uint32, prev / next [cap][nw] int16, cap = min(64, K).
 // Outputs: one thread per (partition, 16 consecutive blocks); the nearest set bit left and
@@ -154,37 +196,64 @@ __device__ __forceinline__ void xpass_mask_row(const uint64_t* __restrict__ mask
         for (int it = tid; it < np * nh; it += kThreads) {
             const int q = it / nh, hw = it - q * nh;
             const int wi = hw >> 1, half = hw & 1;
-            const int xb = wi * 32 + half * 16;              // first block of the item
-            if (xb >= xg.gx) continue;
-            const uint32_t b = s_bits[q * nw + wi];
-            const unsigned below = half ? (b & 0xFFFFu) : 0u;    // bits left of the 16 blocks
-            const unsigned above = half ? 0u : (b >> 16);        // bits right of them
-            int last = below ? (wi * 32 + 31 - __clz(below)) : int(s_prev[q * nw + wi]);
-            int nxt = above ? (wi * 32 + 16 + __ffs(above) - 1) : int(s_next[q * nw + wi]);
-            const unsigned hb = (b >> (16 * half)) & 0xFFFFu;
-            int dl[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if ((hb >> i) & 1u) last = xb + i;
-                dl[i] = xb + i - last;
+            if (wi * 32 + half * 16 >= xg.gx) continue;
+            emit16(s_bits + q * nw, s_prev + q * nw, s_next + q * nw, wi, half, xg,
+                   out + int64_t(w * 64 + q) * xg.plane + rbase);
+        }
+    }
+}
+
+// The same for rows of at most a few words: xg.rpc consecutive block rows per CTA (rows
+// row0 .. row0 + rpc - 1), so that short rows still give every warp a word of blocks and
+// every thread an item.  Shared memory: bits [rpc][cap][nw], prev / next likewise.
+template <int W>
+__device__ __forceinline__ void xpass_mask_rows(const uint64_t* __restrict__ mask, int K,
+                                                const XGeom& xg, uint8_t* __restrict__ out,
+                                                int row0)
+{
+    extern __shared__ uint32_t s_mem[];
+    const int nw = xg.nw;
+    const int cap = min(64, K);
+    const int nrow = min(xg.rpc, xg.rows - row0);            // rows of this CTA
+    const int line = cap * nw;                               // words of one row's lines
+    uint32_t* s_bits = s_mem;
+    int16_t* s_prev = reinterpret_cast<int16_t*>(s_mem + xg.rpc * line);
+    int16_t* s_next = s_prev + xg.rpc * line;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nh = 2 * nw;
+#pragma unroll 1
+    for (int w = 0; w < W; ++w) {
+        const int np = min(64, K - w * 64);
+        if (w) __syncthreads();                              // previous chunk consumed
+        for (int t = warp; t < nrow * nw; t += kThreads / 32) {   // warp-uniform
+            const int r = t / nw, wi = t - r * nw;
+            const int x = wi * 32 + lane;
+            const int64_t rbase = int64_t(row0 + r) * xg.gx;
+            const uint64_t m = x < xg.gx ? mask[(rbase + x) * W + w] : 0;
+            uint32_t* bits = s_bits + r * line;
+            const uint32_t lo = warp_transpose32(uint32_t(m), lane);
+            if (lane < np) bits[lane * nw + wi] = lo;
+            if (np > 32) {                                   // warp-uniform
+                const uint32_t hi = warp_transpose32(uint32_t(m >> 32), lane);
+                if (lane + 32 < np) bits[(lane + 32) * nw + wi] = hi;
             }
-            unsigned pk[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int i = 15; i >= 0; --i) {
-                if ((hb >> i) & 1u) nxt = xb + i;
-                const int d = min(min(dl[i], nxt - (xb + i)), 255);
-                pk[i >> 2] |= unsigned(d) << (8 * (i & 3));
-            }
-            uint8_t* dst = out + int64_t(w * 64 + q) * xg.plane + rbase + xb;
-            if (xg.vec16 && xb + 16 <= xg.gx) {
-                *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            } else if (xg.vec4 && xb + 16 <= xg.gx) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) reinterpret_cast<uint32_t*>(dst)[k] = pk[k];
-            } else {
-                for (int i = 0; i < 16 && xb + i < xg.gx; ++i)
-                    dst[i] = uint8_t(pk[i >> 2] >> (8 * (i & 3)));
-            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nrow * np; q += kThreads) {
+            const int r = q / np;
+            const int o = r * line + (q - r * np) * nw;
+            nearest_tables(s_bits + o, nw, s_prev + o, s_next + o);
+        }
+        __syncthreads();
+        const int per_row = np * nh;
+        for (int it = tid; it < nrow * per_row; it += kThreads) {
+            const int r = it / per_row, rem = it - r * per_row;
+            const int q = rem / nh, hw = rem - q * nh;
+            const int wi = hw >> 1, half = hw & 1;
+            if (wi * 32 + half * 16 >= xg.gx) continue;
+            const int o = r * line + q * nw;
+            emit16(s_bits + o, s_prev + o, s_next + o, wi, half, xg,
+                   out + int64_t(w * 64 + q) * xg.plane + int64_t(row0 + r) * xg.gx);
         }
     }
 }
@@ -197,7 +266,16 @@ k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __rest
     xpass_mask_row<W>(mask, K, xg, out, blockIdx.x);         // row = z * gy + y
 }
 
-// Several volumes' x passes in one grid: one CTA per block row, volume after volume.
+template <int W>
+__global__ void __launch_bounds__(kThreads)
+k_xpass_mask_packed(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
+{
+    pdl_wait();
+    xpass_mask_rows<W>(mask, K, xg, out, int(blockIdx.x) * xg.rpc);
+}
+
+// Several volumes' x passes in one grid: one CTA per xg.rpc block rows, volume after
+// volume.
 struct XBatch {
     int n;
     int start[kMaxBuildBatch + 1];             // first row (CTA) of each volume
@@ -212,8 +290,12 @@ __global__ void __launch_bounds__(kThreads)
 k_xpass_mask_batch(const __grid_constant__ XBatch B)
 {
     const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const XGeom& xg = B.xg[i];
     pdl_wait();
-    xpass_mask_row<W>(B.mask[i], B.K[i], B.xg[i], B.out[i], int(blockIdx.x) - B.start[i]);
+    if (xg.rpc > 1)
+        xpass_mask_rows<W>(B.mask[i], B.K[i], xg, B.out[i], (int(blockIdx.x) - B.start[i]) * xg.rpc);
+    else
+        xpass_mask_row<W>(B.mask[i], B.K[i], xg, B.out[i], int(blockIdx.x) - B.start[i]);
 }
 
 template <typename Src>
@@ -291,7 +373,17 @@ XGeom xgeom(const Geometry& g, int64_t plane, const void* out)
              ((reinterpret_cast<uintptr_t>(out) & 3) == 0);
     x.vec16 = (g.gx % 16 == 0) && (plane % 16 == 0) &&
               ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+    x.rpc = 1;
     return x;
+}
+
+// Block rows per CTA of the K-map x pass: enough rows that a chunk of up to 64 maps gives
+// about one 16-block item per thread (at most 8 rows).
+static int xpass_rows_per_cta(int nw, int K)
+{
+    const int per_row = (K < 64 ? K : 64) * 2 * nw;
+    const int r = kThreads / per_row;
+    return r < 1 ? 1 : (r > 8 ? 8 : r);
 }
 
 // ------------------------------------------------------------------------ y / z passes
@@ -441,6 +533,7 @@ k_line_sweep(uint8_t* buf, LineGeom lg)
     line_sweep_tile<TC, P>(buf, lg, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+
 // Several volumes' y (or z) passes in one grid; each volume keeps its one-volume grid
 // (tiles along x fastest, then the outer index, then the plane).
 struct LineBatch {
@@ -471,10 +564,11 @@ size_t line_pass_smem(int L)
     return sweep_tile_bytes(L, kLineTile) + size_t(257) * kLineTile * pos_bytes;
 }
 
+
 size_t xpass_smem(int gx, int K)
 {
     const int nw = (gx + 31) / 32;
-    const size_t mask_pass = size_t(K < 64 ? K : 64) * nw * 8;
+    const size_t mask_pass = size_t(xpass_rows_per_cta(nw, K)) * (K < 64 ? K : 64) * nw * 8;
     const size_t single = size_t(kThreads / 32) * nw * 8;
     return mask_pass > single ? mask_pass : single;
 }
@@ -483,12 +577,20 @@ cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, ui
                               cudaStream_t s)
 {
     XGeom xg = xgeom(g, g.plane, pdm);
-    const size_t smem = size_t(K < 64 ? K : 64) * xg.nw * 8;
+    xg.rpc = xpass_rows_per_cta(xg.nw, K);
+    const size_t smem = size_t(xg.rpc) * (K < 64 ? K : 64) * xg.nw * 8;
     const int W = (K + 63) / 64;
+    const unsigned ctas = unsigned((xg.rows + xg.rpc - 1) / xg.rpc);
     cudaError_t e = cudaSuccess;
     switch (W) {
 #define DM_XPASS_CASE(WW)                                                                    \
     case WW:                                                                                 \
+        if (xg.rpc > 1) {                                                                    \
+            e = ensure_dynamic_smem<k_xpass_mask_packed<WW>>(int(smem));                     \
+            if (e != cudaSuccess) return e;                                                  \
+            return launch_pdl(k_xpass_mask_packed<WW>, dim3(ctas), dim3(kThreads), smem, s,  \
+                              mask, K, xg, pdm);                                             \
+        }                                                                                    \
         e = ensure_dynamic_smem<k_xpass_mask<WW>>(int(smem));                                \
         if (e != cudaSuccess) return e;                                                      \
         return launch_pdl(k_xpass_mask<WW>, dim3(xg.rows), dim3(kThreads), smem, s, mask, K, \
@@ -571,7 +673,7 @@ static cudaError_t launch_xpass_group(const BuildItem* const* its, int m, cudaSt
 {
     XBatch B;
     B.n = m;
-    int64_t rows = 0;
+    int64_t rows = 0;                                        // CTAs
     size_t smem = 0;
     for (int k = 0; k < m; ++k) {
         const BuildItem& b = *its[k];
@@ -579,10 +681,11 @@ static cudaError_t launch_xpass_group(const BuildItem* const* its, int m, cudaSt
         B.out[k] = b.pdm;
         B.K[k] = b.K;
         B.xg[k] = xgeom(b.g, b.g.plane, b.pdm);
+        B.xg[k].rpc = xpass_rows_per_cta(B.xg[k].nw, b.K);
         B.start[k] = int(rows);
-        rows += B.xg[k].rows;
+        rows += (B.xg[k].rows + B.xg[k].rpc - 1) / B.xg[k].rpc;
         if (rows > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
-        smem = std::max(smem, size_t(b.K < 64 ? b.K : 64) * B.xg[k].nw * 8);
+        smem = std::max(smem, size_t(B.xg[k].rpc) * (b.K < 64 ? b.K : 64) * B.xg[k].nw * 8);
     }
     B.start[m] = int(rows);
     cudaError_t e = ensure_dynamic_smem<k_xpass_mask_batch<W>>(int(smem));
