@@ -603,6 +603,12 @@ k_footprint41(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__
 // footprint reduction of §3.1 whatever order the parts are combined in.
 constexpr int kVZChunk = 8;                    // block-slices per CTA
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+
 template <typename T>
 struct VTraits;
 template <>
@@ -785,7 +791,7 @@ __device__ __forceinline__ void lane_row(const uint4& q, unsigned ev, bool ok, u
 
 // The CTA (cx, cy, cz) of the vector kernel's grid over one volume; the caller has waited
 // for the previous kernel (pdl_wait).
-template <typename T, int NW, int MODE, bool SHIFT>
+template <typename T, int NW, int MODE, bool SHIFT, bool RAG>
 __device__ __forceinline__ void
 pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restrict__ lut,
             const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
@@ -802,7 +808,10 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
     // s_rows: [2 slices][kWarps][5 rows][32 lanes]: the voxel rows, copied one slice ahead
     uint4* s_edge = s_rows + 2 * kWarps * 5 * 32;
     // s_edge: [2 slices][kWarps][5 rows][2]: the 16-byte vectors holding the CTA's edge
-    // voxels (left of lane 0, right of lane 31), copied with the rows
+    // voxels (left of lane 0, right of lane 31), copied with the rows.  RAG (rows of any
+    // length and alignment): the same space is [2 slices][kWarps][5 rows][34], the aligned
+    // 16-byte vectors under the warp's row segment: slot 0 the one before lane 0's, slot
+    // 1 + l lane l's, slot 33 the one after lane 31's
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (!SHIFT) {
         for (int i = tid; i < tab_n; i += kWarps * 32) {
@@ -826,6 +835,27 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
     const bool lane_ok = xv0 < X;
     const int xe = lane == 0 ? cx * 32 * VL - 1 : (cx + 1) * 32 * VL;
     const bool edge_ok = (lane == 0 || lane == 31) && xe >= 0 && xe < X;
+    // RAG: a lane's 16 bytes start `ra` bytes into its aligned vector (ra = the row's
+    // address mod 16) and reach into the next one; voxels past the row end are replaced by
+    // the row's last voxel, which changes no footprint it shares a block with
+    constexpr int S = int(sizeof(T));
+    constexpr int PW = Tr::PER_WORD;
+    const bool tail = RAG && lane_ok && X - xv0 < VL;
+    uint32_t keep[4];
+    int lw = 0, lsub = 0;
+    if (RAG) {
+        const int nv = X - xv0;                                // valid voxels, if < VL
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            keep[k] = 0;
+#pragma unroll
+            for (int i = 0; i < PW; ++i)
+                if (k * PW + i < nv) keep[k] |= (S == 1 ? 0xFFu : 0xFFFFu) << (8 * S * i);
+        }
+        lw = (nv - 1) / PW;
+        lsub = (nv - 1) % PW;
+    }
+    const uintptr_t vaddr = reinterpret_cast<uintptr_t>(vol);
     const int zb0 = cz * p.zchunk, zb1 = min(p.gz, zb0 + p.zchunk);
     const int zs = max(0, 4 * zb0 - 1), ze = min(p.Z - 1, 4 * zb1);
     const int y0 = by * 4;
@@ -847,6 +877,26 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
                            const unsigned (&Mx)[BL]) {
         if (bz < zb0 || bz >= zb1 || by >= p.gy || !lane_ok) return;
         const int64_t blk0 = (int64_t(bz) * p.gy + by) * p.gx + xv0 / 4;
+        if (RAG) {                                             // blocks inside the row only
+#pragma unroll
+            for (int j = 0; j < BL; ++j) {
+                if (xv0 / 4 + j >= p.gx) break;
+                if (MODE == kModePom) {
+                    mask[blk0 + j] = uint64_t(M[j][0]) |
+                                     (NW > 1 ? (uint64_t(M[j][NW > 1 ? 1 : 0]) << 32) : 0ull);
+                    if (want_mm) {
+                        if (sizeof(T) == 1)
+                            reinterpret_cast<uint16_t*>(minmax)[blk0 + j] =
+                                uint16_t(Mn[j] | (Mx[j] << 8));
+                        else
+                            reinterpret_cast<uint32_t*>(minmax)[blk0 + j] = Mn[j] | (Mx[j] << 16);
+                    }
+                } else {
+                    occ[blk0 + j] = uint8_t(M[j][0] != 0);
+                }
+            }
+            return;
+        }
         if (MODE == kModePom) {
             uint64_t m64[BL];
 #pragma unroll
@@ -890,6 +940,22 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
     // copies of slice z's rows (and edge vectors) into buffer `bsel`, asynchronous, one group
     auto fetch = [&](int z, int bsel) {
         const T* slice = vol + int64_t(z) * Y * rowX;
+        if (RAG) {
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                if (!row_ok(t)) continue;                      // warp-uniform
+                const T* row = slice + int64_t(row_y(t)) * rowX;
+                const int ra = int(reinterpret_cast<uintptr_t>(row) & 15);
+                const unsigned char* a = reinterpret_cast<const unsigned char*>(row) + xv0 * S - ra;
+                uint4* dst = s_rows + ((bsel * kWarps + warp) * 5 + t) * 34;
+                // every copied vector holds a byte of the row
+                if (xv0 * S - ra < X * S) cp_async16(dst + lane + 1, a);
+                if (lane == 0 && cx > 0) cp_async16(dst, a - 16);
+                if (lane == 31 && (xv0 + VL) * S - ra < X * S) cp_async16(dst + 33, a + 16);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            return;
+        }
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
             const bool ok = row_ok(t);
@@ -917,11 +983,49 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
         if (z < ze) fetch(z + 1, bsel ^ 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");     // this lane's copies of z
+        if (RAG) __syncwarp();                                // and the neighbours' (RAG)
         const uint4* rows = s_rows + (bsel * kWarps + warp) * 5 * 32 + lane;
         const uint4* edges = s_edge + (bsel * kWarps + warp) * 5 * 2 + eslot;
+        const uint4* rrow = s_rows + (bsel * kWarps + warp) * 5 * 34;      // RAG
+        // RAG: the offset of row t's first byte within its aligned vector
+        auto ra_of = [&](int t) {
+            return int((vaddr + uint64_t((int64_t(z) * Y + row_y(t)) * rowX) * S) & 15);
+        };
+        // the lane's 16 bytes of row t
+        auto vec_of = [&](int t) -> uint4 {
+            if (!RAG) return rows[t * 32];
+            const uint4 va = rrow[t * 34 + lane + 1], vb = rrow[t * 34 + lane + 2];
+            const uint32_t v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+            const int ra = ra_of(t);
+            uint32_t w[5];
+            switch (ra >> 2) {                                // warp-uniform
+            case 0: w[0] = v[0]; w[1] = v[1]; w[2] = v[2]; w[3] = v[3]; w[4] = v[4]; break;
+            case 1: w[0] = v[1]; w[1] = v[2]; w[2] = v[3]; w[3] = v[4]; w[4] = v[5]; break;
+            case 2: w[0] = v[2]; w[1] = v[3]; w[2] = v[4]; w[3] = v[5]; w[4] = v[6]; break;
+            default: w[0] = v[3]; w[1] = v[4]; w[2] = v[5]; w[3] = v[6]; w[4] = v[7]; break;
+            }
+            const unsigned sh8 = unsigned(ra & 3) * 8;
+            uint32_t q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = __funnelshift_r(w[k], w[k + 1], sh8);
+            if (tail) {                                       // past the row end: the last voxel
+                const uint32_t lwv = lw == 0 ? q[0] : (lw == 1 ? q[1] : (lw == 2 ? q[2] : q[3]));
+                const uint32_t last = Tr::get(lwv, lsub);
+                const uint32_t rep = S == 1 ? last * 0x01010101u : last * 0x00010001u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k] = (q[k] & keep[k]) | (rep & ~keep[k]);
+            }
+            return make_uint4(q[0], q[1], q[2], q[3]);
+        };
         // the edge voxel of row t (lanes 0 / 31), else none
         auto edge_of = [&](int t) -> unsigned {
             if (!(row_ok(t) && edge_ok)) return 0xFFFFFFFFu;
+            if (RAG) {
+                const uint32_t* rb = reinterpret_cast<const uint32_t*>(rrow + t * 34);
+                const int ra = ra_of(t);
+                const int off = lane == 0 ? 16 + ra - S : 33 * 16 + ra;
+                return (rb[off >> 2] >> (8 * (off & 3))) & (S == 1 ? 0xFFu : 0xFFFFu);
+            }
             const uint4 q = edges[t * 2];
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
             return lane == 0 ? VTraits<T>::get(w[3], VTraits<T>::PER_WORD - 1)
@@ -969,7 +1073,7 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
             // one row on its own: rows 0, 3 and the apron row
             auto single = [&](int t) {
                 const bool ok = row_ok(t) && lane_ok;
-                lane_row<T, NW, SHIFT>(ok ? rows[t * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(t), ok,
+                lane_row<T, NW, SHIFT>(ok ? vec_of(t) : make_uint4(0u, 0u, 0u, 0u), edge_of(t), ok,
                                        nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) wmx[k] = ok ? wv[k] : 0u;
@@ -991,14 +1095,14 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
             unsigned en12, ex12;
             {
                 const bool ok = row_ok(1) && lane_ok;
-                lane_row<T, NW, SHIFT>(ok ? rows[1 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(1), ok,
+                lane_row<T, NW, SHIFT>(ok ? vec_of(1) : make_uint4(0u, 0u, 0u, 0u), edge_of(1), ok,
                                        nmax2, nmax, sh, s_tab, c12, f12, l12, e12, en12, ex12, mn12);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) mx12[k] = ok ? mn12[k] : 0u;
             }
             {
                 const bool ok = row_ok(2) && lane_ok;
-                lane_row<T, NW, SHIFT>(ok ? rows[2 * 32] : make_uint4(0u, 0u, 0u, 0u), edge_of(2), ok,
+                lane_row<T, NW, SHIFT>(ok ? vec_of(2) : make_uint4(0u, 0u, 0u, 0u), edge_of(2), ok,
                                        nmax2, nmax, sh, s_tab, core, first, last, em, emn, emx, wv);
 #pragma unroll
                 for (int j = 0; j < BL; ++j)
@@ -1088,15 +1192,15 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
     if (ze < 4 * zb1) store_block(ze >> 2, aM, aMn, aMx);
 }
 
-template <typename T, int NW, int MODE, bool SHIFT>
+template <typename T, int NW, int MODE, bool SHIFT, bool RAG>
 __global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
 k_pom_vec(const T* __restrict__ vol, FpParams p, const uint8_t* __restrict__ lut,
           const int32_t* __restrict__ cnt, uint64_t* __restrict__ mask, void* minmax,
           uint8_t* __restrict__ occ, int tab_n, int sh)
 {
     pdl_wait();
-    pom_vec_cta<T, NW, MODE, SHIFT>(vol, p, lut, cnt, mask, minmax, occ, tab_n, sh, blockIdx.x,
-                                    blockIdx.y, blockIdx.z);
+    pom_vec_cta<T, NW, MODE, SHIFT, RAG>(vol, p, lut, cnt, mask, minmax, occ, tab_n, sh,
+                                         blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Several volumes' POM builds in one grid: the CTAs of volume i follow those of volume
@@ -1116,7 +1220,7 @@ struct PomBatch {
     PomBatchItem it[kMaxBuildBatch];
 };
 
-template <typename T, int NW, bool SHIFT>
+template <typename T, int NW, bool SHIFT, bool RAG>
 __global__ void __launch_bounds__(kWarps * 32, (SHIFT && sizeof(T) == 2) ? 3 : 2)
 k_pom_vec_batch(const __grid_constant__ PomBatch B)
 {
@@ -1125,14 +1229,14 @@ k_pom_vec_batch(const __grid_constant__ PomBatch B)
     const int local = int(blockIdx.x) - B.start[i];
     const int cx = local % it.gdx, rest = local / it.gdx;
     pdl_wait();
-    pom_vec_cta<T, NW, kModePom, SHIFT>(static_cast<const T*>(it.vol), it.p, it.lut, nullptr,
-                                        it.mask, it.minmax, nullptr, it.tab_n, it.p.sh, cx,
-                                        rest % it.gdy, rest / it.gdy);
+    pom_vec_cta<T, NW, kModePom, SHIFT, RAG>(static_cast<const T*>(it.vol), it.p, it.lut,
+                                             nullptr, it.mask, it.minmax, nullptr, it.tab_n,
+                                             it.p.sh, cx, rest % it.gdy, rest / it.gdy);
 }
 
 size_t fp_smem(int N, int NW) { return align16(size_t(N)) + size_t(3) * (NW + 1) * kWarps * 32 * 4; }
 
-template <typename T, int NW, int MODE, bool SHIFT>
+template <typename T, int NW, int MODE, bool SHIFT, bool RAG>
 cudaError_t launch_pom_vec(const T* v, const FpParams& p, int tab_n, const uint8_t* lut,
                            const int32_t* cnt, uint64_t* mask, void* minmax, uint8_t* occ,
                            cudaStream_t s)
@@ -1142,26 +1246,28 @@ cudaError_t launch_pom_vec(const T* v, const FpParams& p, int tab_n, const uint8
     const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
     const size_t rows = size_t(2) * kWarps * 5 * (32 + 2) * 16;
     const size_t sm = tab_bytes + xb + rows;
-    dim3 gv((p.X / VL + 31) / 32, (p.gy + kWarps - 1) / kWarps, (p.gz + p.zchunk - 1) / p.zchunk);
-    cudaError_t e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE, SHIFT>>(int(sm));
+    dim3 gv(((p.X + VL - 1) / VL + 31) / 32, (p.gy + kWarps - 1) / kWarps,
+            (p.gz + p.zchunk - 1) / p.zchunk);
+    cudaError_t e = ensure_dynamic_smem<k_pom_vec<T, NW, MODE, SHIFT, RAG>>(int(sm));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_pom_vec<T, NW, MODE, SHIFT>, gv, dim3(kWarps * 32), sm, s, v, p, lut, cnt,
-                      mask, minmax, occ, SHIFT ? 0 : tab_n, p.sh);
+    return launch_pdl(k_pom_vec<T, NW, MODE, SHIFT, RAG>, gv, dim3(kWarps * 32), sm, s, v, p, lut,
+                      cnt, mask, minmax, occ, SHIFT ? 0 : tab_n, p.sh);
 }
 
-// The 16-byte vector kernel takes the volume: b = 4, apron 1, rows of whole 16-byte
-// vectors, an aligned volume, at most 4 mask words per lane (so that the per-lane state
-// stays in registers), and partitions by shift or a mask table that fits shared memory.
+// Whether the 16-byte vector kernel takes the volume: b = 4, apron 1, at most 4 mask words
+// per lane (so that the per-lane state stays in registers), and partitions by shift or a
+// mask table that fits shared memory.  0: no; 1: rows of whole 16-byte vectors and an
+// aligned volume; 2: other rows (the ragged-row form, RAG).
 template <typename T, int NW>
-bool pom_vec_ok(const void* vol, const Geometry& g, int N, bool shift_ok)
+int pom_vec_kind(const void* vol, const Geometry& g, int N, bool shift_ok)
 {
     constexpr int VL = 16 / int(sizeof(T));
     constexpr bool kVecOk = sizeof(T) == 2 ? NW <= 2 : NW == 1;
-    if (!kVecOk) return false;
+    if (!kVecOk) return 0;
     const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
     const size_t tab_bytes = align16(size_t(tab_n) * NW * 4);
-    return g.b == 4 && g.a == 1 && g.X % VL == 0 && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 &&
-           (shift_ok || tab_bytes <= kFpTabLimit);
+    if (g.b != 4 || g.a != 1 || !(shift_ok || tab_bytes <= kFpTabLimit)) return 0;
+    return g.X % VL == 0 && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 ? 1 : 2;
 }
 
 template <typename T, int NW, int MODE>
@@ -1186,14 +1292,21 @@ cudaError_t launch_fp_t(const void* vol, const Geometry& g, int N, int K, const 
     if constexpr (kVecOk) {
         const int tab_n = sizeof(T) == 1 ? (N < 256 ? N : 256) : N;
         const bool shift_ok = MODE == kModePom && shift >= 0;
-        if (pom_vec_ok<T, NW>(vol, g, N, shift_ok)) {
+        const int kind = pom_vec_kind<T, NW>(vol, g, N, shift_ok);
+        if (kind > 0) {
             FpParams pv = p;
             pv.zchunk = kVZChunk;
-            if constexpr (MODE == kModePom)
+            if constexpr (MODE == kModePom) {
                 if (shift_ok)
-                    return launch_pom_vec<T, NW, MODE, true>(v, pv, tab_n, lut, cnt, mask, minmax,
-                                                             occ, s);
-            return launch_pom_vec<T, NW, MODE, false>(v, pv, tab_n, lut, cnt, mask, minmax, occ, s);
+                    return kind == 1 ? launch_pom_vec<T, NW, MODE, true, false>(
+                                           v, pv, tab_n, lut, cnt, mask, minmax, occ, s)
+                                     : launch_pom_vec<T, NW, MODE, true, true>(
+                                           v, pv, tab_n, lut, cnt, mask, minmax, occ, s);
+            }
+            return kind == 1 ? launch_pom_vec<T, NW, MODE, false, false>(v, pv, tab_n, lut, cnt,
+                                                                          mask, minmax, occ, s)
+                             : launch_pom_vec<T, NW, MODE, false, true>(v, pv, tab_n, lut, cnt,
+                                                                         mask, minmax, occ, s);
         }
     }
     if (fast && g.a == 1) {
@@ -1256,7 +1369,7 @@ cudaError_t launch_pom_build(const void* vol, const Geometry& g, int N, int K,
 
 namespace {
 
-template <typename T, int NW, bool SHIFT>
+template <typename T, int NW, bool SHIFT, bool RAG>
 cudaError_t launch_pom_vec_batch(const BuildItem* const* its, int m, cudaStream_t s)
 {
     constexpr int VL = 16 / int(sizeof(T));
@@ -1280,7 +1393,7 @@ cudaError_t launch_pom_vec_batch(const BuildItem* const* its, int m, cudaStream_
         it.minmax = b.minmax;
         it.tab_n = SHIFT ? 0 : (sizeof(T) == 1 ? (b.N < 256 ? b.N : 256) : b.N);
         if (!SHIFT) tab_bytes = std::max(tab_bytes, align16(size_t(it.tab_n) * NW * 4));
-        it.gdx = (p.X / VL + 31) / 32;
+        it.gdx = ((p.X + VL - 1) / VL + 31) / 32;
         it.gdy = (p.gy + kWarps - 1) / kWarps;
         B.start[k] = int(total);
         total += int64_t(it.gdx) * it.gdy * ((p.gz + p.zchunk - 1) / p.zchunk);
@@ -1290,10 +1403,24 @@ cudaError_t launch_pom_vec_batch(const BuildItem* const* its, int m, cudaStream_
     const size_t xb = size_t(2) * 2 * kWarps * (VL / 4) * (NW + 1) * 32 * 4;
     const size_t rows = size_t(2) * kWarps * 5 * (32 + 2) * 16;
     const size_t sm = tab_bytes + xb + rows;
-    cudaError_t e = ensure_dynamic_smem<k_pom_vec_batch<T, NW, SHIFT>>(int(sm));
+    cudaError_t e = ensure_dynamic_smem<k_pom_vec_batch<T, NW, SHIFT, RAG>>(int(sm));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_pom_vec_batch<T, NW, SHIFT>, dim3(unsigned(total)), dim3(kWarps * 32), sm,
-                      s, B);
+    return launch_pdl(k_pom_vec_batch<T, NW, SHIFT, RAG>, dim3(unsigned(total)), dim3(kWarps * 32),
+                      sm, s, B);
+}
+
+// The four vector-kernel variants of one (T, mask words) slot: shift or table, whole or
+// ragged rows (variant index 2 * shift + ragged).
+template <typename T, int NW>
+cudaError_t launch_vec_slot(const BuildItem* const (*by)[kMaxBuildBatch], const int* count,
+                            cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (count[0]) e = launch_pom_vec_batch<T, NW, false, false>(by[0], count[0], s);
+    if (e == cudaSuccess && count[1]) e = launch_pom_vec_batch<T, NW, false, true>(by[1], count[1], s);
+    if (e == cudaSuccess && count[2]) e = launch_pom_vec_batch<T, NW, true, false>(by[2], count[2], s);
+    if (e == cudaSuccess && count[3]) e = launch_pom_vec_batch<T, NW, true, true>(by[3], count[3], s);
+    return e;
 }
 
 template <typename T, int NW>
@@ -1331,21 +1458,25 @@ cudaError_t launch_fp_batch(const BuildItem* const* its, int m, cudaStream_t s)
                       B);
 }
 
-// The batched POM kernel of a volume: variants 0..5 are the vector kernel (T, mask words,
-// shift), 6..9 the general kernel (T, mask words: any b and apron, K <= 64); -1 when
-// neither takes the volume (K > 64), which then runs its one-volume kernel.
-constexpr int kPomVariants = 10;
+// The batched POM kernel of a volume.  Variants 0..11: the vector kernel, slot (uint8, 1
+// mask word), (uint16, 1), (uint16, 2) times 4 + 2 * shift + ragged; 12..15: the general
+// kernel (any b and apron, K <= 64) for (uint8, 1), (uint8, 2), (uint16, 1), (uint16, 2);
+// -1 when neither takes the volume (K > 64), which then runs its one-volume kernel.
+constexpr int kPomVariants = 16;
 int pom_batch_variant(const BuildItem& b)
 {
     const bool sh = b.shift >= 0;
+    int slot = -1, kind = 0;
     if (b.g.bpv == 1) {
-        if (b.K <= 32 && pom_vec_ok<uint8_t, 1>(b.vol, b.g, b.N, sh)) return sh ? 1 : 0;
-        return b.K <= 32 ? 6 : (b.K <= 64 ? 7 : -1);
+        if (b.K <= 32) { slot = 0; kind = pom_vec_kind<uint8_t, 1>(b.vol, b.g, b.N, sh); }
+    } else if (b.K <= 32) {
+        slot = 1; kind = pom_vec_kind<uint16_t, 1>(b.vol, b.g, b.N, sh);
+    } else if (b.K <= 64) {
+        slot = 2; kind = pom_vec_kind<uint16_t, 2>(b.vol, b.g, b.N, sh);
     }
-    if (b.K <= 32 && pom_vec_ok<uint16_t, 1>(b.vol, b.g, b.N, sh)) return sh ? 3 : 2;
-    if (b.K <= 32) return 8;
-    if (b.K <= 64 && pom_vec_ok<uint16_t, 2>(b.vol, b.g, b.N, sh)) return sh ? 5 : 4;
-    return b.K <= 64 ? 9 : -1;
+    if (slot >= 0 && kind > 0) return 4 * slot + (sh ? 2 : 0) + (kind == 2 ? 1 : 0);
+    if (b.K > 64) return -1;
+    return 12 + (b.g.bpv == 1 ? 0 : 2) + (b.K <= 32 ? 0 : 1);
 }
 
 }  // namespace
@@ -1396,22 +1527,13 @@ cudaError_t launch_pom_build_batch(const BuildItem* items, int n, cudaStream_t s
         }
         by_variant[v][count[v]++] = &b;
     }
-    cudaError_t e = cudaSuccess;
-    if (count[0]) e = launch_pom_vec_batch<uint8_t, 1, false>(by_variant[0], count[0], s);
-    if (e == cudaSuccess && count[1])
-        e = launch_pom_vec_batch<uint8_t, 1, true>(by_variant[1], count[1], s);
-    if (e == cudaSuccess && count[2])
-        e = launch_pom_vec_batch<uint16_t, 1, false>(by_variant[2], count[2], s);
-    if (e == cudaSuccess && count[3])
-        e = launch_pom_vec_batch<uint16_t, 1, true>(by_variant[3], count[3], s);
-    if (e == cudaSuccess && count[4])
-        e = launch_pom_vec_batch<uint16_t, 2, false>(by_variant[4], count[4], s);
-    if (e == cudaSuccess && count[5])
-        e = launch_pom_vec_batch<uint16_t, 2, true>(by_variant[5], count[5], s);
-    if (e == cudaSuccess && count[6]) e = launch_fp_batch<uint8_t, 1>(by_variant[6], count[6], s);
-    if (e == cudaSuccess && count[7]) e = launch_fp_batch<uint8_t, 2>(by_variant[7], count[7], s);
-    if (e == cudaSuccess && count[8]) e = launch_fp_batch<uint16_t, 1>(by_variant[8], count[8], s);
-    if (e == cudaSuccess && count[9]) e = launch_fp_batch<uint16_t, 2>(by_variant[9], count[9], s);
+    cudaError_t e = launch_vec_slot<uint8_t, 1>(by_variant + 0, count + 0, s);
+    if (e == cudaSuccess) e = launch_vec_slot<uint16_t, 1>(by_variant + 4, count + 4, s);
+    if (e == cudaSuccess) e = launch_vec_slot<uint16_t, 2>(by_variant + 8, count + 8, s);
+    if (e == cudaSuccess && count[12]) e = launch_fp_batch<uint8_t, 1>(by_variant[12], count[12], s);
+    if (e == cudaSuccess && count[13]) e = launch_fp_batch<uint8_t, 2>(by_variant[13], count[13], s);
+    if (e == cudaSuccess && count[14]) e = launch_fp_batch<uint16_t, 1>(by_variant[14], count[14], s);
+    if (e == cudaSuccess && count[15]) e = launch_fp_batch<uint16_t, 2>(by_variant[15], count[15], s);
     return e;
 }
 

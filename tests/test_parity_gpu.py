@@ -261,6 +261,54 @@ def test_vector_footprint_edges(shape, N, K, dt, borders):
     eng.close()
 
 
+RAGGED_CASES = [
+    # shape (Z, Y, X), N, K, dtype, borders, volume offset in voxels: rows that are not a
+    # whole number of 16-byte vectors (every row starts at another offset within its
+    # vector), partial blocks at the row end, an odd number of blocks per row, several
+    # CTAs along x, and volumes that start off a 16-byte boundary
+    ((23, 37, 70), 4096, 64, np.uint16, None, 0),     # 9 lanes, the last one 6 voxels
+    ((20, 30, 267), 4096, 32, np.uint16, None, 0),    # 2 CTAs in x; gx = 67; 3-voxel block
+    ((17, 21, 5), 4096, 16, np.uint16, None, 0),      # one partial lane
+    ((19, 23, 531), 256, 32, np.uint8, None, 0),      # 2 CTAs in x; gx = 133
+    ((15, 26, 37), 200, 16, np.uint8, None, 0),       # N < 256: voxels clamped
+    ((21, 26, 99), 4096, 41, np.uint16,
+     [0, 1] + [int(v) for v in np.linspace(90, 4000, 39).astype(int)] + [4096], 0),
+    ((18, 22, 64), 4096, 32, np.uint16, None, 1),     # whole-vector rows, unaligned volume
+    ((13, 19, 45), 256, 16, np.uint8, None, 3),       # ragged rows, unaligned volume
+    ((16, 17, 130), 4096, 64, np.uint16, None, 5),
+]
+
+
+@pytest.mark.parametrize("shape,N,K,dt,borders,offset", RAGGED_CASES)
+def test_vector_footprint_ragged_rows(shape, N, K, dt, borders, offset):
+    rng = np.random.default_rng(sum(shape) * 13 + K + offset)
+    vol = rand_volume(rng, shape, N, dt)
+    top = 0xFFFF if dt == np.uint16 else 0xFF
+    if N - 1 < top:
+        vol.reshape(-1)[::47] = min(top, N + 7)      # above the TF domain: treated as N - 1
+    eng = _engine(vol, 4, 1, N, K, borders)
+    src = vol if dt == np.uint8 else vol.view(np.int16)
+    flat = torch.from_numpy(np.ascontiguousarray(src).reshape(-1)).cuda()
+    buf = torch.zeros(flat.numel() + offset + 8, dtype=flat.dtype, device="cuda")
+    vd = buf[offset: offset + flat.numel()]
+    vd.copy_(flat)
+    eng.build_partitions(vd)
+    eng.sync()
+    ref = oracle.build_partitions(vol, 4, 1, N, K, borders)
+    mask_o, pdm_o, vmin_o, vmax_o = ref
+    assert np.array_equal(eng.mask_words().cpu().numpy().view(np.uint64), mask_o), "POM masks"
+    mm = eng.minmax_pairs().cpu().numpy()
+    if dt == np.uint16:
+        mm = mm.view(np.uint16)
+    assert np.array_equal(mm[..., 0].astype(np.int64), vmin_o.astype(np.int64)), "block min"
+    assert np.array_equal(mm[..., 1].astype(np.int64), vmax_o.astype(np.int64)), "block max"
+    assert np.array_equal(eng.pdm_planes().cpu().numpy(), pdm_o), "PDM planes"
+    bd = np.asarray(borders) if borders is not None else T.uniform_borders(N, K)
+    tfs = T.tf_edit_sequence(int(rng.integers(1 << 30)), N, 3) + T.special_tfs(N, bd)[:4]
+    check_updates(eng, vd, vol, ref, tfs, 4, 1, borders, exact_every=2)
+    eng.close()
+
+
 @pytest.mark.parametrize("shape", [(4 * 600, 8, 8), (8, 4 * 300, 8), (8, 8, 4 * 700)])
 def test_long_lines_clamp_at_255(shape):
     """One occupied corner; lines of 300-700 blocks need the 255 clamp on every axis."""
