@@ -455,7 +455,7 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __rest
 // type of the table's positions: uint8_t for lines of at most 256 blocks (each sweep then
 // numbers its rows 0..L-1 from a cleared table), else uint16_t (the backward sweep's
 // positions follow the forward sweep's, so one clearing serves both).
-template <int TC, typename P>
+template <int TC, typename P, bool VEC>
 __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg, int cx,
                                                 int cy, int cz)
 {
@@ -473,7 +473,7 @@ __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg
     // ---- stage the tile (asynchronous copies, all in flight at once); note whether it can
     //      change at all (some value >= 2 and not everything 255)
     int any_big = 0, any_not255 = 0;
-    if (lg.vec_ok) {
+    if (VEC) {                               // lg.vec_ok
         for (int i = tid; i < L * V; i += TC) {
             const int r = i / V, q = i - r * V;
             const unsigned sa = static_cast<unsigned>(
@@ -494,14 +494,20 @@ __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg
                 any_big |= ((w4[k] & 0xFEFEFEFEu) != 0);     // a byte >= 2
             }
         }
-    } else {
-        for (int i = tid; i < L * TC; i += TC) {
-            const int r = i / TC, c = i - r * TC;
-            uint8_t v = 255;
-            if (c < ncols) v = base[int64_t(r) * lg.s + c];
-            s_tile[i] = v;
-            any_not255 |= (c < ncols) && (v != 255);
-            any_big |= (c < ncols) && (v >= 2);
+    } else {                                 // thread c stages column c, 8 rows per round
+        const bool col_ok = tid < ncols;
+        for (int r0 = 0; r0 < L; r0 += 8) {
+            unsigned v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                v[k] = col_ok && r0 + k < L ? base[int64_t(r0 + k) * lg.s + tid] : 255u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (r0 + k >= L) break;
+                s_tile[(r0 + k) * TC + tid] = uint8_t(v[k]);
+                any_not255 |= v[k] != 255u;
+                any_big |= col_ok && v[k] >= 2u;
+            }
         }
     }
     // the table starts at position 0 everywhere: a sweep's T is >= 0 from its first row on,
@@ -525,12 +531,12 @@ __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg
     }
 }
 
-template <int TC, typename P>
+template <int TC, typename P, bool VEC>
 __global__ void __launch_bounds__(TC)
 k_line_sweep(uint8_t* buf, LineGeom lg)
 {
     pdl_wait();
-    line_sweep_tile<TC, P>(buf, lg, blockIdx.x, blockIdx.y, blockIdx.z);
+    line_sweep_tile<TC, P, VEC>(buf, lg, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 
@@ -544,7 +550,7 @@ struct LineBatch {
     int gdx[kMaxBuildBatch];                   // tiles along x
 };
 
-template <int TC, typename P>
+template <int TC, typename P, bool VEC>
 __global__ void __launch_bounds__(TC)
 k_line_sweep_batch(const __grid_constant__ LineBatch B)
 {
@@ -553,7 +559,7 @@ k_line_sweep_batch(const __grid_constant__ LineBatch B)
     const int gdx = B.gdx[i], n_outer = B.lg[i].n_outer;
     const int cx = local % gdx, rest = local / gdx;
     pdl_wait();
-    line_sweep_tile<TC, P>(B.buf[i], B.lg[i], cx, rest % n_outer, rest / n_outer);
+    line_sweep_tile<TC, P, VEC>(B.buf[i], B.lg[i], cx, rest % n_outer, rest / n_outer);
 }
 
 }  // namespace
@@ -658,14 +664,18 @@ cudaError_t launch_line_pass(uint8_t* buf, int P, int64_t plane, const Geometry&
     const size_t smem = line_pass_smem(lg.L);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
     dim3 grid((g.gx + TC - 1) / TC, lg.n_outer, P);
+    cudaError_t e;
+#define DM_SWEEP_LAUNCH(PP, VV)                                                              \
+    e = ensure_dynamic_smem<k_line_sweep<TC, PP, VV>>(int(smem));                            \
+    if (e != cudaSuccess) return e;                                                          \
+    return launch_pdl(k_line_sweep<TC, PP, VV>, grid, dim3(TC), smem, s, buf, lg);
     if (lg.L <= 256) {
-        cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC, uint8_t>>(int(smem));
-        if (e != cudaSuccess) return e;
-        return launch_pdl(k_line_sweep<TC, uint8_t>, grid, dim3(TC), smem, s, buf, lg);
+        if (lg.vec_ok) { DM_SWEEP_LAUNCH(uint8_t, true) }
+        DM_SWEEP_LAUNCH(uint8_t, false)
     }
-    cudaError_t e = ensure_dynamic_smem<k_line_sweep<TC, uint16_t>>(int(smem));
-    if (e != cudaSuccess) return e;
-    return launch_pdl(k_line_sweep<TC, uint16_t>, grid, dim3(TC), smem, s, buf, lg);
+    if (lg.vec_ok) { DM_SWEEP_LAUNCH(uint16_t, true) }
+    DM_SWEEP_LAUNCH(uint16_t, false)
+#undef DM_SWEEP_LAUNCH
 }
 
 template <int W>
@@ -710,7 +720,7 @@ cudaError_t launch_xpass_mask_batch(const BuildItem* items, int n, cudaStream_t 
     return e;
 }
 
-template <typename P>
+template <typename P, bool VEC>
 static cudaError_t launch_line_group(const BuildItem* const* its, const LineGeom* lgs, int m,
                                      cudaStream_t s)
 {
@@ -730,28 +740,34 @@ static cudaError_t launch_line_group(const BuildItem* const* its, const LineGeom
     }
     B.start[m] = int(ctas);
     if (smem > size_t(kLineSmemLimit)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_dynamic_smem<k_line_sweep_batch<TC, P>>(int(smem));
+    cudaError_t e = ensure_dynamic_smem<k_line_sweep_batch<TC, P, VEC>>(int(smem));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_line_sweep_batch<TC, P>, dim3(unsigned(ctas)), dim3(TC), smem, s, B);
+    return launch_pdl(k_line_sweep_batch<TC, P, VEC>, dim3(unsigned(ctas)), dim3(TC), smem, s, B);
 }
 
 cudaError_t launch_line_pass_batch(const BuildItem* items, int n, int axis, cudaStream_t s)
 {
-    // lines of at most 256 blocks take 8-bit table positions, longer ones 16-bit
-    const BuildItem* its[2][kMaxBuildBatch];
-    LineGeom lgs[2][kMaxBuildBatch];
-    int count[2] = {0, 0};
+    // lines of at most 256 blocks take 8-bit table positions, longer ones 16-bit; tiles of
+    // whole 16-byte rows are staged as vectors
+    const BuildItem* its[4][kMaxBuildBatch];
+    LineGeom lgs[4][kMaxBuildBatch];
+    int count[4] = {0, 0, 0, 0};
     for (int i = 0; i < n && i < kMaxBuildBatch; ++i) {
         const BuildItem& b = items[i];
         const LineGeom lg = line_geom(b.pdm, b.g.plane, b.g, axis);
         if (lg.L <= 1) continue;         // a single block per line: h == g
-        const int c = lg.L <= 256 ? 0 : 1;
+        const int c = (lg.L <= 256 ? 0 : 2) + (lg.vec_ok ? 1 : 0);
         its[c][count[c]] = &b;
         lgs[c][count[c]++] = lg;
     }
     cudaError_t e = cudaSuccess;
-    if (count[0]) e = launch_line_group<uint8_t>(its[0], lgs[0], count[0], s);
-    if (e == cudaSuccess && count[1]) e = launch_line_group<uint16_t>(its[1], lgs[1], count[1], s);
+    if (count[0]) e = launch_line_group<uint8_t, false>(its[0], lgs[0], count[0], s);
+    if (e == cudaSuccess && count[1])
+        e = launch_line_group<uint8_t, true>(its[1], lgs[1], count[1], s);
+    if (e == cudaSuccess && count[2])
+        e = launch_line_group<uint16_t, false>(its[2], lgs[2], count[2], s);
+    if (e == cudaSuccess && count[3])
+        e = launch_line_group<uint16_t, true>(its[3], lgs[3], count[3], s);
     return e;
 }
 

@@ -103,6 +103,7 @@ class Scheduler:
         self._uses = 0
         self.waiting = collections.deque()     # specs not admitted yet
         self.pending = collections.OrderedDict()   # sid -> deque of requests
+        self._npending = 0                     # requests in all queues
         self.inflight = []                     # batches on the device
         self.busy = set()                      # sessions with an edit on the device
         self.free_slots = list(range(self.slots))
@@ -176,7 +177,7 @@ class Scheduler:
         """Leave once no edit of the session is pending or in flight; frees its budget."""
         if any(r.session == sid for b in self.inflight for r in b.requests):
             raise RuntimeError("session has edits in flight")
-        self.pending.pop(sid, None)
+        self._npending -= len(self.pending.pop(sid, ()))
         self.last_use.pop(sid, None)
         if sid not in self.sessions and sid not in self.evicted:
             if not self.withdraw_waiting(sid):  # never admitted: just leave the queue
@@ -207,6 +208,7 @@ class Scheduler:
                     rid=self._rid)
         self._rid += 1
         self.pending.setdefault(sid, collections.deque()).append(r)
+        self._npending += 1
         return r
 
     def cancel(self, req: Request) -> bool:
@@ -217,6 +219,7 @@ class Scheduler:
         if req.cancelled or q is None or req not in q:
             return False
         q.remove(req)
+        self._npending -= 1
         req.cancelled = True
         self.stats.cancelled += 1
         return True
@@ -231,6 +234,7 @@ class Scheduler:
         for r in q:
             r.cancelled = True
         q.clear()
+        self._npending -= n
         self.stats.cancelled += n
         if sid in self.evicted:                 # nothing left to readmit it for
             self.waiting = collections.deque(sp for sp in self.waiting if sp.sid != sid)
@@ -246,7 +250,7 @@ class Scheduler:
         return False
 
     def has_work(self) -> bool:
-        return bool(self.inflight) or any(self.pending.values())
+        return bool(self.inflight) or self._npending > 0
 
     # ------------------------------------------------------------------ progress
     def poll(self):
@@ -265,7 +269,7 @@ class Scheduler:
                 still.append(b)
         self.inflight = still
         self._admit_waiting()                   # room freed by retired batches
-        while self.free_slots:
+        while self.free_slots and self._npending:
             reqs = []
             for sid, q in self.pending.items():
                 if q and sid not in self.busy and sid in self.sessions:
@@ -276,6 +280,7 @@ class Scheduler:
                         break
             if not reqs:
                 break
+            self._npending -= len(reqs)
             slot = self.free_slots.pop(0)
             t = self.ex.clock()
             for r in reqs:
@@ -327,11 +332,15 @@ class DeviceExecutor:
         self.results = {}                     # rid -> device D' (kept if keep_results)
         self.keep_results = False
         self.ws = None                        # per-slot workspaces of the several-edit batch
+        from . import _abi as A
+        self._lib = A.load()
         if self.edits_per_session > 1 and mode == "partitioned":
-            from . import _abi as A
             self.ws_bytes = A.dm_batch_workspace_bytes(max_batch)
             self.ws = [torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
                        for _ in range(slots)]
+        # per slot: the C item array of its batches (filled in place) and the raw stream
+        self._items = [(A.dm_batch_item * max_batch)() for _ in range(slots)]
+        self._sh = [ctypes.c_void_p(st.cuda_stream) for st in self.streams]
 
     def clock(self):
         return time.perf_counter()
@@ -347,12 +356,14 @@ class DeviceExecutor:
             spec.payload["engine"] = eng
         eng = spec.payload["engine"]
         E = self.edits_per_session
+        tf = [[torch.empty((eng.N, 4), dtype=torch.float32, device=self.device)
+               for _ in range(E)] for _ in self.streams]
+        out = [[torch.empty(eng.G, dtype=torch.uint8, device=self.device) for _ in range(E)]
+               for _ in self.streams]
         self.sessions[spec.sid] = dict(
-            engine=eng, volume=volume, spec=spec,
-            tf=[[torch.empty((eng.N, 4), dtype=torch.float32, device=self.device)
-                 for _ in range(E)] for _ in self.streams],
-            out=[[torch.empty(eng.G, dtype=torch.uint8, device=self.device) for _ in range(E)]
-                 for _ in self.streams])
+            engine=eng, volume=volume, spec=spec, tf=tf, out=out,
+            tf_ptr=[[t.data_ptr() for t in row] for row in tf],
+            out_ptr=[[t.data_ptr() for t in row] for row in out])
     def release(self, sid):
         """The session left (nothing of it pending or on the device): maps built at
         admission are dropped, so their device memory goes back to torch's allocator."""
@@ -381,42 +392,56 @@ class DeviceExecutor:
         from . import _abi as A
         torch = self.torch
         st = self.streams[slot]
-        items, outs, used = [], [], {}
-        with torch.cuda.stream(st):
-            for r in requests:
-                s = self.sessions[r.session]
-                eng = s["engine"]
-                if eng.ready_event is not None:       # built or readmitted: maps in transit
-                    st.wait_event(eng.ready_event)
-                    if eng.ready_event.query():
-                        eng.ready_event = None
-                e = used.get(r.session, 0)            # the request's place in its session
-                used[r.session] = e + 1
-                out = s["out"][slot][e]
-                if self.tf_from_host and not r.tf.is_cuda and r.tf.is_pinned():
-                    tfp = r.tf.data_ptr()             # read in place; the request keeps it alive
-                else:
-                    tf = s["tf"][slot][e]
-                    tf.copy_(r.tf, non_blocking=True)
-                    tfp = tf.data_ptr()
-                items.append((eng.ctx, tfp, out.data_ptr()))
-                outs.append(out)
-            sh = ctypes.c_void_p(st.cuda_stream)
-            if self.mode == "partitioned":
-                if any(v > 1 for v in used.values()):
-                    A.dm_update_tf_batch_ws(items, None, self.ws[slot].data_ptr(),
-                                            self.ws_bytes, sh)
-                else:
-                    A.dm_update_tf_batch(items, None, sh)
+        sh = self._sh[slot]
+        arr = self._items[slot]
+        copies, used = [], {}
+        for i, r in enumerate(requests):
+            s = self.sessions[r.session]
+            eng = s["engine"]
+            if eng.ready_event is not None:       # built or readmitted: maps in transit
+                st.wait_event(eng.ready_event)
+                if eng.ready_event.query():
+                    eng.ready_event = None
+            e = used.get(r.session, 0)            # the request's place in its session
+            used[r.session] = e + 1
+            if self.tf_from_host and not r.tf.is_cuda and r.tf.is_pinned():
+                tfp = r.tf.data_ptr()             # read in place; the request keeps it alive
             else:
-                for r, (ctx, tfp, outp) in zip(requests, items):
-                    v = self.sessions[r.session]["volume"]
-                    A.dm_full_recompute(ctx, v.data_ptr() if v is not None else None, tfp, outp, sh)
-            if self.keep_results:
-                for r, out in zip(requests, outs):
-                    self.results[r.rid] = out.clone()
-            ev = self.events[slot]
-            ev.record(st)
+                copies.append((s["tf"][slot][e], r.tf))
+                tfp = s["tf_ptr"][slot][e]
+            it = arr[i]
+            it.ctx = eng.ctx
+            it.d_tf_rgba = tfp
+            it.d_out = s["out_ptr"][slot][e]
+        if copies:
+            with torch.cuda.stream(st):
+                for dst, src in copies:
+                    dst.copy_(src, non_blocking=True)
+        n = len(requests)
+        if self.mode == "partitioned":
+            if any(v > 1 for v in used.values()):
+                st_ = self._lib.dm_update_tf_batch_ws(arr, n, None, self.ws[slot].data_ptr(),
+                                                      self.ws_bytes, sh)
+                where = "dm_update_tf_batch_ws"
+            else:
+                st_ = self._lib.dm_update_tf_batch(arr, n, None, sh)
+                where = "dm_update_tf_batch"
+            if st_ != A.DM_OK:
+                raise A.DmError(st_, where, self._lib.dm_last_error_string(arr[0].ctx).decode())
+        else:
+            for i, r in enumerate(requests):
+                v = self.sessions[r.session]["volume"]
+                A.dm_full_recompute(arr[i].ctx, v.data_ptr() if v is not None else None,
+                                    arr[i].d_tf_rgba, arr[i].d_out, sh)
+        if self.keep_results:
+            with torch.cuda.stream(st):
+                used = {}
+                for r in requests:
+                    e = used.get(r.session, 0)
+                    used[r.session] = e + 1
+                    self.results[r.rid] = self.sessions[r.session]["out"][slot][e].clone()
+        ev = self.events[slot]
+        ev.record(st)
         return ev
 
     def done(self, handle):

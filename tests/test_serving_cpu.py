@@ -331,6 +331,7 @@ def test_random_workload_with_eviction_keeps_invariants(seed):
         assert sch.used <= sch.budget
         assert sch.used == sum(sp.device_bytes for sp in sch.sessions.values())
         assert not (set(sch.sessions) & set(sch.evicted))
+        assert sch._npending == sum(len(q) for q in sch.pending.values())
     # drain: the device finishes everything
     for _ in range(2000):
         if not sch.has_work():
