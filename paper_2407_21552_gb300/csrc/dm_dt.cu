@@ -48,6 +48,7 @@ struct XGeom {
     int vec4;           // rows are 4-byte aligned: store 4 outputs as one word
     int vec16;          // rows are 16-byte aligned: store 16 outputs as one vector
     int rpc;            // block rows per CTA of the K-map pass (short rows share a CTA)
+    int warp_rows;      // rows of at most 96 blocks, at most 64 maps: one warp per row
 };
 
 struct SrcMinMax8 {     // min/max occupancy: one visible intensity in [min, max]
@@ -258,6 +259,65 @@ __device__ __forceinline__ void xpass_mask_rows(const uint64_t* __restrict__ mas
     }
 }
 
+// Rows of at most 32 NW blocks (NW <= 3) and at most 64 maps: one warp per block row, no
+// shared memory and no barrier.  Lane l holds the mask words of blocks l, 32 + l, ...; for
+// each map one ballot per word gives the row's bit line, and each lane takes the nearest
+// set bit left and right of each of its blocks from its own word or, beyond it, from the
+// nearest set bits of the other words (the same for the whole warp).
+template <int NW>
+__device__ __forceinline__ void xpass_warp_row(const uint64_t* __restrict__ mask, int K,
+                                               const XGeom& xg, uint8_t* __restrict__ out,
+                                               int row, int lane)
+{
+    const int64_t rbase = int64_t(row) * xg.gx;
+    uint64_t m[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int x = 32 * w + lane;
+        m[w] = x < xg.gx ? mask[rbase + x] : 0ull;
+    }
+    const unsigned lomask = 0xFFFFFFFFu >> (31 - lane);     // bits 0..lane
+    const unsigned himask = 0xFFFFFFFFu << lane;            // bits lane..31
+    uint8_t* plane = out + rbase;
+    for (int p = 0; p < K; ++p, plane += xg.plane) {
+        unsigned b[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) b[w] = __ballot_sync(0xFFFFFFFFu, unsigned(m[w] >> p) & 1u);
+        int lft[NW], rgt[NW];                              // nearest set bit beyond word w
+        int last = kNone;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            lft[w] = last;
+            if (b[w]) last = 32 * w + 31 - __clz(b[w]);
+        }
+        int first = kFar;
+#pragma unroll
+        for (int w = NW - 1; w >= 0; --w) {
+            rgt[w] = first;
+            if (b[w]) first = 32 * w + __ffs(b[w]) - 1;
+        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int x = 32 * w + lane;
+            if (x >= xg.gx) continue;
+            const unsigned lo = b[w] & lomask, hi = b[w] & himask;
+            const int l = lo ? 32 * w + 31 - __clz(lo) : lft[w];
+            const int r = hi ? 32 * w + __ffs(hi) - 1 : rgt[w];
+            plane[x] = uint8_t(min(min(x - l, r - x), 255));
+        }
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kThreads)
+k_xpass_warp_rows(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
+{
+    pdl_wait();
+    const int row = int(blockIdx.x) * (kThreads / 32) + int(threadIdx.x >> 5);
+    if (row >= xg.rows) return;                             // warp-uniform; no barrier
+    xpass_warp_row<NW>(mask, K, xg, out, row, int(threadIdx.x & 31));
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads)
 k_xpass_mask(const uint64_t* __restrict__ mask, int K, XGeom xg, uint8_t* __restrict__ out)
@@ -292,6 +352,15 @@ k_xpass_mask_batch(const __grid_constant__ XBatch B)
     const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
     const XGeom& xg = B.xg[i];
     pdl_wait();
+    if (W == 1 && xg.warp_rows) {                           // one warp per row, 8 rows per CTA
+        const int row = (int(blockIdx.x) - B.start[i]) * (kThreads / 32) + int(threadIdx.x >> 5);
+        if (row >= xg.rows) return;                         // warp-uniform; no barrier
+        const int lane = int(threadIdx.x & 31);
+        if (xg.nw == 1) xpass_warp_row<1>(B.mask[i], B.K[i], xg, B.out[i], row, lane);
+        else if (xg.nw == 2) xpass_warp_row<2>(B.mask[i], B.K[i], xg, B.out[i], row, lane);
+        else xpass_warp_row<3>(B.mask[i], B.K[i], xg, B.out[i], row, lane);
+        return;
+    }
     if (xg.rpc > 1)
         xpass_mask_rows<W>(B.mask[i], B.K[i], xg, B.out[i], (int(blockIdx.x) - B.start[i]) * xg.rpc);
     else
@@ -374,8 +443,12 @@ XGeom xgeom(const Geometry& g, int64_t plane, const void* out)
     x.vec16 = (g.gx % 16 == 0) && (plane % 16 == 0) &&
               ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     x.rpc = 1;
+    x.warp_rows = 0;
     return x;
 }
+
+// The one-warp-per-row x pass takes rows of at most 3 words and at most 64 maps.
+static bool xpass_warp_rows_ok(int nw, int K) { return nw <= 3 && K <= 64; }
 
 // Block rows per CTA of the K-map x pass: enough rows that a chunk of up to 64 maps gives
 // about one 16-block item per thread (at most 8 rows).
@@ -583,6 +656,15 @@ cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, ui
                               cudaStream_t s)
 {
     XGeom xg = xgeom(g, g.plane, pdm);
+    if (xpass_warp_rows_ok(xg.nw, K)) {
+        xg.warp_rows = 1;
+        const unsigned ctas = unsigned((xg.rows + kThreads / 32 - 1) / (kThreads / 32));
+        if (xg.nw == 1)
+            return launch_pdl(k_xpass_warp_rows<1>, dim3(ctas), dim3(kThreads), 0, s, mask, K, xg, pdm);
+        if (xg.nw == 2)
+            return launch_pdl(k_xpass_warp_rows<2>, dim3(ctas), dim3(kThreads), 0, s, mask, K, xg, pdm);
+        return launch_pdl(k_xpass_warp_rows<3>, dim3(ctas), dim3(kThreads), 0, s, mask, K, xg, pdm);
+    }
     xg.rpc = xpass_rows_per_cta(xg.nw, K);
     const size_t smem = size_t(xg.rpc) * (K < 64 ? K : 64) * xg.nw * 8;
     const int W = (K + 63) / 64;
@@ -691,11 +773,16 @@ static cudaError_t launch_xpass_group(const BuildItem* const* its, int m, cudaSt
         B.out[k] = b.pdm;
         B.K[k] = b.K;
         B.xg[k] = xgeom(b.g, b.g.plane, b.pdm);
-        B.xg[k].rpc = xpass_rows_per_cta(B.xg[k].nw, b.K);
         B.start[k] = int(rows);
-        rows += (B.xg[k].rows + B.xg[k].rpc - 1) / B.xg[k].rpc;
+        if (W == 1 && xpass_warp_rows_ok(B.xg[k].nw, b.K)) {     // one warp per row
+            B.xg[k].warp_rows = 1;
+            rows += (B.xg[k].rows + kThreads / 32 - 1) / (kThreads / 32);
+        } else {
+            B.xg[k].rpc = xpass_rows_per_cta(B.xg[k].nw, b.K);
+            rows += (B.xg[k].rows + B.xg[k].rpc - 1) / B.xg[k].rpc;
+            smem = std::max(smem, size_t(B.xg[k].rpc) * (b.K < 64 ? b.K : 64) * B.xg[k].nw * 8);
+        }
         if (rows > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
-        smem = std::max(smem, size_t(B.xg[k].rpc) * (b.K < 64 ? b.K : 64) * B.xg[k].nw * 8);
     }
     B.start[m] = int(rows);
     cudaError_t e = ensure_dynamic_smem<k_xpass_mask_batch<W>>(int(smem));

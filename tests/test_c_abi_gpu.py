@@ -1,6 +1,7 @@
 """libdm driven from plain C (tests/c/abi_driver.c): caller-owned device buffers from
-cudaMalloc, build, updates through dm_update_tf and dm_update_tf_host, full recomputes;
-every PDM plane and map equals the oracle's (its C source is compiled into the driver)."""
+cudaMalloc, build, updates through dm_update_tf and dm_update_tf_host, full recomputes, and
+a batched precompute and batched update of three volumes; every PDM plane and map equals
+the oracle's (its C source is compiled into the driver)."""
 import os
 import shutil
 import subprocess
