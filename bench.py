@@ -63,6 +63,44 @@ NCU_TRAFFIC = {
 }
 
 
+# Warp instructions of the one-time precompute (its five launches: partition table, POM
+# masks, x pass, y pass, z pass) from one ncu capture (smsp__inst_executed.sum, one pass),
+# keyed by workload, with the hash of the kernel code it was taken on; the precompute's ALU
+# roofline is reported as null once that code has changed.
+NCU_PRECOMPUTE_INST = {
+    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 339,585,744 +
+    # 695,549,952
+    "mid": {"source_sha": "5fc059e251d96c33", "warp_instructions": 1739165251.0},
+    # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,014,630,284 +
+    # 1,361,257,104 (y, 256-block lines) + 2,685,460,480 (z, 449-block lines)
+    "large": {"source_sha": "5fc059e251d96c33", "warp_instructions": 6875451524.0},
+}
+
+
+def precompute_kernel_sources(csrc):
+    """The precompute kernels' files and the headers they include."""
+    return [os.path.join(csrc, f) for f in ("dm_footprint.cu", "dm_dt.cu", "dm_internal.cuh",
+                                            "dm_build_batch.cuh")]
+
+
+def precompute_alu(workload, pre_ms, clk, sms):
+    """The precompute against the integer-ALU roofline: warp instructions (committed ncu
+    capture) per second over the issue capacity, 4 warp instructions per cycle per SM at
+    the median SM clock sampled under load; None without a capture of the current code."""
+    tr = NCU_PRECOMPUTE_INST.get(workload)
+    csrc = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc")
+    if not tr or tr.get("source_sha") != code_sha(*precompute_kernel_sources(csrc)):
+        return None
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = 4.0 * sms * mhz * 1e6
+    achieved = tr["warp_instructions"] / (pre_ms * 1e-3)
+    return {"bound": "alu", "warp_instructions": tr["warp_instructions"],
+            "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak,
+            "peak_source": f"4 warp instructions per cycle per SM x {sms} SMs x {mhz:.0f} MHz "
+                           "(median SM clock sampled during the timed region)"}
+
+
 def update_kernel_sources(csrc):
     """The update kernel's file and the header whose device helpers it inlines."""
     return [os.path.join(csrc, "dm_update.cu"), os.path.join(csrc, "dm_internal.cuh")]
@@ -499,7 +537,9 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
         "precompute": {"ms": pre_ms, "min_ms": float(np.min(pre)),
                        "algorithmic_gb": pre_bytes / 1e9,
                        "gbs": pre_bytes / (pre_ms * 1e-3) / 1e9,
-                       "frac_of_hbm": pre_bytes / (pre_ms * 1e-3) / 1e9 / peak[0]},
+                       "frac_of_hbm": pre_bytes / (pre_ms * 1e-3) / 1e9 / peak[0],
+                       "alu_roofline": precompute_alu(
+                           name, pre_ms, clk, torch.cuda.get_device_properties(dev).multi_processor_count)},
         "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": peak[0], "unit": "GB/s",
                      "frac": achieved / peak[0] if achieved else None,

@@ -28,3 +28,17 @@ def test_ncu_traffic_scales_the_record_and_drops_stale_ones(monkeypatch):
     assert bench.ncu_traffic("cur", 2000, 3.0) == 6100.0
     assert bench.ncu_traffic("old", 2000, 3.0) is None
     assert bench.ncu_traffic("none", 2000, 3.0) is None
+
+
+def test_precompute_alu_roofline_uses_the_record_of_the_current_code(monkeypatch):
+    import os
+    csrc = os.path.join(bench.ROOT, "paper_2407_21552_gb300", "csrc")
+    sha = bench.code_sha(*bench.precompute_kernel_sources(csrc))
+    monkeypatch.setattr(bench, "NCU_PRECOMPUTE_INST", {
+        "cur": {"source_sha": sha, "warp_instructions": 1.0e9},
+        "old": {"source_sha": "0" * 16, "warp_instructions": 1.0e9}})
+    r = bench.precompute_alu("cur", 2.0, {"sm_mhz": 2000.0}, 100)
+    # 1e9 warp instructions in 2 ms against 4 x 100 SMs x 2 GHz = 8e11 per second
+    assert r["achieved"] == 5.0e11 and r["peak"] == 8.0e11 and abs(r["frac"] - 0.625) < 1e-12
+    assert bench.precompute_alu("old", 2.0, {"sm_mhz": 2000.0}, 100) is None
+    assert bench.precompute_alu("none", 2.0, {"sm_mhz": 2000.0}, 100) is None
