@@ -197,3 +197,36 @@ def test_batched_precompute_longer_than_one_launch_group():
     _check_batch_updates(second[:64], refs[:64], 500)
     for eng in engs:
         eng.close()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_batched_precompute_random_configurations(seed):
+    """One batch of 16 random configurations (sides 1-70, b in 1..8 with any apron up to b,
+    K 1-100, N from 2 to 4096, uniform or skewed borders, uint8 or uint16, with or without
+    min/max, with or without the range index) against the oracle."""
+    from paper_2407_21552_gb300.maps import build_partitions_batch
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(16):
+        kind = "u8" if rng.random() < 0.5 else "u16"
+        dims = tuple(int(v) for v in rng.integers(1, 71, size=3))
+        b = int(rng.choice([1, 2, 3, 4, 4, 4, 8]))
+        a = int(rng.integers(0, b + 1)) if b > 1 else int(rng.integers(0, 2))
+        a = min(a, b)
+        N = int(rng.choice([2, 200, 256, 1000, 4096] if kind == "u16" else [2, 100, 256]))
+        K = int(rng.integers(1, min(N, 100) + 1))
+        bk = "skew" if (K >= 3 and rng.random() < 0.4) else None
+        opt = {"with_minmax": bool(rng.random() < 0.7), "index": bool(rng.random() < 0.2),
+               "offset": int(rng.integers(0, 3))}
+        specs.append((f"random {seed}.{i}", kind, dims, b, a, K, N, bk, opt))
+    items = _make(specs, 40000 + 100 * seed)
+    build_partitions_batch([e for _, _, _, e in items], [v for _, _, v, _ in items])
+    torch.cuda.synchronize()
+    refs = []
+    for spec, vol_np, vd, eng in items:
+        ref = _oracle(spec, vol_np)
+        _check_maps(eng, vol_np, spec, ref)
+        refs.append(ref)
+    _check_batch_updates(items, refs, 700 + seed)
+    for _, _, _, eng in items:
+        eng.close()
