@@ -134,8 +134,8 @@ dm_status dm_build_partitions(dm_ctx *ctx, const void *d_volume, void *stream);
  * precompute (partition tables, POM masks, x pass, y pass, z pass) runs as one launch per
  * kernel variant over the CTAs of all the volumes, DM_BUILD_BATCH_MAX_ITEMS volumes at a
  * time.  POM builds go to the 16-byte vector kernel where it takes the volume (b = 4,
- * apron 1, rows of whole 16-byte vectors, a 16-byte aligned volume, K <= 32 for uint8 and
- * K <= 64 for uint16), else to the general kernel (K <= 64); a volume with K > 64 gets its
+ * apron 1, K <= 32 for uint8 and K <= 64 for uint16; rows of any length, a volume aligned
+ * to its voxel size), else to the general kernel (K <= 64); a volume with K > 64 gets its
  * own POM launch within the batch.  The range-index levels (DM_INDEX_RANGES) are built
  * per volume after the z pass.  Asynchronous on `stream`.  The call first clears the
  * message of every listed context.  Errors, all found on the host before anything is

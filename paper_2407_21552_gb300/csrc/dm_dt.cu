@@ -14,8 +14,10 @@
 // bit left of it and right of it are precomputed.  The K-map pass gives each thread 16
 // consecutive blocks of one bit line: their left and right neighbours' nearest bits come
 // from the rest of the word or those tables, two 16-step scans give the 16 distances, and
-// one 16-byte store writes them.  The one-map pass (full recompute) takes one masked
-// clz/ffs plus the two lookups per output, four outputs per 32-bit store.
+// one 16-byte store writes them.  Short rows share a CTA; rows of at most 96 blocks (with
+// at most 64 maps) take one warp each instead, their bit lines built by ballots in
+// registers.  The one-map pass (full recompute) takes one masked clz/ffs plus the two
+// lookups per output, four outputs per 32-bit store.
 //
 // y / z passes: one thread per line, a CTA per tile of kLineTile neighbouring lines (along
 // x) staged whole in shared memory.  The transform splits into the sweeps

@@ -10,9 +10,13 @@
 //
 // Tiling: one warp per block row and one lane per block column (32 x 8 blocks per CTA),
 // the CTA streaming a chunk of 4 block-slices along z.  The general kernel reads a voxel
-// once per footprint row it lies in; the b = 4 / apron-1 kernel classifies each voxel row
-// about once and trades apron rows between warps in shared memory.  The x apron reaches
-// the neighbouring block through a warp shuffle.
+// once per footprint row it lies in; the b = 4 / apron-1 kernels classify each voxel row
+// about once and trade apron rows between warps in shared memory.  The x apron reaches
+// the neighbouring block through a warp shuffle.  The vector kernel (k_pom_vec) gives a
+// lane 16 bytes of a row (2 or 4 blocks); rows that are not whole 16-byte vectors, or a
+// volume off a 16-byte boundary, take its ragged-row form.  The batched forms
+// (k_pom_vec_batch, k_footprint_batch, k_partition_lut_batch) run the same per-CTA work
+// over the concatenated grids of several volumes.
 #include <algorithm>
 
 #include "dm_build_batch.cuh"

@@ -100,6 +100,7 @@ MIXED = [
     ("u8 b=1 apron 0", "u8", (24, 20, 16), 1, 0, 8, 256, None, {}),
     ("u16 K=100, own POM launch", "u16", (48, 40, 36), 4, 1, 100, 4096, None, {}),
     ("u8 K=200, own POM launch", "u8", (48, 32, 32), 4, 1, 200, 256, None, {}),
+    ("u16 K=150, three mask words", "u16", (40, 36, 28), 4, 1, 150, 4096, "skew", {}),
     ("u8 z lines of 275 blocks", "u8", (16, 16, 1100), 4, 1, 16, 256, None, {}),
     ("u16 one block along y", "u16", (64, 3, 64), 4, 1, 32, 4096, None, {}),
     ("u8 without min/max", "u8", (48, 48, 48), 4, 1, 16, 256, None,
@@ -228,5 +229,28 @@ def test_batched_precompute_random_configurations(seed):
         _check_maps(eng, vol_np, spec, ref)
         refs.append(ref)
     _check_batch_updates(items, refs, 700 + seed)
+    for _, _, _, eng in items:
+        eng.close()
+
+
+def test_batched_precompute_splits_the_partition_tables_by_border_count():
+    """48 volumes of K = 100 carry 48 x 101 borders, more than one launch of the partition
+    tables holds: the tables are built in two launches, every one still exact."""
+    from paper_2407_21552_gb300.maps import build_partitions_batch
+    specs = []
+    for i in range(48):
+        kind = "u16" if i % 3 else "u8"
+        N = 4096 if kind == "u16" else 256
+        dims = (8 + i % 5, 9 + i % 7, 7 + i % 4)
+        specs.append((f"K=100 item {i}", kind, dims, 4, 1, 100, N, "skew" if i % 2 else None, {}))
+    items = _make(specs, 60000)
+    build_partitions_batch([e for _, _, _, e in items], [v for _, _, v, _ in items])
+    torch.cuda.synchronize()
+    refs = []
+    for spec, vol_np, vd, eng in items:
+        ref = _oracle(spec, vol_np)
+        _check_maps(eng, vol_np, spec, ref)
+        refs.append(ref)
+    _check_batch_updates(items, refs, 900)
     for _, _, _, eng in items:
         eng.close()
