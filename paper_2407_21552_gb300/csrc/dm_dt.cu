@@ -527,9 +527,10 @@ __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __rest
 
 // One tile = TC adjacent columns x one whole line of every column; thread c takes column c.
 // The tile is staged before any output is written, so the pass works in place.  P, the
-// type of the table's positions: uint8_t for lines of at most 256 blocks (each sweep then
-// numbers its rows 0..L-1 from a cleared table), else uint16_t (the backward sweep's
-// positions follow the forward sweep's, so one clearing serves both).
+// type of the table's positions: uint8_t for lines of at most 256 blocks, else uint16_t.
+// The backward sweep's positions follow the forward sweep's (L .. 2L-1), so one clearing
+// serves both, except for 8-bit positions on lines of more than 128 blocks: there each
+// sweep numbers its rows 0..L-1 and the table is cleared between them.
 template <int TC, typename P, bool VEC>
 __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg, int cx,
                                                 int cy, int cz)
@@ -598,10 +599,10 @@ __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg
     uint8_t* tile = s_tile + tid;
     P* tab = s_tab + tid;
     sweep_line<TC, false>(tile, tab, L, 0, nullptr, 0);
-    if (kShort) {                           // clear this column's table again
+    if (kShort && 2 * L > 256) {            // clear this column's table again
         for (int v = 0; v < 256; ++v) tab[v * TC] = P(0);
         sweep_line<TC, true>(tile, tab, L, 0, base + tid, lg.s);
-    } else {
+    } else {                                // both sweeps' positions fit: no clearing
         sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
     }
 }
