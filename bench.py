@@ -68,12 +68,12 @@ NCU_TRAFFIC = {
 # keyed by workload, with the hash of the kernel code it was taken on; the precompute's ALU
 # roofline is reported as null once that code has changed.
 NCU_PRECOMPUTE_INST = {
-    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 339,585,744 +
-    # 695,549,952
-    "mid": {"source_sha": "5fc059e251d96c33", "warp_instructions": 1739165251.0},
+    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 341,718,056 +
+    # 684,269,568
+    "mid": {"source_sha": "0aa7ad3784d871da", "warp_instructions": 1730017179.0},
     # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,014,630,284 +
-    # 1,361,257,104 (y, 256-block lines) + 2,685,460,480 (z, 449-block lines)
-    "large": {"source_sha": "5fc059e251d96c33", "warp_instructions": 6875451524.0},
+    # 1,369,804,552 (y, 256-block lines) + 2,685,460,480 (z, 449-block lines)
+    "large": {"source_sha": "0aa7ad3784d871da", "warp_instructions": 6883998972.0},
 }
 
 
