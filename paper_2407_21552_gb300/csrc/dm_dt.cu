@@ -482,47 +482,65 @@ __host__ __device__ inline size_t sweep_tile_bytes(int L, int TC)
 // One sweep over a line of the tile, rows in the order FINAL gives (forward from row 0, or
 // backward from row L-1).  Positions enter the table as `off` + the step count, so that a
 // sweep never mistakes an entry of an earlier sweep (all below its own `off`) for one of
-// its own.  FINAL: the values go to global memory (column `col` of the tile's rows);
-// otherwise back into the tile.  The values of kRun rows are read before any of them is
-// processed, and the table entry a rise to the next level would need is read one step
-// ahead (then corrected for the value the step itself enters), so that no shared-memory
-// read waits inside a step; every step is the same branch-free sequence.
+// its own.  TO_TILE: the values go back into the tile; otherwise to global memory (column
+// `col` of the tile's rows).
+//
+// A step enters its own row in the table first and then reads the entry of the next level
+// up, so that the read already sees the step's own value.  That read only feeds T, and T
+// only decides the rise of the next step, so its latency spans two steps.  The level can
+// rise by one a step at most (d = pos - T never exceeds lv + 1), so the new level is
+// min(g, max(lv, d)): two min/max operations, with no select on a compare, on the chain
+// from one step's level to the next.  The values of kRun rows are read before any of them
+// is processed; whole runs of kRun rows carry no bound checks, the last partial run does.
 constexpr int kRun = 8;
 
-template <int TC, bool FINAL, typename P>
+struct SweepState {
+    int lv;                      // level of the previous row (255 before the first)
+    int T;                       // last position holding a value <= lv
+};
+
+template <int TC, bool FINAL, bool TO_TILE, bool TAIL, typename P>
+__device__ __forceinline__ void sweep_run(uint8_t* __restrict__ tile, P* __restrict__ tab,
+                                          int L, int k0, int off, SweepState& st,
+                                          uint8_t* __restrict__ col, int64_t gstride)
+{
+    const int r0 = FINAL ? L - 1 : 0;
+    const int dir = FINAL ? -1 : 1;
+    int gv[kRun];
+#pragma unroll
+    for (int i = 0; i < kRun; ++i)
+        gv[i] = (!TAIL || k0 + i < L) ? tile[(r0 + dir * (k0 + i)) * TC] : 0;
+    int lv = st.lv, T = st.T;
+#pragma unroll
+    for (int i = 0; i < kRun; ++i) {
+        const int k = k0 + i;
+        if (TAIL && k >= L) break;
+        const int r = r0 + dir * k;
+        const int g = gv[i];
+        const int pos = off + k;
+        tab[g * TC] = P(pos);
+        const int x = tab[(lv + 1) * TC];                 // last position of level lv + 1
+        const int d = pos - T;                             // at most lv + 1
+        const bool drop = g <= lv;
+        T = drop ? pos : (d > lv ? max(T, x) : T);         // d > lv: level lv ran out here
+        lv = min(g, max(lv, d));                           // g, lv + 1 or lv
+        if (TO_TILE) tile[r * TC] = uint8_t(lv);
+        else col[int64_t(r) * gstride] = uint8_t(lv);
+    }
+    st.lv = lv;
+    st.T = T;
+}
+
+template <int TC, bool FINAL, bool TO_TILE, typename P>
 __device__ __forceinline__ void sweep_line(uint8_t* __restrict__ tile, P* __restrict__ tab,
                                            int L, int off, uint8_t* __restrict__ col,
                                            int64_t gstride)
 {
-    const int r0 = FINAL ? L - 1 : 0;
-    const int dir = FINAL ? -1 : 1;
-    int lv = 255;                // level of the previous row (255 before the first)
-    int T = off;                 // last position holding a value <= lv
-    int x = off;                 // the table entry of level lv + 1, read one step ahead
-    for (int k0 = 0; k0 < L; k0 += kRun) {
-        int gv[kRun];
-#pragma unroll
-        for (int i = 0; i < kRun; ++i)
-            gv[i] = k0 + i < L ? tile[(r0 + dir * (k0 + i)) * TC] : 0;
-#pragma unroll
-        for (int i = 0; i < kRun; ++i) {
-            const int k = k0 + i;
-            if (k >= L) break;
-            const int r = r0 + dir * k;
-            const int g = gv[i];
-            const int pos = off + k;
-            tab[g * TC] = P(pos);
-            const int w = lv + 1;
-            const int xw = g == w ? pos : x;                 // this step's own entry
-            const bool drop = g <= lv;
-            const bool rise = !drop && pos - T > lv;
-            T = drop ? pos : (rise ? max(T, xw) : T);
-            lv = drop ? g : (rise ? w : lv);
-            x = tab[(lv + 1) * TC];                          // for the next step
-            if (FINAL) col[int64_t(r) * gstride] = uint8_t(lv);
-            else tile[r * TC] = uint8_t(lv);
-        }
-    }
+    SweepState st{255, off};
+    int k0 = 0;
+    for (; k0 + kRun <= L; k0 += kRun)
+        sweep_run<TC, FINAL, TO_TILE, false>(tile, tab, L, k0, off, st, col, gstride);
+    if (k0 < L) sweep_run<TC, FINAL, TO_TILE, true>(tile, tab, L, k0, off, st, col, gstride);
 }
 
 // One tile = TC adjacent columns x one whole line of every column; thread c takes column c.
@@ -595,15 +613,22 @@ __device__ __forceinline__ void line_sweep_tile(uint8_t* buf, const LineGeom& lg
     any_big = __syncthreads_or(any_big);
     any_not255 = __syncthreads_or(any_not255);
     if (!any_big || !any_not255) return;   // all values <= 1, or all 255: h == g
-    if (tid >= ncols) return;               // no barrier follows
+    if (!VEC && tid >= ncols) return;       // (whole-row tiles have every column)
     uint8_t* tile = s_tile + tid;
     P* tab = s_tab + tid;
-    sweep_line<TC, false>(tile, tab, L, 0, nullptr, 0);
-    if (kShort && 2 * L > 256) {            // clear this column's table again
+    sweep_line<TC, false, true>(tile, tab, L, 0, nullptr, 0);
+    // whole-row tiles keep the result in the tile and write it out as 16-byte rows
+    const int off2 = kShort && 2 * L > 256 ? 0 : L;
+    if (off2 == 0)                          // clear this column's table again
         for (int v = 0; v < 256; ++v) tab[v * TC] = P(0);
-        sweep_line<TC, true>(tile, tab, L, 0, base + tid, lg.s);
-    } else {                                // both sweeps' positions fit: no clearing
-        sweep_line<TC, true>(tile, tab, L, L, base + tid, lg.s);
+    sweep_line<TC, true, VEC>(tile, tab, L, off2, base + tid, lg.s);
+    if (VEC) {
+        __syncthreads();
+        for (int i = tid; i < L * V; i += TC) {
+            const int r = i / V, q = i - r * V;
+            *reinterpret_cast<uint4*>(base + int64_t(r) * lg.s + 16 * q) =
+                reinterpret_cast<const uint4*>(s_tile)[i];
+        }
     }
 }
 

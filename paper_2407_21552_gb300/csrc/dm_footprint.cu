@@ -944,7 +944,7 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
     // copies of slice z's rows (and edge vectors) into buffer `bsel`, asynchronous, one group
     auto fetch = [&](int z, int bsel) {
         const T* slice = vol + int64_t(z) * Y * rowX;
-        if (RAG) {
+        if constexpr (RAG) {
 #pragma unroll
             for (int t = 0; t < 5; ++t) {
                 if (!row_ok(t)) continue;                      // warp-uniform
@@ -957,26 +957,25 @@ pom_vec_cta(const T* __restrict__ vol, const FpParams& p, const uint8_t* __restr
                 if (lane == 0 && cx > 0) cp_async16(dst, a - 16);
                 if (lane == 31 && (xv0 + VL) * S - ra < X * S) cp_async16(dst + 33, a + 16);
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int t = 0; t < 5; ++t) {
-            const bool ok = row_ok(t);
-            const T* row = slice + int64_t(ok ? row_y(t) : 0) * rowX;
-            if (ok && lane_ok) {
-                const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
-                    s_rows + ((bsel * kWarps + warp) * 5 + t) * 32 + lane));
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
-                             "l"(row + xv0)
-                             : "memory");
-            }
-            if (ok && edge_ok) {
-                const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
-                    s_edge + ((bsel * kWarps + warp) * 5 + t) * 2 + eslot));
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
-                             "l"(row + xev)
-                             : "memory");
+            for (int t = 0; t < 5; ++t) {
+                const bool ok = row_ok(t);
+                const T* row = slice + int64_t(ok ? row_y(t) : 0) * rowX;
+                if (ok && lane_ok) {
+                    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
+                        s_rows + ((bsel * kWarps + warp) * 5 + t) * 32 + lane));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                                 "l"(row + xv0)
+                                 : "memory");
+                }
+                if (ok && edge_ok) {
+                    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(
+                        s_edge + ((bsel * kWarps + warp) * 5 + t) * 2 + eslot));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa),
+                                 "l"(row + xev)
+                                 : "memory");
+                }
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
