@@ -111,10 +111,11 @@ dm_status dm_query_sizes(const dm_ctx *ctx, dm_sizes *out);
  * the full recompute is never used in DM_OCC_MINMAX mode), d_scratch (scratch_bytes,
  * 256-byte aligned).  d_mask is only written and read by dm_build_partitions (the POMs are
  * an intermediate, §5) and may be released afterwards by binding NULL.  Rebinding is
- * allowed between calls.  The scratch buffer holds a per-context table (the partition of
- * every intensity) that dm_build_partitions and dm_mark_built write: binding another pdm
- * or scratch buffer marks the context unbuilt, and the updates return DM_ERR_NOT_BOUND
- * until one of those two calls has run on the new buffers.
+ * allowed between calls.  The scratch buffer holds two per-context tables that
+ * dm_build_partitions and dm_mark_built write: the partition of every intensity, and the
+ * order in which the updates read the planes (below).  Binding another pdm or scratch
+ * buffer marks the context unbuilt, and the updates return DM_ERR_NOT_BOUND until one of
+ * those two calls has run on the new buffers.
  */
 dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *d_scratch);
 
@@ -123,7 +124,8 @@ dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *
  * (dims / dtype of the config) build the partition table, the K POMs as per-block bit
  * masks over each block's footprint (b^3 voxels plus the apron), the block min/max (if
  * d_minmax is bound), and the K PDMs as Chebyshev distance transforms of the POMs,
- * clamped to uint8 (§3.2).  Asynchronous on `stream`.
+ * clamped to uint8 (§3.2).  Last, the plane order: the K planes ranked by their count of
+ * zero bytes (occupied blocks) on a fixed sample, most first.  Asynchronous on `stream`.
  */
 dm_status dm_build_partitions(dm_ctx *ctx, const void *d_volume, void *stream);
 
@@ -157,6 +159,9 @@ dm_status dm_build_partitions_batch(dm_ctx *const *ctxs, const void *const *d_vo
  * d_out: device uint8 [G], D' = min over active p of PDM_p, 255 where no partition is
  * active.  d_active_mask_out: optional device uint64 [ceil(K/64)] receiving S as a bit
  * set.  Reads the PDMs built by dm_build_partitions.  Asynchronous; no host round trip.
+ * Without the range index the active planes are read in the context's plane order, and a
+ * 16-byte chunk of D' whose minimum is already 0 in every byte reads no further plane, so
+ * the traffic is at most (|S| + 1) * G bytes (D' is the same in any order).
  */
 dm_status dm_update_tf(dm_ctx *ctx, const float *d_tf_rgba, uint8_t *d_out,
                        uint64_t *d_active_mask_out, void *stream);
@@ -190,7 +195,8 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
  * context, and later copies them back into the bound buffers of a context with the same
  * hash, declares them built with dm_mark_built(ctx, hash); the call fails with
  * DM_ERR_INVALID_ARG when the hash differs, and with DM_ERR_NOT_BOUND when pdm / scratch
- * are not bound.  The partition table in scratch is rebuilt on `stream`.  The paper
+ * are not bound.  The partition table and the plane order in scratch are rebuilt on
+ * `stream` (the order from the planes as they are at that point of the stream).  The paper
  * recomputes the maps at every load (§3.1, one-time initialisation).
  */
 dm_status dm_config_hash(const dm_ctx *ctx, uint64_t *out);
@@ -234,8 +240,9 @@ dm_status dm_update_tf_batch(const dm_batch_item *items, int32_t n,
  * are those of dm_update_tf on each item alone).  The items of one context, in their
  * order, form groups of up to DM_BATCH_MAX_EDITS_PER_GROUP; the combine reads every PDM
  * plane that one of a group's TFs needs once and folds it into each of those TFs' maps,
- * so a group's HBM traffic is (|S_1 u ... u S_E| + E) * G bytes instead of
- * sum_e (|S_e| + 1) * G.  The active sets live in d_workspace, a caller-allocated device
+ * so a group's HBM traffic is at most (|S_1 u ... u S_E| + E) * G bytes instead of
+ * sum_e (|S_e| + 1) * G (planes in the plane order; a chunk at 0 in every byte of every
+ * TF of the group reads no further plane).  The active sets live in d_workspace, a caller-allocated device
  * buffer of at least dm_batch_workspace_bytes(n) bytes, 256-byte aligned, which must not
  * be used by other work while the call's kernels run (no context's scratch is written, so
  * calls on other streams may share contexts but not a workspace).  Up to

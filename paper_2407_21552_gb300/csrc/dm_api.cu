@@ -25,7 +25,7 @@ struct dm_ctx {
     int planes;                     // planes in the pdm buffer
     int num_sms;
     // scratch layout (byte offsets)
-    size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_tf, off_out;
+    size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_cover, off_order, off_tf, off_out;
     void* d_mask;
     void* d_pdm;
     void* d_minmax;
@@ -163,6 +163,8 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     x->off_act = o;   o = align_up(o + size_t(dmk::kMaxPartitions + 8) * 2, 256);
     x->off_nact = o;  o = align_up(o + 64, 64);
     x->off_smask = o; o = align_up(o + 64, 256);
+    x->off_cover = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 4, 256);
+    x->off_order = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 2, 256);
     x->off_tf = o;    o = align_up(o + size_t(N) * 16, 256);
     x->off_out = o;   o = align_up(o + size_t(g.G), 256);
     s.scratch_bytes = o;
@@ -205,6 +207,27 @@ dm_status dm_bind(dm_ctx* ctx, void* d_mask, void* d_pdm, void* d_minmax, void* 
     return DM_OK;
 }
 
+// The plane order of a context (in its scratch, next to the partition table): written by
+// dm_build_partitions, dm_build_partitions_batch and dm_mark_built, read by the updates.
+static dmk::PlaneOrderItem plane_order_item(const dm_ctx* c)
+{
+    uint8_t* scratch = static_cast<uint8_t*>(c->d_scratch);
+    dmk::PlaneOrderItem it;
+    it.pdm = static_cast<const uint8_t*>(c->d_pdm);
+    it.plane = c->geo.plane;
+    it.G = c->geo.G;
+    it.K = c->cfg.num_partitions;
+    it.cover = reinterpret_cast<uint32_t*>(scratch + c->off_cover);
+    it.order = reinterpret_cast<uint16_t*>(scratch + c->off_order);
+    return it;
+}
+
+static const uint16_t* plane_order(const dm_ctx* c)
+{
+    return reinterpret_cast<const uint16_t*>(static_cast<const uint8_t*>(c->d_scratch) +
+                                             c->off_order);
+}
+
 // Uniform partitions of a power-of-two width: the partition of intensity i is i >> shift.
 // Else -1.
 static int pom_shift(const dm_ctx* c)
@@ -242,6 +265,9 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM y pass");
     e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 2, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM z pass");
+    const dmk::PlaneOrderItem po = plane_order_item(ctx);
+    e = dmk::launch_plane_order(&po, 1, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plane order");
     if (ctx->J > 0) {
         e = dmk::launch_build_index(pdm, ctx->geo.plane, ctx->geo.G, K, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "range index");
@@ -337,6 +363,10 @@ dm_status dm_build_partitions_batch(dm_ctx* const* ctxs, const void* const* d_vo
         if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: y pass");
         e = dmk::launch_line_pass_batch(items, m, 2, s);
         if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: z pass");
+        dmk::PlaneOrderItem po[dmk::kMaxBuildBatch];
+        for (int k = 0; k < m; ++k) po[k] = plane_order_item(ctxs[i0 + k]);
+        e = dmk::launch_plane_order(po, m, s);
+        if (e != cudaSuccess) return cuda_fail(first, e, "batched precompute: plane order");
         for (int k = 0; k < m; ++k) {
             dm_ctx* c = ctxs[i0 + k];
             if (c->J > 0) {
@@ -383,7 +413,7 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         cudaError_t e = dmk::launch_update_fused(static_cast<const uint8_t*>(ctx->d_pdm),
                                                  ctx->geo.plane, ctx->geo.G, d_tf, N, K,
                                                  ctx->J, ctx->borders, ctx->uniform_borders ? 1 : 0,
-                                                 act, nact, smask,
+                                                 plane_order(ctx), act, nact, smask,
                                                  d_active_mask_out, d_out, ctx->num_sms, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "update");
         if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
@@ -391,8 +421,8 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         ctx->err[0] = 0;
         return DM_OK;
     }
-    cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->J, ctx->borders, act, nact, smask,
-                                           d_active_mask_out, s);
+    cudaError_t e = dmk::launch_active_set(d_tf, N, K, ctx->J, ctx->borders, plane_order(ctx),
+                                           act, nact, smask, d_active_mask_out, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "active set");
     if (ctx->ev_begin && (e = cudaEventRecord(ctx->ev_begin, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "profile event");
@@ -540,6 +570,9 @@ dm_status dm_mark_built(dm_ctx* ctx, uint64_t hash, int32_t with_minmax, void* s
     cudaError_t e = dmk::launch_partition_lut(lut, ctx->cfg.tf_size, ctx->cfg.num_partitions,
                                               ctx->borders, as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "partition table");
+    const dmk::PlaneOrderItem po = plane_order_item(ctx);
+    e = dmk::launch_plane_order(&po, 1, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plane order");
     ctx->built = true;
     ctx->minmax_built = with_minmax != 0;
     ctx->err[0] = 0;
@@ -580,6 +613,7 @@ static void group_of(dm_ctx* c, dmk::BatchGroup& d)
     d.plane = c->geo.plane;
     d.G = c->geo.G;
     d.lut = scratch + c->off_lut;
+    d.order = plane_order(c);
     d.N = c->cfg.tf_size;
     d.K = c->cfg.num_partitions;
     d.J = c->J;

@@ -28,6 +28,7 @@ struct Group {
     int64_t plane;
     int64_t G;
     const uint8_t* lut;                        // partition of each intensity (precompute)
+    const uint16_t* order;                     // plane order (precompute; null: ascending)
     uint16_t* list;                            // plane list, padded (workspace or scratch)
     uint8_t* emask;                            // per list entry: the TFs taking the plane
     int32_t* count;
@@ -57,9 +58,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
 // few mask words: it ORs each word over the warp and one lane sets it, with no
 // same-address shared atomics between the lanes.  Each TF's planes (the active partitions,
 // or index planes covering their runs) are marked in a per-plane TF set; the planes any TF
-// takes are then listed in ascending order with their TF sets, followed by kPad copies of
-// the first entry, so that the combine can read the list in groups of up to kPad without
-// knowing its length first (a repeated plane changes no minimum).
+// takes are then listed with their TF sets (in the volume's plane order without the index,
+// else ascending), followed by kPad copies of the first entry, so that the combine can read
+// the list in groups of up to kPad without knowing its length first (a repeated plane
+// changes no minimum).
 template <int EMAX>
 __global__ void __launch_bounds__(kActThreads) k_active_group(const __grid_constant__ Params P)
 {
@@ -67,9 +69,13 @@ __global__ void __launch_bounds__(kActThreads) k_active_group(const __grid_const
     __shared__ uint32_t s_S[kMaxPartitions / 32];
     __shared__ uint16_t s_list[kMaxPartitions + 8];
     __shared__ uint8_t s_em[EMAX > 1 ? kMaxPlanes : 1];
+    __shared__ uint16_t s_ord[EMAX > 1 ? kMaxPartitions : 1];
     __shared__ int s_scan[33];
     const Group& g = P.g[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mine = g.order && tid < g.K ? int(g.order[tid]) : tid;   // this thread's plane
+    const bool ordered = EMAX > 1 && g.J < 0 && g.order != nullptr;
+    if (ordered && tid < g.K) s_ord[tid] = uint16_t(mine);
     const int planes = EMAX > 1 ? (g.J < 0 ? g.K : index_level_base(g.K, g.J + 1)) : 0;
     if (EMAX > 1)
         for (int j = tid; j < planes; j += kActThreads) s_em[j] = 0;
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kActThreads) k_active_group(const __grid_const
             }
         }
         __syncthreads();
-        n = plan_maps(s_S, g.K, g.J, s_list, s_scan);        // ends with a CTA barrier
+        n = plan_maps(s_S, g.K, g.J, s_list, s_scan, mine);  // ends with a CTA barrier
         if (EMAX > 1)
             for (int j = tid; j < n; j += kActThreads) s_em[s_list[j]] |= uint8_t(1u << e);
     }
@@ -113,10 +119,13 @@ __global__ void __launch_bounds__(kActThreads) k_active_group(const __grid_const
         return;
     }
     __syncthreads();
-    // list the planes some TF takes, ascending: each thread scans two consecutive planes
+    // list the planes some TF takes: each thread scans two consecutive list positions, the
+    // planes at those positions of the plane order (or those positions themselves)
     const int p0 = 2 * tid;
-    const int c0 = p0 < planes && s_em[p0] ? 1 : 0;
-    const int c1 = p0 + 1 < planes && s_em[p0 + 1] ? 1 : 0;
+    const int q0 = p0 < planes ? (ordered ? int(s_ord[p0]) : p0) : 0;
+    const int q1 = p0 + 1 < planes ? (ordered ? int(s_ord[p0 + 1]) : p0 + 1) : 0;
+    const int c0 = p0 < planes && s_em[q0] ? 1 : 0;
+    const int c1 = p0 + 1 < planes && s_em[q1] ? 1 : 0;
     int incl = c0 + c1;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -137,13 +146,13 @@ __global__ void __launch_bounds__(kActThreads) k_active_group(const __grid_const
     __syncthreads();
     int pos = s_scan[warp] + incl - c0 - c1;
     if (c0) {
-        g.list[pos] = uint16_t(p0);
-        g.emask[pos] = s_em[p0];
+        g.list[pos] = uint16_t(q0);
+        g.emask[pos] = s_em[q0];
         ++pos;
     }
     if (c1) {
-        g.list[pos] = uint16_t(p0 + 1);
-        g.emask[pos] = s_em[p0 + 1];
+        g.list[pos] = uint16_t(q1);
+        g.emask[pos] = s_em[q1];
     }
     const int u = s_scan[32];
     __syncthreads();                                          // the first entry is written
@@ -168,6 +177,15 @@ struct GroupMin {
 #pragma unroll
         for (int e = 0; e < EMAX; ++e)
             if (EMAX == 1 || ((em >> e) & 1u)) acc[e].fold(v);
+    }
+    // some TF of the group (e < E) still has a byte above 0: later planes may lower it
+    __device__ __forceinline__ bool live(int E) const
+    {
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e < EMAX; ++e)
+            if (EMAX == 1 || e < E) any = any || acc[e].nonzero();
+        return any;
     }
 };
 
@@ -268,7 +286,9 @@ k_combine_group(const __grid_constant__ Params P)
                     asm volatile("cp.async.commit_group;" ::: "memory");
                 }
                 for (int b = 0; b < nb; ++b) {
-                    if (b + 1 < nb)
+                    // a chunk at 0 in every byte of every TF is final: its later planes are
+                    // not loaded, and their stale slots fold into minima of 0
+                    if (b + 1 < nb && acc.live(g.E))
                         for (int k = 0; k < KB; ++k)
                             cp_async16(&s_stage[(b + 1) & 1][k][tid], src + s_off[(b + 1) * KB + k]);
                     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -341,6 +361,7 @@ cudaError_t launch_update_batch(const BatchGroup* groups, int n, const BatchTuni
         g.plane = d.plane;
         g.G = d.G;
         g.lut = d.lut;
+        g.order = d.order;
         g.list = d.list;
         g.emask = d.emask;
         g.count = d.count;

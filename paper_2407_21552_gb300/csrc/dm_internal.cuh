@@ -114,6 +114,11 @@ struct ByteMin16 {                                   // running byte minimum of 
     {
         return make_uint4(e[0] | o[0], e[1] | o[1], e[2] | o[2], e[3] | o[3]);
     }
+    // some byte above 0: a minimum that reached 0 everywhere no plane can lower
+    __device__ __forceinline__ bool nonzero() const
+    {
+        return ((e[0] | e[1] | e[2] | e[3]) | (o[0] | o[1] | o[2] | o[3])) != 0u;
+    }
 };
 
 // ---------------------------------------------------------------- partition-range index
@@ -136,21 +141,25 @@ __host__ __device__ inline int index_levels(int K)
 
 // From the active-partition bit set `bits` (shared memory, 8 words, bit p = partition p),
 // write the plane indices to combine to `list` and return their number (to every thread).
-// Without the index (J < 0) the planes are the active partitions; with it, one or two
-// planes per maximal run of active partitions.  Every thread of the CTA must call it (it
-// synchronises the CTA); threads 0..255 handle partition threadIdx.x; `s_scan` is 9 ints
-// of shared scratch.
-__device__ inline int plan_maps(const uint32_t* bits, int K, int J, uint16_t* list, int* s_scan)
+// Without the index (J < 0) the planes are the active partitions, listed in the order in
+// which thread t < K passes them as `mine` (a permutation of 0..K-1: the context's plane
+// order, or t itself); with it, one or two planes per maximal run of active partitions,
+// threads 0..255 handling partition threadIdx.x.  Every thread of the CTA must call it (it
+// synchronises the CTA); `s_scan` is 9 ints of shared scratch.
+__device__ inline int plan_maps(const uint32_t* bits, int K, int J, uint16_t* list, int* s_scan,
+                                int mine)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto on = [&](int p) { return (bits[p >> 5] >> (p & 31)) & 1u; };
     int c = 0;
     int m0 = 0, m1 = 0;
-    if (tid < K && on(tid)) {
-        if (J < 0) {
+    if (J < 0) {                                          // the planes, in the given order
+        if (tid < K && on(mine)) {
             c = 1;
-            m0 = tid;
-        } else if (tid == 0 || !on(tid - 1)) {           // run start: find the run's end
+            m0 = mine;
+        }
+    } else if (tid < K && on(tid)) {
+        if (tid == 0 || !on(tid - 1)) {                   // run start: find the run's end
             int e = tid;
             while (e + 1 < K && on(e + 1)) ++e;
             const int k = 31 - __clz(e - tid + 1);
@@ -228,19 +237,21 @@ cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, i
                              uint16_t* act, int32_t* nact, uint64_t* smask,
                              uint64_t* smask_out, cudaStream_t s);
 
-// The active set alone (no prefix count), for the update path.
+// The active set alone (no prefix count), for the update path; without the index (J < 0)
+// act lists the active planes in the plane order `order` (null: ascending).
 cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Borders& bd,
-                              uint16_t* act, int32_t* nact, uint64_t* smask,
-                              uint64_t* smask_out, cudaStream_t s);
+                              const uint16_t* order, uint16_t* act, int32_t* nact,
+                              uint64_t* smask, uint64_t* smask_out, cudaStream_t s);
 
 // Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
 bool update_fused_ok(int N);
 // `uniform`: the borders are the default floor(p N / K), which the kernel computes instead of
-// indexing the parameter array per thread.
+// indexing the parameter array per thread.  `order` as in launch_active_set.
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, int J, const Borders& bd, int uniform, uint16_t* act,
-                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
-                                uint8_t* out, int num_sms, cudaStream_t s);
+                                int N, int K, int J, const Borders& bd, int uniform,
+                                const uint16_t* order, uint16_t* act, int32_t* nact,
+                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
+                                cudaStream_t s);
 
 // D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
@@ -257,6 +268,7 @@ struct BatchGroup {
     const uint8_t* pdm;
     int64_t plane, G;
     const uint8_t* lut;                // the volume's partition table (its scratch)
+    const uint16_t* order;             // the volume's plane order (its scratch; null: ascending)
     uint16_t* list;
     uint8_t* emask;
     int32_t* count;

@@ -10,8 +10,14 @@
 // kernel: each thread owns 16-byte chunks of the map, reads the same chunk of every active
 // plane (independent 16-byte loads, several in flight) and folds them byte-wise, two bytes
 // per min.u16x2 (ByteMin16).  On large maps the chunks are taken in plane-major tiles: a
-// warp reads 4 KiB of one plane per step and keeps 8 accumulators per thread.  The HBM traffic is (|S| + 1) * G bytes,
-// the algorithmic minimum.  An empty S yields 255.
+// warp reads 4 KiB of one plane per step and keeps 8 accumulators per thread.  An empty S
+// yields 255.
+//
+// A byte minimum of 0 is final, so a chunk stops loading planes once its minimum is 0 in
+// every byte, and the active planes are read in the context's plane order: most-covered
+// (most zero bytes on a sample) first, which brings most chunks to 0 soonest.  The HBM
+// traffic is at most (|S| + 1) * G bytes; D' is the same in any order.
+#include "dm_build_batch.cuh"
 #include "dm_internal.cuh"
 
 namespace dmk {
@@ -97,8 +103,9 @@ k_tf_active(const float* __restrict__ tf, int N, int K, Borders bd, int32_t* __r
 // [lo_p, hi_p] is set; compacted ascending.  Lets the combine's CTAs launch at once.
 __global__ void __launch_bounds__(kActThreads)
 k_active_set(const float* __restrict__ tf, int N, int K, int J, Borders bd,
-             uint16_t* __restrict__ act, int32_t* __restrict__ nact,
-             uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out)
+             const uint16_t* __restrict__ order, uint16_t* __restrict__ act,
+             int32_t* __restrict__ nact, uint64_t* __restrict__ smask,
+             uint64_t* __restrict__ smask_out)
 {
     pdl_trigger();
     constexpr int kBatch = 8;
@@ -107,6 +114,7 @@ k_active_set(const float* __restrict__ tf, int N, int K, int J, Borders bd,
     __shared__ uint16_t s_list[kMaxPartitions + 8];
     __shared__ int s_scan[9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mine = order && tid < K ? int(order[tid]) : tid;     // this thread's plane
     for (int base = 0; base < N; base += kActThreads * kBatch) {
         float a[kBatch];
 #pragma unroll
@@ -138,7 +146,7 @@ k_active_set(const float* __restrict__ tf, int N, int K, int J, Borders bd,
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, on);
     if (lane == 0 && warp < 8) s_bits[warp] = bal;
     __syncthreads();
-    const int n = plan_maps(s_bits, K, J, s_list, s_scan);
+    const int n = plan_maps(s_bits, K, J, s_list, s_scan, mine);
     for (int j = tid; j < n; j += kActThreads) act[j] = s_list[j];
     if (tid == 0) *nact = n;
     if (tid < 4) {
@@ -170,6 +178,9 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // `stage` is this thread's [2][kAsyncBatch] slot array (stride `ld` uint4 between slots);
 // s_off holds the n plane offsets followed by kAsyncBatch copies of the first one, so a
 // last, partial batch reads plane 0 again (same bytes, no effect on the min).
+// A chunk whose minimum has reached 0 in every byte is final: its later batches are not
+// loaded.  Their slots are folded all the same, with whatever bytes they hold, which
+// leaves a minimum of 0 at 0.
 constexpr int kAsyncBatch = 8;
 
 __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__ pdm,
@@ -186,25 +197,28 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
     // flattened sequence of (chunk, batch) steps; step i+1 is issued before step i is used
     int64_t v = t0;
     int jb = 0;
-    auto issue = [&](int64_t vv, int b, int slot) {
+    auto issue = [&](int64_t vv, int b, int slot, bool load) {
         const uint8_t* src = pdm + (vv << 4);
+        if (load) {
 #pragma unroll
-        for (int k = 0; k < kAsyncBatch; ++k)
-            cp_async16(stage + (slot * kAsyncBatch + k) * ld, src + s_off[b * kAsyncBatch + k]);
+            for (int k = 0; k < kAsyncBatch; ++k)
+                cp_async16(stage + (slot * kAsyncBatch + k) * ld,
+                           src + s_off[b * kAsyncBatch + k]);
+        }
         cp_async_commit();
     };
     if (v >= nvec) return;
-    issue(v, 0, 0);
+    issue(v, 0, 0, true);
     int slot = 0;
     ByteMin16 acc;
     acc.reset();
     while (true) {
-        // next step
+        // next step (its chunk's minimum so far covers the batches before jb)
         int64_t nv = v;
         int njb = jb + 1;
         if (njb == nb) { njb = 0; nv = v + stride; }
         const bool more = nv < nvec;
-        if (more) issue(nv, njb, slot ^ 1); else cp_async_commit();
+        if (more) issue(nv, njb, slot ^ 1, njb == 0 || acc.nonzero()); else cp_async_commit();
         cp_async_wait1();                                     // step (v, jb) landed
 #pragma unroll
         for (int k = 0; k < kAsyncBatch; ++k) acc.fold(stage[(slot * kAsyncBatch + k) * ld]);
@@ -224,7 +238,8 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
 // warp owns 256 consecutive chunks (4 KiB), lane l chunks base + 32 k + l for k < 8.
 // One step loads the warp's 4 KiB of one plane (8 cp.async per thread, each instruction
 // 512 contiguous bytes), so every DRAM burst of a step is 4 KiB of one plane; the 8
-// per-thread accumulators fold the planes and are stored once per tile.
+// per-thread accumulators fold the planes and are stored once per tile.  As in the
+// per-chunk path, a chunk whose minimum is 0 in every byte loads no further plane.
 constexpr int kPM = 8;                                        // chunks per thread per tile
 __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__ pdm,
                                                      const int64_t* s_off, int n, int64_t ntiles,
@@ -245,24 +260,26 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
                 __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), make_uint4(~0u, ~0u, ~0u, ~0u));
         return;
     }
-    auto issue = [&](int64_t tt, int p, int slot) {
-        const uint8_t* src = pdm + s_off[p];
-#pragma unroll
-        for (int k = 0; k < kPM; ++k)
-            cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
-        cp_async_commit();
-    };
     ByteMin16 acc[kPM];
 #pragma unroll
     for (int k = 0; k < kPM; ++k) acc[k].reset();
+    // fresh: the first plane of a tile (the accumulators still hold the previous tile)
+    auto issue = [&](int64_t tt, int p, int slot, bool fresh) {
+        const uint8_t* src = pdm + s_off[p];
+#pragma unroll
+        for (int k = 0; k < kPM; ++k)
+            if (fresh || acc[k].nonzero())
+                cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
+        cp_async_commit();
+    };
     int p = 0, slot = 0;
-    issue(t, 0, 0);
+    issue(t, 0, 0, true);
     while (true) {
         int64_t nt = t;
         int np = p + 1;
         if (np == n) { np = 0; nt = t + tstride; }
         const bool more = nt < ntiles;
-        if (more) issue(nt, np, slot ^ 1); else cp_async_commit();
+        if (more) issue(nt, np, slot ^ 1, np == 0); else cp_async_commit();
         cp_async_wait1();
 #pragma unroll
         for (int k = 0; k < kPM; ++k) acc[k].fold(stage[(slot * kPM + k) * ld]);
@@ -323,7 +340,8 @@ constexpr int kFusedMaxN = 8192;
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
                const float* __restrict__ tf, int N, int K, int J, Borders bd, int uniform,
-               uint16_t* __restrict__ act, int32_t* __restrict__ nact,
+               const uint16_t* __restrict__ order, uint16_t* __restrict__ act,
+               int32_t* __restrict__ nact,
                uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
                uint8_t* __restrict__ out, int vec_ok)
 {
@@ -337,6 +355,7 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     extern __shared__ uint4 s_stage[];                 // [2][kAsyncBatch][kFusedThreads]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     pdl_wait();
+    const int mine = order && tid < K ? int(order[tid]) : tid;     // this thread's plane
     // ---- visibility bits: thread t holds intensities t + k * blockDim
     float a[kPer];
 #pragma unroll
@@ -371,7 +390,7 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     if (lane == 0 && warp < 8) s_bits[warp] = bal;
     __syncthreads();
     // ---- planes to combine: the active partitions, or index planes covering their runs
-    const int n = plan_maps(s_bits, K, J, s_list, s_scan);
+    const int n = plan_maps(s_bits, K, J, s_list, s_scan, mine);
     for (int j = tid; j < kMaxPartitions + kBatch; j += kFusedThreads)
         s_off[j] = int64_t(s_list[j < n ? j : 0]) * plane;     // padding: copies of plane 0
     if (blockIdx.x == 0) {
@@ -436,6 +455,79 @@ k_index_level(uint8_t* __restrict__ pdm, int64_t plane, int64_t G, int prev_base
     for (int64_t j = done + t0; j < G; j += stride) o[j] = min(a[j], b[j]);
 }
 
+// ---------------------------------------------------------------- plane order
+// Zero bytes of each plane on a fixed sample (kCoverSamples 16-byte chunks at an even
+// stride, or bytes where the plane is not 16-byte aligned): one CTA per plane, no atomics,
+// so the count is the same on every run.
+constexpr int kCoverSamples = 16384;
+constexpr int kOrderThreads = 256;
+static_assert(kMaxPartitions <= kOrderThreads, "one thread per partition ranks the planes");
+
+struct PlaneOrderBatch {
+    int n;
+    int start[kMaxBuildBatch + 1];             // first CTA (plane) of each context
+    PlaneOrderItem it[kMaxBuildBatch];
+};
+
+__global__ void __launch_bounds__(kOrderThreads)
+k_plane_cover(const __grid_constant__ PlaneOrderBatch B)
+{
+    __shared__ uint32_t s_w[kOrderThreads / 32];
+    const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
+    const PlaneOrderItem& it = B.it[i];
+    const int p = int(blockIdx.x) - B.start[i];
+    const uint8_t* src = it.pdm + int64_t(p) * it.plane;
+    const int tid = threadIdx.x;
+    pdl_wait();
+    uint32_t z = 0;                                            // zero bytes x 8 (vector path)
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && it.G >= 16) {
+        const int64_t nvec = it.G >> 4;
+        const int64_t ns = nvec < kCoverSamples ? nvec : kCoverSamples;
+        const int64_t step = nvec / ns;
+        const uint4* v4 = reinterpret_cast<const uint4*>(src);
+        for (int64_t j = tid; j < ns; j += kOrderThreads) {
+            const uint4 v = __ldcs(v4 + j * step);
+            z += __popc(__vcmpeq4(v.x, 0u)) + __popc(__vcmpeq4(v.y, 0u)) +
+                 __popc(__vcmpeq4(v.z, 0u)) + __popc(__vcmpeq4(v.w, 0u));
+        }
+    } else {
+        const int64_t ns = it.G < 16 * kCoverSamples ? it.G : 16 * kCoverSamples;
+        const int64_t step = ns > 0 ? it.G / ns : 1;
+        for (int64_t j = tid; j < ns; j += kOrderThreads) z += src[j * step] == 0 ? 8u : 0u;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, d);
+    if ((tid & 31) == 0) s_w[tid >> 5] = z;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kOrderThreads / 32; ++w) t += s_w[w];
+        it.cover[p] = t >> 3;
+    }
+}
+
+// Rank of partition t: the planes with more zero bytes, and those with as many and a lower
+// index, come before it.
+__global__ void __launch_bounds__(kOrderThreads)
+k_plane_order(const __grid_constant__ PlaneOrderBatch B)
+{
+    __shared__ uint32_t s_c[kMaxPartitions];
+    const PlaneOrderItem& it = B.it[blockIdx.x];
+    const int tid = threadIdx.x;
+    pdl_wait();
+    if (tid < it.K) s_c[tid] = it.cover[tid];
+    __syncthreads();
+    if (tid < it.K) {
+        const uint32_t c = s_c[tid];
+        int r = 0;
+        for (int q = 0; q < it.K; ++q) {
+            const uint32_t d = s_c[q];
+            r += (d > c || (d == c && q < tid)) ? 1 : 0;
+        }
+        it.order[r] = uint16_t(tid);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cudaStream_t s)
@@ -459,9 +551,10 @@ cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cu
 bool update_fused_ok(int N) { return N <= kFusedMaxN; }
 
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
-                                int N, int K, int J, const Borders& bd, int uniform, uint16_t* act,
-                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
-                                uint8_t* out, int num_sms, cudaStream_t s)
+                                int N, int K, int J, const Borders& bd, int uniform,
+                                const uint16_t* order, uint16_t* act, int32_t* nact,
+                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
+                                cudaStream_t s)
 {
     if (N > kFusedMaxN) return cudaErrorInvalidValue;
     const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
@@ -473,8 +566,9 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
     const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
     cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
     if (e != cudaSuccess) return e;
-    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform, act,
-                                                      nact, smask, smask_out, out, vec_ok);
+    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform,
+                                                      order, act, nact, smask, smask_out, out,
+                                                      vec_ok);
     return cudaGetLastError();
 }
 
@@ -487,10 +581,10 @@ cudaError_t launch_tf_active(const float* tf, int N, int K, const Borders& bd, i
 }
 
 cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Borders& bd,
-                              uint16_t* act, int32_t* nact, uint64_t* smask,
-                              uint64_t* smask_out, cudaStream_t s)
+                              const uint16_t* order, uint16_t* act, int32_t* nact,
+                              uint64_t* smask, uint64_t* smask_out, cudaStream_t s)
 {
-    k_active_set<<<1, kActThreads, 0, s>>>(tf, N, K, J, bd, act, nact, smask, smask_out);
+    k_active_set<<<1, kActThreads, 0, s>>>(tf, N, K, J, bd, order, act, nact, smask, smask_out);
     return cudaGetLastError();
 }
 
@@ -508,6 +602,25 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
     if (e != cudaSuccess) return e;
     return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), smem, s, pdm, plane, G,
                       act, nact, out, vec_ok);
+}
+
+cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > kMaxBuildBatch) return cudaErrorInvalidValue;
+    PlaneOrderBatch B;
+    B.n = n;
+    int ctas = 0;
+    for (int k = 0; k < n; ++k) {
+        if (items[k].K < 1 || items[k].K > kMaxPartitions) return cudaErrorInvalidValue;
+        B.it[k] = items[k];
+        B.start[k] = ctas;
+        ctas += items[k].K;
+    }
+    B.start[n] = ctas;
+    cudaError_t e = launch_pdl(k_plane_cover, dim3(unsigned(ctas)), dim3(kOrderThreads), 0, s, B);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_plane_order, dim3(unsigned(n)), dim3(kOrderThreads), 0, s, B);
 }
 
 }  // namespace dmk

@@ -218,9 +218,10 @@ class PartitionedDistanceMaps:
 
     def reload(self, stream=None, wait: bool = True):
         """Inverse of offload(): device buffers again, the maps copied back, the context
-        marked built (dm_mark_built rewrites the scratch's partition table).  With
-        wait=False the work stays queued on `stream` and `ready_event` marks its end: work
-        on another stream that reads the maps must wait for that event first."""
+        marked built (dm_mark_built rewrites the scratch's partition table and plane
+        order).  With wait=False the work stays queued on `stream` and `ready_event` marks
+        its end: work on another stream that reads the maps must wait for that event
+        first."""
         h = self._host
         if h is None:
             return
