@@ -44,22 +44,12 @@ L2_FLUSH_BYTES = 256 << 20
 # slow (the 64-item batch), so that the start event is reached only once the call is queued
 # and the interval holds device time alone.
 SPIN_CYCLES = 200_000
-# DRAM bytes per update launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by workload, with the hash of the kernel code it was taken
-# on; reported as null once that code has changed.
+# DRAM bytes of the update kernel from one ncu capture (dram__bytes_read.sum and
+# dram__bytes_write.sum over a few launches), keyed by workload, with the hash of the kernel
+# code it was taken on; reported as null once that code has changed.  Reads are kept per
+# byte of PDM planes that the same launches load (the kernel's own count), writes per
+# block of the grid, so that the record scales to other edits and sizes.
 NCU_TRAFFIC = {
-    # k_update_fused on ct (G = 2,097,152), the first five edits (|S| = 7, 7, 7, 6, 6):
-    # 2,112,963 B read per active plane on average, 0 B written (D' stays in L2)
-    "ct": {"source_sha": "60681a3863a8b7b4", "G": 2097152,
-           "read_per_active_plane": 2112963.0, "write": 0.0},
-    # k_update_fused on mid (the large recipe cut to 448 slices, G = 7,340,032), the first
-    # five edits (|S| = 30, 31, 31, 31, 35): 7,343,537 B read per active plane on average,
-    # 4,175,104 B written; the large workload's traffic is this capture scaled by G (the
-    # kernel streams the same per-block bytes at both sizes)
-    "mid": {"source_sha": "60681a3863a8b7b4", "G": 7340032,
-            "read_per_active_plane": 7343537.0, "write": 4175104.0},
-    "large": {"source_sha": "60681a3863a8b7b4", "G": 7340032,
-              "read_per_active_plane": 7343537.0, "write": 4175104.0},
 }
 
 
@@ -106,14 +96,14 @@ def update_kernel_sources(csrc):
     return [os.path.join(csrc, "dm_update.cu"), os.path.join(csrc, "dm_internal.cuh")]
 
 
-def ncu_traffic(workload, G, mean_active):
+def ncu_traffic(workload, G, mean_loaded):
     """DRAM bytes per update launch from the committed ncu capture, scaled to this grid and
-    to the mean number of active planes; None once the kernel source has changed."""
+    to the mean PDM bytes a launch loads; None once the kernel source has changed."""
     tr = NCU_TRAFFIC.get(workload)
     csrc = os.path.join(ROOT, "paper_2407_21552_gb300", "csrc")
     if not tr or tr.get("source_sha") != code_sha(*update_kernel_sources(csrc)):
         return None
-    return float((tr["read_per_active_plane"] * mean_active + tr["write"]) * G / tr["G"])
+    return float(tr["read_per_loaded_byte"] * mean_loaded + tr["write_per_block"] * G)
 
 
 def parse():
@@ -437,7 +427,17 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
     del evs
     masks = am.cpu().numpy().view(np.uint64)
     nact = np.array([sum(bin(int(x)).count("1") for x in row) for row in masks])
-    bytes_upd = np.tile((nact + 1) * G, steps).astype(np.float64)  # per launch, algorithmic
+    # the PDM bytes each edit's combine loads (plane order, stop at 0), counted in the kernel
+    # on an untimed replay of the same edits on the same maps: with the write of D', the
+    # update's algorithmic bytes per launch, at most the method's (|S| + 1) G
+    loaded = torch.zeros(E, dtype=torch.int64, device=dev)
+    for e in range(E):
+        eng.set_profile_counter(loaded[e:e + 1])
+        eng.update_tf(tfs[e], out=out)
+    eng.set_profile_counter(None)
+    loaded = loaded.cpu().numpy().astype(np.float64)
+    bytes_upd = np.tile(loaded + G, steps)                          # per launch, algorithmic
+    bytes_plain = np.tile((nact + 1) * G, steps).astype(np.float64)  # every active plane read
     upd_a = np.asarray(upd)
     # the update of an N <= 8192 TF is one kernel (k_update_fused): its events bracket it
     fused = w["N"] <= 8192
@@ -528,7 +528,12 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
         "update": {"p50_ms": p50u, "p99_ms": p99u, "mean_ms": float(upd_a.mean()),
                    "calls": len(upd),
                    "gbs_p50": float(np.median(bytes_upd / (upd_a * 1e-3)) / 1e9),
-                   "voxels_per_s_p50": V / (p50u * 1e-3)},
+                   "voxels_per_s_p50": V / (p50u * 1e-3),
+                   "loaded_fraction_of_active_planes": float(loaded.sum() / (nact.sum() * G))
+                   if nact.sum() else None,
+                   "plain_bytes_per_launch": float(bytes_plain.mean()),
+                   "plain_gbs_mean": float(bytes_plain.sum() / (upd_a.sum() * 1e-3)) / 1e9,
+                   "loaded_bytes_first_edits": [int(x) for x in loaded[:5]]},
         "full_recompute": {"p50_ms": p50f, "p99_ms": p99f, "mean_ms": float(np.mean(full)),
                            "mode": "min/max occupancy", "voxels_per_s_p50": V / (p50f * 1e-3)},
         "speedup_vs_full_recompute_p50": p50f / p50u,
@@ -543,13 +548,13 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
         "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": peak[0], "unit": "GB/s",
                      "frac": achieved / peak[0] if achieved else None,
-                     "traffic": ncu_traffic(name, G, float(nact.mean())),
+                     "traffic": ncu_traffic(name, G, float(loaded.mean())),
                      "peak_source": peak[1],
                      "algorithmic_bytes_per_launch": float(bytes_upd.mean()),
                      "mean_launch_us": float(upd_a.mean() * 1e3)},
         "clocks": clk,
         "e2e": e2e_res,
-        "gpu_launches": steps * (5 + E * ((1 if fused else 2) + 4)),
+        "gpu_launches": steps * (7 + E * ((1 if fused else 2) + 4)),
     }
     if idx:
         idx["speedup_vs_full_recompute_p50"] = p50f / idx["p50_ms"]
@@ -729,13 +734,24 @@ def run_batch(args, ws, rank, local):
     bat = [ev[k][2].elapsed_time(ev[k][3]) for k in range(K)]
     gra = [ev[k][4].elapsed_time(ev[k][5]) for k in range(K)]
     vox = sum(int(np.prod(sp["dims"])) for sp in specs)
-    # algorithmic bytes of a step: sum over items of (|S_i| + 1) * G_i (the same edits go
-    # through the separate and the batched updates)
+    # algorithmic bytes of a step: the PDM bytes the batched combine loads for the step's
+    # edits (plane order, stop at 0), counted in the kernel on an untimed replay of the same
+    # calls, plus the writes of the n maps D'; at most sum over items of (|S_i| + 1) G_i,
+    # the bytes when every active plane is read (the same edits go through the separate and
+    # the batched updates)
     Gs = np.array([e.G for e in engs], dtype=np.float64)
     masks = am.cpu().numpy().view(np.uint64)
     nact = np.array([[sum(bin(int(x)).count("1") for x in masks[k, i]) for i in range(n)]
                      for k in range(K)], dtype=np.float64)
-    step_bytes = ((nact + 1) * Gs).sum(axis=1)
+    counted = torch.zeros(E, dtype=torch.int64, device=dev)
+    for kk in sorted({k % E for k in range(K)}):       # the counter of items[0]'s context
+        engs[0].set_profile_counter(counted[kk:kk + 1])
+        A.dm_update_tf_batch(prepared[kk], tr.tuning, sp_)
+    engs[0].set_profile_counter(None)
+    counted = counted.cpu().numpy().astype(np.float64)
+    step_loaded = np.array([counted[k % E] for k in range(K)])
+    step_bytes = step_loaded + Gs.sum()
+    plain_step_bytes = ((nact + 1) * Gs).sum(axis=1)
     bat_gbs = step_bytes / (np.array(bat) * 1e-3) / 1e9
     peak, peak_src = measured_peak()
     multi = multi_edit_leg(engs, edits, specs, tr, flush, stream, min(8, E), reps=max(5, K))
@@ -763,6 +779,9 @@ def run_batch(args, ws, rank, local):
                      "unit": "GB/s", "frac": float(step_bytes.sum() / (np.sum(bat) * 1e-3) / 1e9) / peak,
                      "traffic": None, "peak_source": peak_src,
                      "algorithmic_bytes_per_step": float(step_bytes.mean()),
+                     "plain_bytes_per_step": float(plain_step_bytes.mean()),
+                     "loaded_fraction_of_active_planes":
+                         float(step_loaded.sum() / (nact * Gs).sum()) if nact.sum() else None,
                      "mean_active_partitions": float(nact.mean())},
         "autotune": {"block": tr.block, "combine_ctas_per_sm": tr.ctas_per_sm,
                      "loads_per_stage": tr.loads_per_stage,
@@ -803,9 +822,21 @@ def multi_edit_leg(engs, edits, specs, tr, flush, stream, n_edits, reps):
     m = am.cpu().numpy().view(np.uint64)
     Gs = np.array([e.G for e in engs], dtype=np.float64)
     cnt = lambda row: sum(bin(int(x)).count("1") for x in row)  # noqa: E731
-    sep_bytes = sum((cnt(m[k, i]) + 1) * Gs[i] for k in range(n_edits) for i in range(n))
+    sep_plain = sum((cnt(m[k, i]) + 1) * Gs[i] for k in range(n_edits) for i in range(n))
     union = [np.bitwise_or.reduce(m[:, i], axis=0) for i in range(n)]
-    ws_bytes = sum((cnt(union[i]) + n_edits) * Gs[i] for i in range(n))
+    ws_plain = sum((cnt(union[i]) + n_edits) * Gs[i] for i in range(n))
+    # algorithmic bytes: the PDM bytes each variant's combines load (counted in the kernels
+    # on an untimed replay, the counter of items[0]'s context) plus the writes of the maps
+    loaded = torch.zeros(2, dtype=torch.int64, device=dev)
+    engs[0].set_profile_counter(loaded[0:1])
+    for k in range(n_edits):
+        A.dm_update_tf_batch(per_call[k], tr.tuning, sp_)
+    engs[0].set_profile_counter(loaded[1:2])
+    A.dm_update_tf_batch_ws(every, tr.tuning, ws.data_ptr(), nbytes, sp_)
+    engs[0].set_profile_counter(None)
+    loaded = loaded.cpu().numpy().astype(np.float64)
+    sep_bytes = float(loaded[0] + n_edits * Gs.sum())
+    ws_bytes = float(loaded[1] + n_edits * Gs.sum())
     t_sep, t_ws = [], []
     for r in range(reps + 2):
         flush()
@@ -829,8 +860,8 @@ def multi_edit_leg(engs, edits, specs, tr, flush, stream, n_edits, reps):
     p_ws = pct(t_ws, 50)
     return {"volumes": n, "edits_per_volume": n_edits,
             "separate_calls": {"p50_ms": pct(t_sep, 50), "calls": n_edits,
-                               "algorithmic_bytes": sep_bytes},
-            "one_call": {"p50_ms": p_ws, "algorithmic_bytes": ws_bytes,
+                               "algorithmic_bytes": sep_bytes, "plain_bytes": sep_plain},
+            "one_call": {"p50_ms": p_ws, "algorithmic_bytes": ws_bytes, "plain_bytes": ws_plain,
                          "gbs": ws_bytes / (p_ws * 1e-3) / 1e9,
                          "frac": ws_bytes / (p_ws * 1e-3) / 1e9 / peak},
             "speedup": pct(t_sep, 50) / p_ws}

@@ -266,6 +266,19 @@ dm_status dm_update_tf_batch_ws(const dm_batch_item *items, int32_t n,
 dm_status dm_set_profile_events(dm_ctx *ctx, void *ev_begin, void *ev_end);
 
 /*
+ * Instrumentation: when d_bytes (device memory, 8-byte aligned, owned and zeroed by the
+ * caller) is set, every later dm_update_tf() / dm_update_tf_host() on the context adds to
+ * *d_bytes the bytes of PDM planes its combine loads (Eq. 1): 16 per 16-byte chunk of a
+ * plane, 1 per byte past the last whole chunk.  With the plane order and the stop at 0 of
+ * the update this is at most |S| * G; it is the update's algorithmic read traffic, which a
+ * caller divides by the kernel time for its bandwidth.  dm_update_tf_batch and
+ * dm_update_tf_batch_ws add the bytes of the whole call to the counter of items[0].ctx (a
+ * separate build of their combine kernel does the counting).  The count costs a few
+ * instructions per load and one atomic per warp; pass NULL to stop.  No effect on D'.
+ */
+dm_status dm_set_profile_counter(dm_ctx *ctx, uint64_t *d_bytes);
+
+/*
  * TF update for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is a deployment variant of dm_update_tf (same results, bit for bit).
  *

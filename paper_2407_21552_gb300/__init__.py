@@ -16,7 +16,8 @@ from ._abi import (DM_OK, DM_ERR_INVALID_ARG, DM_ERR_UNSUPPORTED, DM_ERR_CUDA,  
                    DM_INDEX_RANGES, DmError,
                    dm_create, dm_query_sizes, dm_bind, dm_build_partitions,
                    dm_build_partitions_batch, dm_update_tf, dm_update_tf_host,
-                   dm_full_recompute, dm_set_profile_events, dm_update_tf_batch,
+                   dm_full_recompute, dm_set_profile_events, dm_set_profile_counter,
+                   dm_update_tf_batch,
                    dm_batch_workspace_bytes, dm_update_tf_batch_ws, dm_update_tf_noalloc,
                    dm_render,
                    dm_sync, dm_destroy,

@@ -34,6 +34,7 @@ DM_BUILD_BATCH_MAX_ITEMS = 64
 EXPORTED = ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions",
             "dm_build_partitions_batch", "dm_update_tf",
             "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
+            "dm_set_profile_counter",
             "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_batch_workspace_bytes",
             "dm_update_tf_batch_ws", "dm_render", "dm_config_hash",
             "dm_mark_built", "dm_sync", "dm_destroy",
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.dm_update_tf_host.argtypes = [P, P, P, P]
     lib.dm_full_recompute.argtypes = [P, P, P, P, P]
     lib.dm_set_profile_events.argtypes = [P, P, P]
+    lib.dm_set_profile_counter.argtypes = [P, P]
     lib.dm_update_tf_noalloc.argtypes = [P, ctypes.c_size_t, ctypes.c_int64, S, P, S, P, P, P]
     lib.dm_update_tf_batch.argtypes = [ctypes.POINTER(dm_batch_item), S,
                                        ctypes.POINTER(dm_batch_tuning), P]
@@ -123,6 +125,7 @@ def load(path: str = LIB_PATH):
     for n in ("dm_create", "dm_query_sizes", "dm_bind", "dm_build_partitions",
               "dm_build_partitions_batch", "dm_update_tf",
               "dm_update_tf_host", "dm_full_recompute", "dm_set_profile_events",
+              "dm_set_profile_counter",
               "dm_update_tf_noalloc", "dm_update_tf_batch", "dm_update_tf_batch_ws",
               "dm_render", "dm_config_hash", "dm_mark_built", "dm_sync", "dm_version"):
         getattr(lib, n).restype = S
@@ -228,6 +231,11 @@ def dm_full_recompute(ctx, d_volume, d_tf_rgba, d_out, stream):
 
 def dm_set_profile_events(ctx, ev_begin, ev_end):
     _check(ctx, load().dm_set_profile_events(ctx, ev_begin, ev_end), "dm_set_profile_events")
+
+
+def dm_set_profile_counter(ctx, d_bytes):
+    """d_bytes: device address of a zeroed uint64 (or None to stop)."""
+    _check(ctx, load().dm_set_profile_counter(ctx, d_bytes), "dm_set_profile_counter")
 
 
 def dm_update_tf_noalloc(d_pdm, plane_stride, num_blocks, num_partitions, borders, tf_size,

@@ -33,6 +33,7 @@ struct dm_ctx {
     bool built;
     bool minmax_built;
     cudaEvent_t ev_begin, ev_end;   // optional, caller-owned (dm_set_profile_events)
+    uint64_t* prof_bytes;           // optional, caller-owned (dm_set_profile_counter)
     char err[256];
 };
 
@@ -220,6 +221,12 @@ static dmk::PlaneOrderItem plane_order_item(const dm_ctx* c)
     it.cover = reinterpret_cast<uint32_t*>(scratch + c->off_cover);
     it.order = reinterpret_cast<uint16_t*>(scratch + c->off_order);
     return it;
+}
+
+static unsigned long long* prof_count(const dm_ctx* c)
+{
+    static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "64-bit counter");
+    return reinterpret_cast<unsigned long long*>(c->prof_bytes);
 }
 
 static const uint16_t* plane_order(const dm_ctx* c)
@@ -414,7 +421,8 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
                                                  ctx->geo.plane, ctx->geo.G, d_tf, N, K,
                                                  ctx->J, ctx->borders, ctx->uniform_borders ? 1 : 0,
                                                  plane_order(ctx), act, nact, smask,
-                                                 d_active_mask_out, d_out, ctx->num_sms, s);
+                                                 d_active_mask_out, d_out, ctx->num_sms,
+                                                 prof_count(ctx), s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "update");
         if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
             return cuda_fail(ctx, e, "profile event");
@@ -427,7 +435,7 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
     if (ctx->ev_begin && (e = cudaEventRecord(ctx->ev_begin, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "profile event");
     e = dmk::launch_combine(static_cast<const uint8_t*>(ctx->d_pdm), ctx->geo.plane, ctx->geo.G,
-                            act, nact, d_out, ctx->num_sms, s);
+                            act, nact, d_out, ctx->num_sms, prof_count(ctx), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "combine");
     if (ctx->ev_end && (e = cudaEventRecord(ctx->ev_end, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "profile event");
@@ -647,7 +655,8 @@ dm_status dm_update_tf_batch(const dm_batch_item* items, int32_t n, const dm_bat
             d.tf[0] = items[i0 + k].d_tf_rgba;
             d.out[0] = items[i0 + k].d_out;
         }
-        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
+        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms,
+                                                 prof_count(first), s);
         if (e != cudaSuccess) return cuda_fail(first, e, "batched update");
     }
     return DM_OK;
@@ -705,7 +714,8 @@ dm_status dm_update_tf_batch_ws(const dm_batch_item* items, int32_t n,
                 ++d.E;
             }
             if (++m == dmk::kMaxBatch) {
-                cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
+                cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms,
+                                                 prof_count(first), s);
                 if (e != cudaSuccess) {
                     delete[] taken;
                     return cuda_fail(first, e, "batched update");
@@ -717,7 +727,8 @@ dm_status dm_update_tf_batch_ws(const dm_batch_item* items, int32_t n,
     }
     delete[] taken;
     if (m > 0) {
-        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms, s);
+        cudaError_t e = dmk::launch_update_batch(desc, m, bt, first->num_sms,
+                                                 prof_count(first), s);
         if (e != cudaSuccess) return cuda_fail(first, e, "batched update");
     }
     return DM_OK;
@@ -730,6 +741,15 @@ dm_status dm_set_profile_events(dm_ctx* ctx, void* ev_begin, void* ev_end)
         return fail(ctx, DM_ERR_INVALID_ARG, "dm_set_profile_events: set both events or neither");
     ctx->ev_begin = static_cast<cudaEvent_t>(ev_begin);
     ctx->ev_end = static_cast<cudaEvent_t>(ev_end);
+    return DM_OK;
+}
+
+dm_status dm_set_profile_counter(dm_ctx* ctx, uint64_t* d_bytes)
+{
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    if (d_bytes && !aligned(d_bytes, 8))
+        return fail(ctx, DM_ERR_INVALID_ARG, "dm_set_profile_counter: misaligned counter");
+    ctx->prof_bytes = d_bytes;
     return DM_OK;
 }
 

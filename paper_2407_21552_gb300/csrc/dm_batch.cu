@@ -41,6 +41,7 @@ struct Group {
 
 struct Params {
     int n;
+    unsigned long long* count;                 // PDM bytes loaded (measurement; may be null)
     int64_t q, r;                              // CTA b takes q units, plus one if b < r
     int64_t unit_prefix[kMaxBatch + 1];        // work units before group i (256 lanes each)
     Group g[kMaxBatch];
@@ -191,8 +192,8 @@ struct GroupMin {
 
 // Bytes past the last whole 16-byte chunk of a group (fewer than 16): one warp, the lanes
 // over the group's planes, then a warp min per byte and TF.
-template <int EMAX>
-__device__ __forceinline__ void group_tail(const Group& g, int lane)
+template <int EMAX, bool COUNT>
+__device__ __forceinline__ void group_tail(const Group& g, int lane, unsigned& loaded)
 {
     const int64_t g0 = (g.G >> 4) << 4;
     const int rem = int(g.G - g0);
@@ -209,6 +210,7 @@ __device__ __forceinline__ void group_tail(const Group& g, int lane)
 #pragma unroll
             for (int r = 0; r < 16; ++r)
                 if (r < rem) m[r] = min(m[r], unsigned(src[r]));
+            if (COUNT) loaded += unsigned(rem);
         }
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -222,8 +224,10 @@ __device__ __forceinline__ void group_tail(const Group& g, int lane)
 
 // Eq. 1 over every group's work units; CTA b takes a contiguous range of units.  KB plane
 // loads per stage, two stages in flight.  With one TF per group, at most 40 registers a
-// thread, so that 6 CTAs fit an SM next to their 6 x 34 KiB of shared memory.
-template <int EMAX, int KB>
+// thread, so that 6 CTAs fit an SM next to their 6 x 34 KiB of shared memory.  COUNT: the
+// measurement variant, which adds the PDM bytes it loads to *P.count (its own
+// instantiation, so that the counter costs the timed kernel no register).
+template <int EMAX, int KB, bool COUNT>
 __global__ void __launch_bounds__(kThreads, EMAX == 1 ? 6 : 2)
 k_combine_group(const __grid_constant__ Params P)
 {
@@ -246,10 +250,11 @@ k_combine_group(const __grid_constant__ Params P)
     }
     while (gi < P.n && P.unit_prefix[gi + 1] <= u0) ++gi;     // skip empty groups
     pdl_wait();                                               // active sets are visible
+    unsigned bytes = 0;                                       // PDM bytes loaded (P.count)
     // bytes past the last whole chunk of each vectorised group: one warp per group
     for (int i = int(blockIdx.x) * (kThreads / 32) + (tid >> 5); i < P.n;
          i += int(gridDim.x) * (kThreads / 32))
-        if (P.g[i].vec) group_tail<EMAX>(P.g[i], tid & 31);
+        if (P.g[i].vec) group_tail<EMAX, COUNT>(P.g[i], tid & 31, bytes);
     int loaded = -1, n = 0;
     for (int64_t u = u0; u < u1; ++u) {
         while (P.unit_prefix[gi + 1] <= u) ++gi;
@@ -284,13 +289,16 @@ k_combine_group(const __grid_constant__ Params P)
                 if (nb > 0) {
                     for (int k = 0; k < KB; ++k) cp_async16(&s_stage[0][k][tid], src + s_off[k]);
                     asm volatile("cp.async.commit_group;" ::: "memory");
+                    if (COUNT) bytes += 16u * unsigned(min(KB, n));
                 }
                 for (int b = 0; b < nb; ++b) {
                     // a chunk at 0 in every byte of every TF is final: its later planes are
                     // not loaded, and their stale slots fold into minima of 0
-                    if (b + 1 < nb && acc.live(g.E))
+                    if (b + 1 < nb && acc.live(g.E)) {
                         for (int k = 0; k < KB; ++k)
                             cp_async16(&s_stage[(b + 1) & 1][k][tid], src + s_off[(b + 1) * KB + k]);
+                        if (COUNT) bytes += 16u * unsigned(min(KB, n - (b + 1) * KB));
+                    }
                     asm volatile("cp.async.commit_group;" ::: "memory");
                     asm volatile("cp.async.wait_group 1;" ::: "memory");
 #pragma unroll
@@ -308,6 +316,7 @@ k_combine_group(const __grid_constant__ Params P)
             unsigned a[EMAX];
 #pragma unroll
             for (int e = 0; e < EMAX; ++e) a[e] = 255;
+            if (COUNT) bytes += unsigned(n);
             for (int j = 0; j < n; ++j) {
                 const unsigned v = g.pdm[s_off[j] + lane_unit];
                 const unsigned em = EMAX > 1 ? unsigned(s_emk[j]) : 1u;
@@ -320,15 +329,24 @@ k_combine_group(const __grid_constant__ Params P)
                 if (EMAX == 1 || e < g.E) g.out[e][lane_unit] = uint8_t(a[e]);
         }
     }
+    if (COUNT) add_warp_count(P.count, bytes);
+}
+
+template <int EMAX, int KB, bool COUNT>
+cudaError_t launch_combine_group_t(const Params& P, int64_t ctas, cudaStream_t s)
+{
+    const size_t smem = size_t(2) * KB * kThreads * sizeof(uint4);
+    cudaError_t e = ensure_dynamic_smem<k_combine_group<EMAX, KB, COUNT>>(int(smem));
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_combine_group<EMAX, KB, COUNT>, dim3(unsigned(ctas)), dim3(kThreads),
+                      smem, s, P);
 }
 
 template <int EMAX, int KB>
 cudaError_t launch_combine_group(const Params& P, int64_t ctas, cudaStream_t s)
 {
-    const size_t smem = size_t(2) * KB * kThreads * sizeof(uint4);
-    cudaError_t e = ensure_dynamic_smem<k_combine_group<EMAX, KB>>(int(smem));
-    if (e != cudaSuccess) return e;
-    return launch_pdl(k_combine_group<EMAX, KB>, dim3(unsigned(ctas)), dim3(kThreads), smem, s, P);
+    return P.count ? launch_combine_group_t<EMAX, KB, true>(P, ctas, s)
+                   : launch_combine_group_t<EMAX, KB, false>(P, ctas, s);
 }
 
 template <int EMAX>
@@ -346,11 +364,12 @@ cudaError_t launch_pair(const Params& P, int64_t ctas, int kb, cudaStream_t s)
 size_t batch_list_entries(int planes) { return size_t(planes) + kPad; }
 
 cudaError_t launch_update_batch(const BatchGroup* groups, int n, const BatchTuning& tune,
-                                int num_sms, cudaStream_t s)
+                                int num_sms, unsigned long long* count, cudaStream_t s)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     Params P;
     P.n = n;
+    P.count = count;
     P.unit_prefix[0] = 0;
     int emax = 1;
     for (int i = 0; i < n; ++i) {

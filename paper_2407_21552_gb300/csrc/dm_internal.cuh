@@ -121,6 +121,15 @@ struct ByteMin16 {                                   // running byte minimum of 
     }
 };
 
+// Adds a warp's sum of v to *count (one atomic, lane 0).  Every lane of the warp must call
+// it at the same point (the update kernels do so at their end).
+__device__ __forceinline__ void add_warp_count(unsigned long long* count, unsigned long long v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(count, v);
+}
+
 // ---------------------------------------------------------------- partition-range index
 // Optional sparse index over the K PDMs: plane (k, i) = min of PDM_i .. PDM_{i + 2^k - 1}
 // for k = 0..J (level 0 = the PDMs), J = floor(log2 K).  Level k starts at plane
@@ -246,16 +255,19 @@ cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Border
 // Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
 bool update_fused_ok(int N);
 // `uniform`: the borders are the default floor(p N / K), which the kernel computes instead of
-// indexing the parameter array per thread.  `order` as in launch_active_set.
+// indexing the parameter array per thread.  `order` as in launch_active_set.  `count`: a
+// device counter to which the kernel adds the bytes of PDM planes it loads (null: none).
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
                                 int N, int K, int J, const Borders& bd, int uniform,
                                 const uint16_t* order, uint16_t* act, int32_t* nact,
                                 uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                cudaStream_t s);
+                                unsigned long long* count, cudaStream_t s);
 
-// D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.
+// D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.  `count` as in
+// launch_update_fused.
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
-                           const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s);
+                           const int32_t* nact, uint8_t* out, int num_sms,
+                           unsigned long long* count, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched update
 constexpr int kMaxBatch = 64;          // groups per launch pair (descriptors as parameters)
@@ -288,8 +300,9 @@ struct BatchTuning {
 size_t batch_list_entries(int planes);
 
 // Active sets of up to kMaxBatch groups (one CTA each), then one combine over all their
-// work units (PDL).
+// work units (PDL).  `count`: a device counter to which the combine adds the bytes of PDM
+// planes it loads (null: none).
 cudaError_t launch_update_batch(const BatchGroup* groups, int n, const BatchTuning& tune,
-                                int num_sms, cudaStream_t s);
+                                int num_sms, unsigned long long* count, cudaStream_t s);
 
 }  // namespace dmk

@@ -139,7 +139,7 @@ extern "C" dm_status dm_update_tf_noalloc(const uint8_t* d_pdm, size_t plane_str
     cudaError_t e = dmk::launch_combine(d_pdm, int64_t(plane_stride), num_blocks,
                                         reinterpret_cast<const uint16_t*>(scratch + kOffAct),
                                         reinterpret_cast<const int32_t*>(scratch + kOffCount),
-                                        d_out, sms, s);
+                                        d_out, sms, nullptr, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return DM_ERR_CUDA;

@@ -172,6 +172,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Measurement aid: the combine functions add the bytes of PDM planes each thread loads to
+// *loads (a per-thread counter; null: not counted), and the kernel adds each warp's total
+// to the caller's device counter once, at its end (add_warp_count).
+
 // D' for `nvec` 16-byte chunks through cp.async: each thread streams its chunk of every
 // active plane into its own shared-memory slots, kAsyncBatch planes per group with two
 // groups in flight (no registers held by the loads), and folds a group once it landed.
@@ -186,7 +190,8 @@ constexpr int kAsyncBatch = 8;
 __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__ pdm,
                                                      const int64_t* s_off, int n, int64_t nvec,
                                                      int64_t t0, int64_t stride, uint4* stage,
-                                                     int ld, uint8_t* __restrict__ out)
+                                                     int ld, uint8_t* __restrict__ out,
+                                                     unsigned* loads)
 {
     const int nb = (n + kAsyncBatch - 1) / kAsyncBatch;       // batches per chunk
     if (nb == 0) {
@@ -206,6 +211,7 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
                            src + s_off[b * kAsyncBatch + k]);
         }
         cp_async_commit();
+        if (loads && load) *loads += 16u * unsigned(min(kAsyncBatch, n - b * kAsyncBatch));
     };
     if (v >= nvec) return;
     issue(v, 0, 0, true);
@@ -245,7 +251,8 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
                                                      const int64_t* s_off, int n, int64_t ntiles,
                                                      int64_t tile0, int64_t tstride, uint4* stage,
                                                      int ld, uint8_t* __restrict__ out, int warp,
-                                                     int lane, int warps)
+                                                     int lane, int warps,
+                                                     unsigned* loads)
 {
     const int64_t tile_chunks = int64_t(warps) * 32 * kPM;
     auto chunk_of = [&](int64_t t, int k) {
@@ -266,11 +273,15 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
     // fresh: the first plane of a tile (the accumulators still hold the previous tile)
     auto issue = [&](int64_t tt, int p, int slot, bool fresh) {
         const uint8_t* src = pdm + s_off[p];
+        unsigned issued = 0;
 #pragma unroll
         for (int k = 0; k < kPM; ++k)
-            if (fresh || acc[k].nonzero())
+            if (fresh || acc[k].nonzero()) {
                 cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
+                ++issued;
+            }
         cp_async_commit();
+        if (loads) *loads += 16u * issued;
     };
     int p = 0, slot = 0;
     issue(t, 0, 0, true);
@@ -301,7 +312,7 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
 __global__ void __launch_bounds__(kCombineThreads)
 k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
           const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
-          uint8_t* __restrict__ out, int vec_ok)
+          uint8_t* __restrict__ out, int vec_ok, unsigned long long* __restrict__ count)
 {
     constexpr int kBatch = 8;                          // plane loads issued before any use
     __shared__ int64_t s_off[kMaxPartitions + kBatch];
@@ -317,9 +328,11 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     const int64_t stride = int64_t(gridDim.x) * kCombineThreads;
     const int64_t t0 = int64_t(blockIdx.x) * kCombineThreads + threadIdx.x;
     int64_t done = 0;
+    unsigned loaded = 0;
+    unsigned* lp = count ? &loaded : nullptr;
     if (vec_ok) {
         combine_chunks_async(pdm, s_off, n, G >> 4, t0, stride, s_stage + threadIdx.x,
-                             kCombineThreads, out);
+                             kCombineThreads, out, lp);
         done = (G >> 4) << 4;
     }
     // bytes not covered by whole aligned chunks
@@ -327,7 +340,9 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         unsigned acc = 255;
         for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
         out[i] = uint8_t(acc);
+        loaded += unsigned(n);
     }
+    if (count) add_warp_count(count, loaded);
 }
 
 // Step 1 and step 2 in one launch (TFs with N <= kFusedMaxN): every CTA derives S from
@@ -343,7 +358,7 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
                const uint16_t* __restrict__ order, uint16_t* __restrict__ act,
                int32_t* __restrict__ nact,
                uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
-               uint8_t* __restrict__ out, int vec_ok)
+               uint8_t* __restrict__ out, int vec_ok, unsigned long long* __restrict__ count)
 {
     constexpr int kBatch = 8;
     constexpr int kPer = kFusedMaxN / kFusedThreads;          // alphas per thread (max)
@@ -407,6 +422,8 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     const int64_t stride = int64_t(gridDim.x) * kFusedThreads;
     const int64_t t0 = int64_t(blockIdx.x) * kFusedThreads + tid;
     int64_t done = 0;
+    unsigned loaded = 0;                                       // plane bytes (count only)
+    unsigned* lp = count ? &loaded : nullptr;
     if (vec_ok) {
         // Large maps: whole plane-major tiles while every CTA gets at least two and they
         // spread evenly (all of them when the last round fills three quarters of the CTAs,
@@ -419,16 +436,18 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         else if (ntiles % grid != 0 && 4 * (ntiles % grid) < 3 * grid) ntiles -= ntiles % grid;
         if (ntiles > 0)
             combine_tiles_planar(pdm, s_off, n, ntiles, blockIdx.x, grid, s_stage + tid,
-                                 kFusedThreads, out, warp, lane, kFusedThreads / 32);
+                                 kFusedThreads, out, warp, lane, kFusedThreads / 32, lp);
         combine_chunks_async(pdm, s_off, n, nvec, ntiles * tile_chunks + t0, stride,
-                             s_stage + tid, kFusedThreads, out);
+                             s_stage + tid, kFusedThreads, out, lp);
         done = nvec << 4;
     }
     for (int64_t i = done + t0; i < G; i += stride) {
         unsigned acc = 255;
         for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
         out[i] = uint8_t(acc);
+        loaded += unsigned(n);
     }
+    if (count) add_warp_count(count, loaded);
 }
 
 // One level of the partition-range index: plane (k, i) = min(plane (k-1, i),
@@ -554,7 +573,7 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
                                 int N, int K, int J, const Borders& bd, int uniform,
                                 const uint16_t* order, uint16_t* act, int32_t* nact,
                                 uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                cudaStream_t s)
+                                unsigned long long* count, cudaStream_t s)
 {
     if (N > kFusedMaxN) return cudaErrorInvalidValue;
     const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
@@ -568,7 +587,7 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
     if (e != cudaSuccess) return e;
     k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform,
                                                       order, act, nact, smask, smask_out, out,
-                                                      vec_ok);
+                                                      vec_ok, count);
     return cudaGetLastError();
 }
 
@@ -589,7 +608,8 @@ cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Border
 }
 
 cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const uint16_t* act,
-                           const int32_t* nact, uint8_t* out, int num_sms, cudaStream_t s)
+                           const int32_t* nact, uint8_t* out, int num_sms,
+                           unsigned long long* count, cudaStream_t s)
 {
     const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
                        ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (plane % 16 == 0);
@@ -601,7 +621,7 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
     cudaError_t e = ensure_dynamic_smem<k_combine>(int(smem));
     if (e != cudaSuccess) return e;
     return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), smem, s, pdm, plane, G,
-                      act, nact, out, vec_ok);
+                      act, nact, out, vec_ok, count);
 }
 
 cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t s)

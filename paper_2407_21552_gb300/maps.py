@@ -121,6 +121,14 @@ class PartitionedDistanceMaps:
         A.dm_full_recompute(self.ctx, vp, tf.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
+    def set_profile_counter(self, counter: torch.Tensor | None):
+        """Count the bytes of PDM planes that later updates load into `counter` (a zeroed
+        device int64 tensor of one element, kept alive by the caller), or stop (None)."""
+        if counter is not None and (counter.device.type != "cuda" or counter.numel() != 1
+                                    or counter.element_size() != 8):
+            raise ValueError("the counter is one 8-byte element in device memory")
+        A.dm_set_profile_counter(self.ctx, counter.data_ptr() if counter is not None else None)
+
     def sync(self, stream=None):
         A.dm_sync(self.ctx, _stream_handle(stream))
 

@@ -21,13 +21,12 @@ def test_ncu_traffic_scales_the_record_and_drops_stale_ones(monkeypatch):
     csrc = os.path.join(bench.ROOT, "paper_2407_21552_gb300", "csrc")
     sha = bench.code_sha(*bench.update_kernel_sources(csrc))
     monkeypatch.setattr(bench, "NCU_TRAFFIC", {
-        "cur": {"source_sha": sha, "G": 1000, "read_per_active_plane": 1000.0, "write": 50.0},
-        "old": {"source_sha": "0" * 16, "G": 1000, "read_per_active_plane": 1000.0,
-                "write": 50.0}})
-    # 2000 blocks, 3 active planes: (3 * 1000 + 50) * 2000 / 1000
-    assert bench.ncu_traffic("cur", 2000, 3.0) == 6100.0
-    assert bench.ncu_traffic("old", 2000, 3.0) is None
-    assert bench.ncu_traffic("none", 2000, 3.0) is None
+        "cur": {"source_sha": sha, "read_per_loaded_byte": 1.25, "write_per_block": 0.5},
+        "old": {"source_sha": "0" * 16, "read_per_loaded_byte": 1.25, "write_per_block": 0.5}})
+    # 2000 blocks, 4000 PDM bytes loaded: 1.25 * 4000 + 0.5 * 2000
+    assert bench.ncu_traffic("cur", 2000, 4000.0) == 6000.0
+    assert bench.ncu_traffic("old", 2000, 4000.0) is None
+    assert bench.ncu_traffic("none", 2000, 4000.0) is None
 
 
 def test_precompute_alu_roofline_uses_the_record_of_the_current_code(monkeypatch):
