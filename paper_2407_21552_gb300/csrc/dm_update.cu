@@ -169,17 +169,22 @@ __device__ __forceinline__ void cp_async16(void* smem, const uint8_t* gmem)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Measurement aid: the combine functions add the bytes of PDM planes each thread loads to
 // *loads (a per-thread counter; null: not counted), and the kernel adds each warp's total
 // to the caller's device counter once, at its end (add_warp_count).
 
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // D' for `nvec` 16-byte chunks through cp.async: each thread streams its chunk of every
-// active plane into its own shared-memory slots, kAsyncBatch planes per group with two
+// active plane into its own shared-memory slots, kAsyncBatch planes per group with S
 // groups in flight (no registers held by the loads), and folds a group once it landed.
-// `stage` is this thread's [2][kAsyncBatch] slot array (stride `ld` uint4 between slots);
+// `stage` is this thread's [S][kAsyncBatch] slot array (stride `ld` uint4 between slots);
 // s_off holds the n plane offsets followed by kAsyncBatch copies of the first one, so a
 // last, partial batch reads plane 0 again (same bytes, no effect on the min).
 // A chunk whose minimum has reached 0 in every byte is final: its later batches are not
@@ -187,6 +192,7 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // leaves a minimum of 0 at 0.
 constexpr int kAsyncBatch = 8;
 
+template <int S>
 __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__ pdm,
                                                      const int64_t* s_off, int n, int64_t nvec,
                                                      int64_t t0, int64_t stride, uint4* stage,
@@ -199,43 +205,50 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
             __stcs(reinterpret_cast<uint4*>(out + (v << 4)), make_uint4(~0u, ~0u, ~0u, ~0u));
         return;
     }
-    // flattened sequence of (chunk, batch) steps; step i+1 is issued before step i is used
     int64_t v = t0;
-    int jb = 0;
-    auto issue = [&](int64_t vv, int b, int slot, bool load) {
-        const uint8_t* src = pdm + (vv << 4);
+    if (v >= nvec) return;
+    ByteMin16 acc;                                            // chunk v, batches before jb
+    acc.reset();
+    // the flattened sequence of (chunk, batch) steps; a step is issued S - 1 steps before
+    // it is folded, and loads nothing when the minimum of its chunk is already final
+    auto issue = [&](int64_t vv, int b, int slot) {
+        const bool load = vv < nvec && (vv != v || acc.nonzero());
         if (load) {
+            const uint8_t* src = pdm + (vv << 4);
 #pragma unroll
             for (int k = 0; k < kAsyncBatch; ++k)
                 cp_async16(stage + (slot * kAsyncBatch + k) * ld,
                            src + s_off[b * kAsyncBatch + k]);
+            if (loads) *loads += 16u * unsigned(min(kAsyncBatch, n - b * kAsyncBatch));
         }
         cp_async_commit();
-        if (loads && load) *loads += 16u * unsigned(min(kAsyncBatch, n - b * kAsyncBatch));
     };
-    if (v >= nvec) return;
-    issue(v, 0, 0, true);
-    int slot = 0;
-    ByteMin16 acc;
-    acc.reset();
+    int64_t iv = v;                                           // next step to issue
+    int ib = 0, islot = 0;
+    auto advance = [&](int64_t& vv, int& b) {
+        if (++b == nb) { b = 0; vv += stride; }
+    };
+#pragma unroll
+    for (int a = 0; a < S - 1; ++a) {
+        issue(iv, ib, islot);
+        advance(iv, ib);
+        islot = islot + 1 == S ? 0 : islot + 1;
+    }
+    int jb = 0, slot = 0;
     while (true) {
-        // next step (its chunk's minimum so far covers the batches before jb)
-        int64_t nv = v;
-        int njb = jb + 1;
-        if (njb == nb) { njb = 0; nv = v + stride; }
-        const bool more = nv < nvec;
-        if (more) issue(nv, njb, slot ^ 1, njb == 0 || acc.nonzero()); else cp_async_commit();
-        cp_async_wait1();                                     // step (v, jb) landed
+        issue(iv, ib, islot);
+        advance(iv, ib);
+        islot = islot + 1 == S ? 0 : islot + 1;
+        cp_async_wait_n<S - 1>();                             // step (v, jb) landed
 #pragma unroll
         for (int k = 0; k < kAsyncBatch; ++k) acc.fold(stage[(slot * kAsyncBatch + k) * ld]);
         if (jb == nb - 1) {
             __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc.value());
             acc.reset();
         }
-        if (!more) break;
-        v = nv;
-        jb = njb;
-        slot ^= 1;
+        advance(v, jb);
+        if (v >= nvec) break;
+        slot = slot + 1 == S ? 0 : slot + 1;
     }
     cp_async_wait0();
 }
@@ -244,9 +257,11 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
 // warp owns 256 consecutive chunks (4 KiB), lane l chunks base + 32 k + l for k < 8.
 // One step loads the warp's 4 KiB of one plane (8 cp.async per thread, each instruction
 // 512 contiguous bytes), so every DRAM burst of a step is 4 KiB of one plane; the 8
-// per-thread accumulators fold the planes and are stored once per tile.  As in the
-// per-chunk path, a chunk whose minimum is 0 in every byte loads no further plane.
+// per-thread accumulators fold the planes and are stored once per tile.  A step is issued
+// S - 1 steps before it is folded.  As in the per-chunk path, a chunk whose minimum is 0
+// in every byte loads no further plane.
 constexpr int kPM = 8;                                        // chunks per thread per tile
+template <int S>
 __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__ pdm,
                                                      const int64_t* s_off, int n, int64_t ntiles,
                                                      int64_t tile0, int64_t tstride, uint4* stage,
@@ -267,31 +282,41 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
                 __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), make_uint4(~0u, ~0u, ~0u, ~0u));
         return;
     }
-    ByteMin16 acc[kPM];
+    ByteMin16 acc[kPM];                                       // tile t, planes before p
 #pragma unroll
     for (int k = 0; k < kPM; ++k) acc[k].reset();
-    // fresh: the first plane of a tile (the accumulators still hold the previous tile)
-    auto issue = [&](int64_t tt, int p, int slot, bool fresh) {
-        const uint8_t* src = pdm + s_off[p];
-        unsigned issued = 0;
+    // a step of another tile than t loads every chunk (the accumulators hold tile t)
+    auto issue = [&](int64_t tt, int pp, int slot) {
+        if (tt < ntiles) {
+            const uint8_t* src = pdm + s_off[pp];
+            unsigned issued = 0;
 #pragma unroll
-        for (int k = 0; k < kPM; ++k)
-            if (fresh || acc[k].nonzero()) {
-                cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
-                ++issued;
-            }
+            for (int k = 0; k < kPM; ++k)
+                if (tt != t || acc[k].nonzero()) {
+                    cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
+                    ++issued;
+                }
+            if (loads) *loads += 16u * issued;
+        }
         cp_async_commit();
-        if (loads) *loads += 16u * issued;
     };
+    auto advance = [&](int64_t& tt, int& pp) {
+        if (++pp == n) { pp = 0; tt += tstride; }
+    };
+    int64_t it = t;                                           // next step to issue
+    int ip = 0, islot = 0;
+#pragma unroll
+    for (int a = 0; a < S - 1; ++a) {
+        issue(it, ip, islot);
+        advance(it, ip);
+        islot = islot + 1 == S ? 0 : islot + 1;
+    }
     int p = 0, slot = 0;
-    issue(t, 0, 0, true);
     while (true) {
-        int64_t nt = t;
-        int np = p + 1;
-        if (np == n) { np = 0; nt = t + tstride; }
-        const bool more = nt < ntiles;
-        if (more) issue(nt, np, slot ^ 1, np == 0); else cp_async_commit();
-        cp_async_wait1();
+        issue(it, ip, islot);
+        advance(it, ip);
+        islot = islot + 1 == S ? 0 : islot + 1;
+        cp_async_wait_n<S - 1>();                             // step (t, p) landed
 #pragma unroll
         for (int k = 0; k < kPM; ++k) acc[k].fold(stage[(slot * kPM + k) * ld]);
         if (p == n - 1) {
@@ -301,10 +326,9 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
                 acc[k].reset();
             }
         }
-        if (!more) break;
-        t = nt;
-        p = np;
-        slot ^= 1;
+        advance(t, p);
+        if (t >= ntiles) break;
+        slot = slot + 1 == S ? 0 : slot + 1;
     }
     cp_async_wait0();
 }
@@ -331,8 +355,8 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     unsigned loaded = 0;
     unsigned* lp = count ? &loaded : nullptr;
     if (vec_ok) {
-        combine_chunks_async(pdm, s_off, n, G >> 4, t0, stride, s_stage + threadIdx.x,
-                             kCombineThreads, out, lp);
+        combine_chunks_async<2>(pdm, s_off, n, G >> 4, t0, stride, s_stage + threadIdx.x,
+                                kCombineThreads, out, lp);
         done = (G >> 4) << 4;
     }
     // bytes not covered by whole aligned chunks
@@ -351,6 +375,11 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
 // publishes S (list, count, bit set) for callers that read it back.
 constexpr int kFusedThreads = 512;
 constexpr int kFusedMaxN = 8192;
+// plane loads in flight per thread: kFusedStages - 1 steps ahead of the fold (192 KiB of
+// staging for 3 stages; chunks whose minimum is 0 load nothing, so deeper staging keeps
+// more bytes in flight once many chunks are done)
+constexpr int kFusedStages = 3;
+static_assert(kPM == kAsyncBatch, "both paths use the same slots");
 
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
@@ -367,7 +396,7 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     __shared__ uint32_t s_bits[8];
     __shared__ uint16_t s_list[kMaxPartitions + kBatch];
     __shared__ int s_scan[9];
-    extern __shared__ uint4 s_stage[];                 // [2][kAsyncBatch][kFusedThreads]
+    extern __shared__ uint4 s_stage[];      // [kFusedStages][kAsyncBatch][kFusedThreads]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     pdl_wait();
     const int mine = order && tid < K ? int(order[tid]) : tid;     // this thread's plane
@@ -435,10 +464,11 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         if (ntiles < 2 * grid) ntiles = 0;
         else if (ntiles % grid != 0 && 4 * (ntiles % grid) < 3 * grid) ntiles -= ntiles % grid;
         if (ntiles > 0)
-            combine_tiles_planar(pdm, s_off, n, ntiles, blockIdx.x, grid, s_stage + tid,
-                                 kFusedThreads, out, warp, lane, kFusedThreads / 32, lp);
-        combine_chunks_async(pdm, s_off, n, nvec, ntiles * tile_chunks + t0, stride,
-                             s_stage + tid, kFusedThreads, out, lp);
+            combine_tiles_planar<kFusedStages>(pdm, s_off, n, ntiles, blockIdx.x, grid,
+                                               s_stage + tid, kFusedThreads, out, warp, lane,
+                                               kFusedThreads / 32, lp);
+        combine_chunks_async<kFusedStages>(pdm, s_off, n, nvec, ntiles * tile_chunks + t0,
+                                           stride, s_stage + tid, kFusedThreads, out, lp);
         done = nvec << 4;
     }
     for (int64_t i = done + t0; i < G; i += stride) {
@@ -477,9 +507,10 @@ k_index_level(uint8_t* __restrict__ pdm, int64_t plane, int64_t G, int prev_base
 // ---------------------------------------------------------------- plane order
 // Zero bytes of each plane on a fixed sample (kCoverSamples 16-byte chunks at an even
 // stride, or bytes where the plane is not 16-byte aligned): one CTA per plane, no atomics,
-// so the count is the same on every run.
-constexpr int kCoverSamples = 16384;
+// so the count is the same on every run; a thread issues its loads 8 at a time.
+constexpr int kCoverSamples = 8192;
 constexpr int kOrderThreads = 256;
+constexpr int kCoverPer = kCoverSamples / kOrderThreads;
 static_assert(kMaxPartitions <= kOrderThreads, "one thread per partition ranks the planes");
 
 struct PlaneOrderBatch {
@@ -504,10 +535,18 @@ k_plane_cover(const __grid_constant__ PlaneOrderBatch B)
         const int64_t ns = nvec < kCoverSamples ? nvec : kCoverSamples;
         const int64_t step = nvec / ns;
         const uint4* v4 = reinterpret_cast<const uint4*>(src);
-        for (int64_t j = tid; j < ns; j += kOrderThreads) {
-            const uint4 v = __ldcs(v4 + j * step);
-            z += __popc(__vcmpeq4(v.x, 0u)) + __popc(__vcmpeq4(v.y, 0u)) +
-                 __popc(__vcmpeq4(v.z, 0u)) + __popc(__vcmpeq4(v.w, 0u));
+        constexpr int kRound = 8;                              // loads in flight
+        for (int r0 = 0; r0 < kCoverPer; r0 += kRound) {
+            uint4 v[kRound];
+#pragma unroll
+            for (int r = 0; r < kRound; ++r) {
+                const int64_t j = int64_t(r0 + r) * kOrderThreads + tid;
+                v[r] = j < ns ? __ldcs(v4 + j * step) : make_uint4(1u, 1u, 1u, 1u);
+            }
+#pragma unroll
+            for (int r = 0; r < kRound; ++r)
+                z += __popc(__vcmpeq4(v[r].x, 0u)) + __popc(__vcmpeq4(v[r].y, 0u)) +
+                     __popc(__vcmpeq4(v[r].z, 0u)) + __popc(__vcmpeq4(v[r].w, 0u));
         }
     } else {
         const int64_t ns = it.G < 16 * kCoverSamples ? it.G : 16 * kCoverSamples;
@@ -580,7 +619,8 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
                        ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (plane % 16 == 0);
     const int64_t work = vec_ok ? (G >> 4) : G;
     const int64_t want = (work + kFusedThreads - 1) / kFusedThreads;
-    const size_t smem = vec_ok ? size_t(2) * kAsyncBatch * kFusedThreads * sizeof(uint4) : 0;
+    const size_t smem =
+        vec_ok ? size_t(kFusedStages) * kAsyncBatch * kFusedThreads * sizeof(uint4) : 0;
     const int64_t cap = int64_t(num_sms > 0 ? num_sms : 152);  // one 512-thread CTA per SM
     const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
     cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
