@@ -333,6 +333,8 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
     cp_async_wait0();
 }
 
+// COUNT: the measurement build, which adds the PDM bytes it loads to *count.
+template <bool COUNT>
 __global__ void __launch_bounds__(kCombineThreads)
 k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
           const uint16_t* __restrict__ act, const int32_t* __restrict__ nact,
@@ -353,7 +355,7 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     const int64_t t0 = int64_t(blockIdx.x) * kCombineThreads + threadIdx.x;
     int64_t done = 0;
     unsigned loaded = 0;
-    unsigned* lp = count ? &loaded : nullptr;
+    unsigned* lp = COUNT ? &loaded : nullptr;
     if (vec_ok) {
         combine_chunks_async<2>(pdm, s_off, n, G >> 4, t0, stride, s_stage + threadIdx.x,
                                 kCombineThreads, out, lp);
@@ -364,9 +366,9 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         unsigned acc = 255;
         for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
         out[i] = uint8_t(acc);
-        loaded += unsigned(n);
+        if (COUNT) loaded += unsigned(n);
     }
-    if (count) add_warp_count(count, loaded);
+    if (COUNT) add_warp_count(count, loaded);
 }
 
 // Step 1 and step 2 in one launch (TFs with N <= kFusedMaxN): every CTA derives S from
@@ -375,12 +377,14 @@ k_combine(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
 // publishes S (list, count, bit set) for callers that read it back.
 constexpr int kFusedThreads = 512;
 constexpr int kFusedMaxN = 8192;
-// plane loads in flight per thread: kFusedStages - 1 steps ahead of the fold (192 KiB of
-// staging for 3 stages; chunks whose minimum is 0 load nothing, so deeper staging keeps
-// more bytes in flight once many chunks are done)
-constexpr int kFusedStages = 3;
+// plane loads in flight per thread: kFusedStages - 1 steps ahead of the fold (128 KiB of
+// staging for 2 stages; 3 stages, 192 KiB, measured no faster on the large map and slower
+// on the smaller ones)
+constexpr int kFusedStages = 2;
 static_assert(kPM == kAsyncBatch, "both paths use the same slots");
 
+// COUNT: the measurement build, which adds the PDM bytes it loads to *count.
+template <bool COUNT>
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
                const float* __restrict__ tf, int N, int K, int J, Borders bd, int uniform,
@@ -451,8 +455,8 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
     const int64_t stride = int64_t(gridDim.x) * kFusedThreads;
     const int64_t t0 = int64_t(blockIdx.x) * kFusedThreads + tid;
     int64_t done = 0;
-    unsigned loaded = 0;                                       // plane bytes (count only)
-    unsigned* lp = count ? &loaded : nullptr;
+    unsigned loaded = 0;                                       // plane bytes (COUNT only)
+    unsigned* lp = COUNT ? &loaded : nullptr;
     if (vec_ok) {
         // Large maps: whole plane-major tiles while every CTA gets at least two and they
         // spread evenly (all of them when the last round fills three quarters of the CTAs,
@@ -475,9 +479,9 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         unsigned acc = 255;
         for (int j = 0; j < n; ++j) acc = min(acc, unsigned(pdm[s_off[j] + i]));
         out[i] = uint8_t(acc);
-        loaded += unsigned(n);
+        if (COUNT) loaded += unsigned(n);
     }
-    if (count) add_warp_count(count, loaded);
+    if (COUNT) add_warp_count(count, loaded);
 }
 
 // One level of the partition-range index: plane (k, i) = min(plane (k-1, i),
@@ -623,11 +627,12 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
         vec_ok ? size_t(kFusedStages) * kAsyncBatch * kFusedThreads * sizeof(uint4) : 0;
     const int64_t cap = int64_t(num_sms > 0 ? num_sms : 152);  // one 512-thread CTA per SM
     const int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
-    cudaError_t e = ensure_dynamic_smem<k_update_fused>(int(smem));
+    auto kern = count ? k_update_fused<true> : k_update_fused<false>;
+    cudaError_t e = count ? ensure_dynamic_smem<k_update_fused<true>>(int(smem))
+                          : ensure_dynamic_smem<k_update_fused<false>>(int(smem));
     if (e != cudaSuccess) return e;
-    k_update_fused<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform,
-                                                      order, act, nact, smask, smask_out, out,
-                                                      vec_ok, count);
+    kern<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform, order, act,
+                                            nact, smask, smask_out, out, vec_ok, count);
     return cudaGetLastError();
 }
 
@@ -658,10 +663,12 @@ cudaError_t launch_combine(const uint8_t* pdm, int64_t plane, int64_t G, const u
     const size_t smem = vec_ok ? size_t(2) * kAsyncBatch * kCombineThreads * sizeof(uint4) : 0;
     int64_t cap = int64_t(num_sms > 0 ? num_sms : 152) * 3;   // 3 resident CTAs per SM
     int blocks = int(want < cap ? (want > 0 ? want : 1) : cap);
-    cudaError_t e = ensure_dynamic_smem<k_combine>(int(smem));
+    cudaError_t e = count ? ensure_dynamic_smem<k_combine<true>>(int(smem))
+                          : ensure_dynamic_smem<k_combine<false>>(int(smem));
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_combine, dim3(blocks), dim3(kCombineThreads), smem, s, pdm, plane, G,
-                      act, nact, out, vec_ok, count);
+    return launch_pdl(count ? k_combine<true> : k_combine<false>, dim3(blocks),
+                      dim3(kCombineThreads), smem, s, pdm, plane, G, act, nact, out, vec_ok,
+                      count);
 }
 
 cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t s)
