@@ -187,9 +187,8 @@ __device__ __forceinline__ void cp_async_wait_n()
 // `stage` is this thread's [S][kAsyncBatch] slot array (stride `ld` uint4 between slots);
 // s_off holds the n plane offsets followed by kAsyncBatch copies of the first one, so a
 // last, partial batch reads plane 0 again (same bytes, no effect on the min).
-// A chunk whose minimum has reached 0 in every byte is final: its later batches are not
-// loaded.  Their slots are folded all the same, with whatever bytes they hold, which
-// leaves a minimum of 0 at 0.
+// A chunk whose minimum has reached 0 in every byte is final: its later batches are
+// neither loaded nor folded.
 constexpr int kAsyncBatch = 8;
 
 template <int S>
@@ -209,10 +208,11 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
     if (v >= nvec) return;
     ByteMin16 acc;                                            // chunk v, batches before jb
     acc.reset();
+    bool live = true;                                         // acc may still fall
     // the flattened sequence of (chunk, batch) steps; a step is issued S - 1 steps before
     // it is folded, and loads nothing when the minimum of its chunk is already final
     auto issue = [&](int64_t vv, int b, int slot) {
-        const bool load = vv < nvec && (vv != v || acc.nonzero());
+        const bool load = vv < nvec && (vv != v || live);
         if (load) {
             const uint8_t* src = pdm + (vv << 4);
 #pragma unroll
@@ -240,11 +240,16 @@ __device__ __forceinline__ void combine_chunks_async(const uint8_t* __restrict__
         advance(iv, ib);
         islot = islot + 1 == S ? 0 : islot + 1;
         cp_async_wait_n<S - 1>();                             // step (v, jb) landed
+        if (live) {
 #pragma unroll
-        for (int k = 0; k < kAsyncBatch; ++k) acc.fold(stage[(slot * kAsyncBatch + k) * ld]);
+            for (int k = 0; k < kAsyncBatch; ++k)
+                acc.fold(stage[(slot * kAsyncBatch + k) * ld]);
+            live = acc.nonzero();
+        }
         if (jb == nb - 1) {
             __stcs(reinterpret_cast<uint4*>(out + (v << 4)), acc.value());
             acc.reset();
+            live = true;
         }
         advance(v, jb);
         if (v >= nvec) break;
@@ -285,14 +290,15 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
     ByteMin16 acc[kPM];                                       // tile t, planes before p
 #pragma unroll
     for (int k = 0; k < kPM; ++k) acc[k].reset();
+    unsigned live = (1u << kPM) - 1;                          // bit k: acc[k] may still fall
     // a step of another tile than t loads every chunk (the accumulators hold tile t)
     auto issue = [&](int64_t tt, int pp, int slot) {
-        if (tt < ntiles) {
+        if (tt < ntiles && (tt != t || live != 0u)) {
             const uint8_t* src = pdm + s_off[pp];
             unsigned issued = 0;
 #pragma unroll
             for (int k = 0; k < kPM; ++k)
-                if (tt != t || acc[k].nonzero()) {
+                if (tt != t || ((live >> k) & 1u)) {
                     cp_async16(stage + (slot * kPM + k) * ld, src + (chunk_of(tt, k) << 4));
                     ++issued;
                 }
@@ -317,14 +323,21 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
         advance(it, ip);
         islot = islot + 1 == S ? 0 : islot + 1;
         cp_async_wait_n<S - 1>();                             // step (t, p) landed
+        if (live != 0u) {
 #pragma unroll
-        for (int k = 0; k < kPM; ++k) acc[k].fold(stage[(slot * kPM + k) * ld]);
+            for (int k = 0; k < kPM; ++k)
+                if ((live >> k) & 1u) {
+                    acc[k].fold(stage[(slot * kPM + k) * ld]);
+                    if (!acc[k].nonzero()) live &= ~(1u << k);
+                }
+        }
         if (p == n - 1) {
 #pragma unroll
             for (int k = 0; k < kPM; ++k) {
                 __stcs(reinterpret_cast<uint4*>(out) + chunk_of(t, k), acc[k].value());
                 acc[k].reset();
             }
+            live = (1u << kPM) - 1;
         }
         advance(t, p);
         if (t >= ntiles) break;
