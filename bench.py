@@ -68,9 +68,10 @@ NCU_PRECOMPUTE_INST = {
 
 
 def precompute_kernel_sources(csrc):
-    """The precompute kernels' files and the headers they include."""
-    return [os.path.join(csrc, f) for f in ("dm_footprint.cu", "dm_dt.cu", "dm_internal.cuh",
-                                            "dm_build_batch.cuh")]
+    """The precompute kernels' files (the plane order and region bounds are in the update's
+    file) and the headers they include."""
+    return [os.path.join(csrc, f) for f in ("dm_footprint.cu", "dm_dt.cu", "dm_update.cu",
+                                            "dm_internal.cuh", "dm_build_batch.cuh")]
 
 
 def precompute_alu(workload, pre_ms, clk, sms):
@@ -554,7 +555,7 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
                      "mean_launch_us": float(upd_a.mean() * 1e3)},
         "clocks": clk,
         "e2e": e2e_res,
-        "gpu_launches": steps * (7 + E * ((1 if fused else 2) + 4)),
+        "gpu_launches": steps * (8 + E * ((1 if fused else 2) + 4)),
     }
     if idx:
         idx["speedup_vs_full_recompute_p50"] = p50f / idx["p50_ms"]

@@ -25,7 +25,8 @@ struct dm_ctx {
     int planes;                     // planes in the pdm buffer
     int num_sms;
     // scratch layout (byte offsets)
-    size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_cover, off_order, off_tf, off_out;
+    size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_cover, off_order, off_rmin, off_tf,
+        off_out;
     void* d_mask;
     void* d_pdm;
     void* d_minmax;
@@ -166,6 +167,7 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     x->off_smask = o; o = align_up(o + 64, 256);
     x->off_cover = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 4, 256);
     x->off_order = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 2, 256);
+    x->off_rmin = o;  o = align_up(o + size_t(dmk::num_regions(g.G)) * size_t(K), 256);
     x->off_tf = o;    o = align_up(o + size_t(N) * 16, 256);
     x->off_out = o;   o = align_up(o + size_t(g.G), 256);
     s.scratch_bytes = o;
@@ -220,6 +222,7 @@ static dmk::PlaneOrderItem plane_order_item(const dm_ctx* c)
     it.K = c->cfg.num_partitions;
     it.cover = reinterpret_cast<uint32_t*>(scratch + c->off_cover);
     it.order = reinterpret_cast<uint16_t*>(scratch + c->off_order);
+    it.rmin = scratch + c->off_rmin;
     return it;
 }
 
@@ -227,6 +230,11 @@ static unsigned long long* prof_count(const dm_ctx* c)
 {
     static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "64-bit counter");
     return reinterpret_cast<unsigned long long*>(c->prof_bytes);
+}
+
+static const uint8_t* region_bounds(const dm_ctx* c)
+{
+    return static_cast<const uint8_t*>(c->d_scratch) + c->off_rmin;
 }
 
 static const uint16_t* plane_order(const dm_ctx* c)
@@ -420,7 +428,8 @@ static dm_status update_into(dm_ctx* ctx, const float* d_tf, uint8_t* d_out,
         cudaError_t e = dmk::launch_update_fused(static_cast<const uint8_t*>(ctx->d_pdm),
                                                  ctx->geo.plane, ctx->geo.G, d_tf, N, K,
                                                  ctx->J, ctx->borders, ctx->uniform_borders ? 1 : 0,
-                                                 plane_order(ctx), act, nact, smask,
+                                                 plane_order(ctx), region_bounds(ctx), act,
+                                                 nact, smask,
                                                  d_active_mask_out, d_out, ctx->num_sms,
                                                  prof_count(ctx), s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "update");

@@ -43,11 +43,13 @@ cudaError_t launch_pom_build_batch(const BuildItem* items, int n, cudaStream_t s
 cudaError_t launch_xpass_mask_batch(const BuildItem* items, int n, cudaStream_t s);
 cudaError_t launch_line_pass_batch(const BuildItem* items, int n, int axis, cudaStream_t s);
 
-// ---------------------------------------------------------------- plane order
-// The order in which the combine reads a context's active planes: descending count of zero
-// bytes (occupied blocks) on a fixed sample of each plane, ties by partition index.  The
-// combine stops loading a 16-byte chunk once its minimum is 0 in every byte, so the
-// most-covered planes first read the fewest bytes; D' does not depend on the order.
+// ---------------------------------------------------------------- plane order, bounds
+// What the combine needs to read few bytes (D' does not depend on either):
+//  * the plane order: descending count of zero bytes (occupied blocks) on a fixed sample of
+//    each plane, ties by partition index;
+//  * the region bounds: for each region of kRegionBlocks consecutive blocks and each plane,
+//    the plane's minimum over the region.  No byte of D' in a region can be lowered by a
+//    plane whose regional minimum is at least the region's current maximum.
 struct PlaneOrderItem {
     const uint8_t* pdm;                // K planes, `plane` bytes apart
     int64_t plane;
@@ -55,10 +57,12 @@ struct PlaneOrderItem {
     int K;
     uint32_t* cover;                   // [K] sampled zero-byte counts (device, written)
     uint16_t* order;                   // [K] partitions, most covered first (device, written)
+    uint8_t* rmin;                     // [regions(G)][K] regional minima (device, written)
 };
 
-// Two launches over up to kMaxBuildBatch contexts: one CTA per plane counts, one CTA per
-// context ranks.  Runs after the context's z pass on the same stream.
+// Three launches over up to kMaxBuildBatch contexts: one CTA per plane counts, one CTA per
+// context ranks, one warp per (region, plane) takes the minimum.  Runs after the context's
+// z pass on the same stream.
 cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t s);
 
 }  // namespace dmk

@@ -94,6 +94,20 @@ __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
     return d;
 }
 
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Byte minimum of 16 bytes.
+__device__ __forceinline__ unsigned bytemin16(const uint4& v)
+{
+    const unsigned w = __vminu4(__vminu4(v.x, v.y), __vminu4(v.z, v.w));
+    return min(min(w & 0xFFu, (w >> 8) & 0xFFu), min((w >> 16) & 0xFFu, w >> 24));
+}
+
 struct ByteMin16 {                                   // running byte minimum of 16 bytes
     uint32_t e[4], o[4];
     __device__ __forceinline__ void reset()
@@ -119,7 +133,24 @@ struct ByteMin16 {                                   // running byte minimum of 
     {
         return ((e[0] | e[1] | e[2] | e[3]) | (o[0] | o[1] | o[2] | o[3])) != 0u;
     }
+    // the largest of the 16 minima
+    __device__ __forceinline__ uint32_t max_byte() const
+    {
+        const uint32_t a = max_u16x2(max_u16x2(e[0], e[1]), max_u16x2(e[2], e[3]));
+        const uint32_t b = max_u16x2(max_u16x2(o[0], o[1]), max_u16x2(o[2], o[3])) >> 8;
+        const uint32_t c = max_u16x2(a, b & 0x00FF00FFu);
+        return max(c & 0xFFFFu, c >> 16);
+    }
 };
+
+// Regions of the combine's bound (Eq. 1 read region by region): kRegionBlocks consecutive
+// blocks of a map, 256 chunks of 16 bytes, one warp's 8 chunks per lane.
+constexpr int64_t kRegionBlocks = 4096;
+constexpr int kRegionChunks = 256;
+__host__ __device__ inline int64_t num_regions(int64_t G)
+{
+    return (G + kRegionBlocks - 1) / kRegionBlocks;
+}
 
 // Adds a warp's sum of v to *count (one atomic, lane 0).  Every lane of the warp must call
 // it at the same point (the update kernels do so at their end).
@@ -255,13 +286,16 @@ cudaError_t launch_active_set(const float* tf, int N, int K, int J, const Border
 // Step 1 and Eq. 1 in one launch: each CTA derives S from the TF itself (N <= 8192).
 bool update_fused_ok(int N);
 // `uniform`: the borders are the default floor(p N / K), which the kernel computes instead of
-// indexing the parameter array per thread.  `order` as in launch_active_set.  `count`: a
-// device counter to which the kernel adds the bytes of PDM planes it loads (null: none).
+// indexing the parameter array per thread.  `order` as in launch_active_set; `rmin`: the
+// context's region bounds [regions(G)][K] (null: none), which the plain path (J < 0) reads
+// region by region.  `count`: a device counter to which the kernel adds the bytes of PDM
+// planes it loads (null: none).
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
                                 int N, int K, int J, const Borders& bd, int uniform,
-                                const uint16_t* order, uint16_t* act, int32_t* nact,
-                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                unsigned long long* count, cudaStream_t s);
+                                const uint16_t* order, const uint8_t* rmin, uint16_t* act,
+                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                                uint8_t* out, int num_sms, unsigned long long* count,
+                                cudaStream_t s);
 
 // D' = byte-wise min over the active planes (Eq. 1); 255 when S is empty.  `count` as in
 // launch_update_fused.

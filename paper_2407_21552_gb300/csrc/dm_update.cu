@@ -346,6 +346,105 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
     cp_async_wait0();
 }
 
+// D' region by region, without the range index: warp w of the grid (w = warp * gridDim.x
+// + block, so that small maps spread over every SM) takes regions w, w + warps, ...  For a
+// region it lists the active planes (the CTA's list, in the plane order) in ascending order
+// of their minimum over the region, ties kept in list order, and reads them one plane per
+// step, lane l loading chunks r * 256 + 32 k + l (k < 8) of the plane: 512 contiguous bytes
+// per instruction.  A chunk whose minimum is 0 loads no further plane, and the region stops
+// as soon as the next plane's regional minimum is at least the largest minimum of the
+// region so far: that plane, and every later one, is at least every byte of D' there.
+// The first plane is folded before the second is issued (a region that one plane settles
+// reads one plane); after that a plane is issued while the one before it is folded, and
+// the bound it is checked against is the region's maximum one plane earlier.
+// Each warp keeps its sorted list in w_list / w_bnd (kMaxPartitions entries) and uses
+// w_key as scratch; `stage` is the thread's [2][kPM] slot array.
+__device__ __forceinline__ void combine_regions(const uint8_t* __restrict__ pdm, int64_t plane,
+                                                const uint16_t* s_list, int n, int K,
+                                                const uint8_t* __restrict__ rmin, int64_t nvec,
+                                                int64_t nreg, uint4* stage, int ld,
+                                                uint8_t* __restrict__ out, uint16_t* w_list,
+                                                uint8_t* w_bnd, uint32_t* w_key, int lane,
+                                                int64_t w0, int64_t warps, unsigned* loads)
+{
+    for (int64_t r = w0; r < nreg; r += warps) {
+        // ---- the region's plane list, by regional minimum
+        for (int j = lane; j < n; j += 32) {
+            const int p = s_list[j];
+            w_key[j] = (uint32_t(rmin[r * K + p]) << 16) | uint32_t(j);
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            const uint32_t key = w_key[j];
+            int rank = 0;
+            for (int q = 0; q < n; ++q) rank += w_key[q] < key ? 1 : 0;
+            w_list[rank] = s_list[j];
+            w_bnd[rank] = uint8_t(key >> 16);
+        }
+        __syncwarp();
+        // ---- stream the planes
+        const int64_t c0 = r * kRegionChunks + lane;
+        unsigned live = 0;                                    // bit k: chunk k may still fall
+#pragma unroll
+        for (int k = 0; k < kPM; ++k)
+            if (c0 + 32 * k < nvec) live |= 1u << k;
+        const unsigned valid = live;
+        ByteMin16 acc[kPM];
+#pragma unroll
+        for (int k = 0; k < kPM; ++k) acc[k].reset();
+        auto issue = [&](int q, int slot) {
+            const uint8_t* src = pdm + int64_t(w_list[q]) * plane;
+            unsigned issued = 0;
+#pragma unroll
+            for (int k = 0; k < kPM; ++k)
+                if ((live >> k) & 1u) {
+                    cp_async16(stage + (slot * kPM + k) * ld, src + ((c0 + 32 * k) << 4));
+                    ++issued;
+                }
+            cp_async_commit();
+            if (loads) *loads += 16u * issued;
+        };
+        unsigned wmax = 255u;                                 // largest minimum so far
+        auto fold = [&](int slot) {
+            unsigned tmax = 0;
+#pragma unroll
+            for (int k = 0; k < kPM; ++k) {
+                if ((live >> k) & 1u) {
+                    acc[k].fold(stage[(slot * kPM + k) * ld]);
+                    const unsigned mk = acc[k].max_byte();
+                    if (mk == 0u) live &= ~(1u << k);
+                    tmax = max(tmax, mk);
+                }
+            }
+            wmax = __reduce_max_sync(0xFFFFFFFFu, tmax);
+        };
+        if (n > 0 && w_bnd[0] < wmax) {                       // warp-uniform from here on
+            // the first plane alone: the region's minima after it decide the second
+            issue(0, 0);
+            cp_async_wait_n<0>();
+            fold(0);
+            int q = 1, slot = 1;
+            bool go = q < n && w_bnd[q] < wmax;
+            if (go) issue(q, slot);
+            while (go) {                                      // then one plane ahead
+                const bool next = q + 1 < n && w_bnd[q + 1] < wmax;
+                if (next) issue(q + 1, slot ^ 1); else cp_async_commit();
+                cp_async_wait_n<1>();                         // plane q landed
+                fold(slot);
+                go = next;
+                ++q;
+                slot ^= 1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPM; ++k)
+            if ((valid >> k) & 1u)
+                __stcs(reinterpret_cast<uint4*>(out) + c0 + 32 * k, acc[k].value());
+        __syncwarp();                                         // w_key / w_list are reused
+    }
+    cp_async_wait0();
+}
+
 // COUNT: the measurement build, which adds the PDM bytes it loads to *count.
 template <bool COUNT>
 __global__ void __launch_bounds__(kCombineThreads)
@@ -401,14 +500,18 @@ template <bool COUNT>
 __global__ void __launch_bounds__(kFusedThreads)
 k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
                const float* __restrict__ tf, int N, int K, int J, Borders bd, int uniform,
-               const uint16_t* __restrict__ order, uint16_t* __restrict__ act,
-               int32_t* __restrict__ nact,
+               const uint16_t* __restrict__ order, const uint8_t* __restrict__ rmin,
+               uint16_t* __restrict__ act, int32_t* __restrict__ nact,
                uint64_t* __restrict__ smask, uint64_t* __restrict__ smask_out,
                uint8_t* __restrict__ out, int vec_ok, unsigned long long* __restrict__ count)
 {
     constexpr int kBatch = 8;
     constexpr int kPer = kFusedMaxN / kFusedThreads;          // alphas per thread (max)
+    constexpr int kWarps = kFusedThreads / 32;
     __shared__ uint32_t s_vis[kFusedMaxN / 32];
+    __shared__ uint32_t s_wkey[kWarps][kMaxPartitions];       // per warp: region plan
+    __shared__ uint16_t s_wlist[kWarps][kMaxPartitions];
+    __shared__ uint8_t s_wbnd[kWarps][kMaxPartitions];
     __shared__ int64_t s_off[kMaxPartitions + kBatch];
     __shared__ uint32_t s_bits[8];
     __shared__ uint16_t s_list[kMaxPartitions + kBatch];
@@ -475,17 +578,28 @@ k_update_fused(const uint8_t* __restrict__ pdm, int64_t plane, int64_t G,
         // spread evenly (all of them when the last round fills three quarters of the CTAs,
         // else a multiple of the grid); every other chunk through the per-chunk path.
         const int64_t nvec = G >> 4;
-        const int64_t tile_chunks = int64_t(kFusedThreads) * kPM;
-        const int64_t grid = gridDim.x;
-        int64_t ntiles = nvec / tile_chunks;
-        if (ntiles < 2 * grid) ntiles = 0;
-        else if (ntiles % grid != 0 && 4 * (ntiles % grid) < 3 * grid) ntiles -= ntiles % grid;
-        if (ntiles > 0)
-            combine_tiles_planar<kFusedStages>(pdm, s_off, n, ntiles, blockIdx.x, grid,
-                                               s_stage + tid, kFusedThreads, out, warp, lane,
-                                               kFusedThreads / 32, lp);
-        combine_chunks_async<kFusedStages>(pdm, s_off, n, nvec, ntiles * tile_chunks + t0,
-                                           stride, s_stage + tid, kFusedThreads, out, lp);
+        if (J < 0 && rmin && 2 * num_regions(G) >= int64_t(kWarps) * gridDim.x) {
+            // the plain planes with their region bounds, region by region, when there are
+            // regions for at least half of the warps (a smaller map is bound by the latency
+            // of its plane steps, which the per-chunk path overlaps 8 planes at a time)
+            combine_regions(pdm, plane, s_list, n, K, rmin, nvec, num_regions(G),
+                            s_stage + tid, kFusedThreads, out, s_wlist[warp], s_wbnd[warp],
+                            s_wkey[warp], lane, int64_t(warp) * gridDim.x + blockIdx.x,
+                            int64_t(kWarps) * gridDim.x, lp);
+        } else {
+            const int64_t tile_chunks = int64_t(kFusedThreads) * kPM;
+            const int64_t grid = gridDim.x;
+            int64_t ntiles = nvec / tile_chunks;
+            if (ntiles < 2 * grid) ntiles = 0;
+            else if (ntiles % grid != 0 && 4 * (ntiles % grid) < 3 * grid)
+                ntiles -= ntiles % grid;
+            if (ntiles > 0)
+                combine_tiles_planar<kFusedStages>(pdm, s_off, n, ntiles, blockIdx.x, grid,
+                                                   s_stage + tid, kFusedThreads, out, warp,
+                                                   lane, kWarps, lp);
+            combine_chunks_async<kFusedStages>(pdm, s_off, n, nvec, ntiles * tile_chunks + t0,
+                                               stride, s_stage + tid, kFusedThreads, out, lp);
+        }
         done = nvec << 4;
     }
     for (int64_t i = done + t0; i < G; i += stride) {
@@ -533,8 +647,13 @@ static_assert(kMaxPartitions <= kOrderThreads, "one thread per partition ranks t
 struct PlaneOrderBatch {
     int n;
     int start[kMaxBuildBatch + 1];             // first CTA (plane) of each context
+    int rstart[kMaxBuildBatch + 1];            // first CTA of each context's region minima
     PlaneOrderItem it[kMaxBuildBatch];
 };
+
+constexpr int kRminWarps = 8;                  // (region, plane) pairs per CTA
+
+
 
 __global__ void __launch_bounds__(kOrderThreads)
 k_plane_cover(const __grid_constant__ PlaneOrderBatch B)
@@ -603,6 +722,41 @@ k_plane_order(const __grid_constant__ PlaneOrderBatch B)
     }
 }
 
+// The minimum of plane p over region r: one warp per (region, plane), plane-major so that
+// neighbouring warps read neighbouring regions; 16-byte loads where the plane is aligned,
+// the bytes past the last whole chunk one by one.
+__global__ void __launch_bounds__(kRminWarps * 32)
+k_region_min(const __grid_constant__ PlaneOrderBatch B)
+{
+    const int i = batch_item_of(B.rstart, B.n, int(blockIdx.x));
+    const PlaneOrderItem& it = B.it[i];
+    const int lane = threadIdx.x & 31;
+    const int64_t nreg = num_regions(it.G);
+    const int64_t u = int64_t(int(blockIdx.x) - B.rstart[i]) * kRminWarps + (threadIdx.x >> 5);
+    pdl_wait();
+    if (u >= nreg * it.K) return;                            // warp-uniform
+    const int p = int(u / nreg);
+    const int64_t r = u - int64_t(p) * nreg;
+    const uint8_t* src = it.pdm + int64_t(p) * it.plane;
+    const int64_t b0 = r * kRegionBlocks;
+    const int64_t b1 = b0 + kRegionBlocks < it.G ? b0 + kRegionBlocks : it.G;
+    unsigned m = 255u;
+    int64_t done = b0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int64_t c0 = b0 >> 4, c1 = b1 >> 4;           // b0 is a multiple of 16
+        const uint4* v4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+        for (int k = 0; k < kRegionChunks / 32; ++k) {
+            const int64_t c = c0 + k * 32 + lane;
+            if (c < c1) m = min(m, bytemin16(__ldcs(v4 + c)));
+        }
+        done = c1 << 4;
+    }
+    for (int64_t b = done + lane; b < b1; b += 32) m = min(m, unsigned(src[b]));
+    m = __reduce_min_sync(0xFFFFFFFFu, m);
+    if (lane == 0) it.rmin[r * it.K + p] = uint8_t(m);
+}
+
 }  // namespace
 
 cudaError_t launch_build_index(uint8_t* pdm, int64_t plane, int64_t G, int K, cudaStream_t s)
@@ -627,9 +781,10 @@ bool update_fused_ok(int N) { return N <= kFusedMaxN; }
 
 cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, const float* tf,
                                 int N, int K, int J, const Borders& bd, int uniform,
-                                const uint16_t* order, uint16_t* act, int32_t* nact,
-                                uint64_t* smask, uint64_t* smask_out, uint8_t* out, int num_sms,
-                                unsigned long long* count, cudaStream_t s)
+                                const uint16_t* order, const uint8_t* rmin, uint16_t* act,
+                                int32_t* nact, uint64_t* smask, uint64_t* smask_out,
+                                uint8_t* out, int num_sms, unsigned long long* count,
+                                cudaStream_t s)
 {
     if (N > kFusedMaxN) return cudaErrorInvalidValue;
     const int vec_ok = ((reinterpret_cast<uintptr_t>(pdm) & 15) == 0) &&
@@ -644,8 +799,9 @@ cudaError_t launch_update_fused(const uint8_t* pdm, int64_t plane, int64_t G, co
     cudaError_t e = count ? ensure_dynamic_smem<k_update_fused<true>>(int(smem))
                           : ensure_dynamic_smem<k_update_fused<false>>(int(smem));
     if (e != cudaSuccess) return e;
-    kern<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform, order, act,
-                                            nact, smask, smask_out, out, vec_ok, count);
+    kern<<<blocks, kFusedThreads, smem, s>>>(pdm, plane, G, tf, N, K, J, bd, uniform, order,
+                                            rmin, act, nact, smask, smask_out, out, vec_ok,
+                                            count);
     return cudaGetLastError();
 }
 
@@ -698,9 +854,18 @@ cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t 
         ctas += items[k].K;
     }
     B.start[n] = ctas;
+    int64_t rctas = 0;
+    for (int k = 0; k < n; ++k) {
+        B.rstart[k] = int(rctas);
+        rctas += (num_regions(items[k].G) * items[k].K + kRminWarps - 1) / kRminWarps;
+        if (rctas > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+    }
+    B.rstart[n] = int(rctas);
     cudaError_t e = launch_pdl(k_plane_cover, dim3(unsigned(ctas)), dim3(kOrderThreads), 0, s, B);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_plane_order, dim3(unsigned(n)), dim3(kOrderThreads), 0, s, B);
+    e = launch_pdl(k_plane_order, dim3(unsigned(n)), dim3(kOrderThreads), 0, s, B);
+    if (e != cudaSuccess || rctas == 0) return e;
+    return launch_pdl(k_region_min, dim3(unsigned(rctas)), dim3(kRminWarps * 32), 0, s, B);
 }
 
 }  // namespace dmk

@@ -1,18 +1,24 @@
-"""The update's plane order and its stop at 0 (Eq. 1 read most-covered plane first; a
-16-byte chunk whose minimum is 0 in every byte loads no further plane), through the C ABI.
+"""The update's reading schedule (Eq. 1 without the range index), through the C ABI.
+
+Maps of about 5 M blocks or more are read region by region (4096 blocks): the active
+planes in ascending order of their minimum over the region (ties in the plane order, most
+zero bytes first), a 16-byte chunk whose minimum is 0 in every byte loading no further
+plane, and the region stopping once the next plane's regional minimum is at least the
+largest minimum of the region.  Smaller maps are read chunk by chunk, 8 planes per batch
+in the plane order, with the same stop at 0.
 
 D' must not change: every case is compared with the oracle or with the value the
 definition fixes.  The plane bytes the combine loads (dm_set_profile_counter) are pinned
 where the schedule fixes them:
-  * one active partition: every chunk of its plane is loaded once, so exactly G bytes;
-  * a volume whose every block lies in the LAST partition, all partitions active: that
-    plane is all 0 and is ranked first, so the per-chunk path loads only the batches of 8
-    planes that are in flight before the first batch is folded (two or three, by the
-    pipeline depth) and no more: at most 24 G bytes for K = 64, where ascending order
-    would load all 64 G;
-  * the same on a map large enough for the plane-major tiles: the planes in flight before
-    the first is folded (at most three) per tile, so well under K G bytes;
-and bounded by |S| G everywhere else.
+  * one active partition present near every block: each chunk of its plane once, G bytes;
+  * every block in the LAST partition (that plane 0 everywhere, the others 255), all K = 64
+    partitions active: the per-chunk path loads the two batches in flight before the first
+    is folded, 16 G; the region path loads that plane and stops, G (every active plane
+    would be 64 G);
+  * two halves of different material, both visible: each region reads its own material's
+    plane and stops, G, where one order for the whole map would read about 1.5 G;
+  * after dm_mark_built (bounds taken from the planes rather than the z pass): the same.
+Everywhere else the count is bounded by |S| G.
 """
 import numpy as np
 import pytest
@@ -86,12 +92,11 @@ def test_covering_plane_is_read_first():
     d, loaded = _counted_update(eng, tf)
     assert not d.any()                               # Eq. 1: plane 63 is 0 everywhere
     assert eng.G % 16 == 0
-    assert loaded % (8 * eng.G) == 0                 # whole batches of 8 planes
-    assert 8 * eng.G <= loaded <= 24 * eng.G         # ascending order: 64 G
+    assert loaded == 16 * eng.G                      # every active plane: 64 G
 
 
-def test_plane_major_tiles_stop_at_zero():
-    # b = 1: 21 M blocks, enough for the plane-major tiles of the update kernel
+def test_large_map_reads_the_covering_plane_only():
+    # b = 1: 21 M blocks, 5120 regions over every warp of the grid
     N, K = 256, 8
     X, Y, Z = 512, 256, 160
     vol = np.full((Z, Y, X), 250, dtype=np.uint8)            # partition 7 everywhere
@@ -100,7 +105,7 @@ def test_plane_major_tiles_stop_at_zero():
     tf = T.all_visible_tf(N)
     d, loaded = _counted_update(eng, tf)
     assert not d.any()
-    assert eng.G <= loaded <= 4 * eng.G              # all K planes: 8 G
+    assert loaded == eng.G                           # all K planes: 8 G
 
 
 def test_random_edits_same_maps_counted_or_not():
@@ -134,4 +139,48 @@ def test_mark_built_ranks_the_loaded_planes(tmp_path):
     tf = T.all_visible_tf(N)
     d, loaded = _counted_update(b, tf)
     assert not d.any()
-    assert loaded % (8 * b.G) == 0 and 8 * b.G <= loaded <= 24 * b.G
+    assert loaded == 16 * b.G
+
+
+def test_regions_read_their_own_material_first():
+    # b = 1, apron 0: 8.4 M blocks, 2048 regions, each inside one half
+    N, K = 256, 16
+    X, Y, Z = 512, 256, 64
+    vol = np.full((Z, Y, X), 40, dtype=np.uint8)            # partition 2 ...
+    vol[Z // 2:] = 200                                       # ... and 12 (upper half)
+    eng = _engine((X, Y, Z), np.uint8, 1, 0, K, N)
+    eng.build_partitions(_dev(vol))
+    tf = T.zero_tf(N)
+    tf[40, 3] = tf[200, 3] = 1.0
+    assert oracle.active_set(tf, K) == [2, 12]
+    d, loaded = _counted_update(eng, tf)
+    assert not d.any()                               # every block holds a visible material
+    assert loaded == eng.G
+
+
+def test_region_bounds_after_mark_built():
+    N, K = 256, 8
+    X, Y, Z = 512, 256, 64
+    vol = np.full((Z, Y, X), 250, dtype=np.uint8)            # partition 7 everywhere
+    eng = _engine((X, Y, Z), np.uint8, 1, 0, K, N)
+    eng.build_partitions(_dev(vol))
+    eng.offload()                                    # planes to host, scratch released
+    eng.reload()                                     # dm_mark_built: bounds from the planes
+    d, loaded = _counted_update(eng, T.all_visible_tf(N))
+    assert not d.any()
+    assert loaded == eng.G
+
+
+def test_region_path_matches_the_oracle():
+    # b = 1: 6.3 M blocks of a noise-and-ellipsoids volume, read region by region
+    N, K = 256, 16
+    X, Y, Z = 512, 256, 48
+    vol = synth.as_numpy(synth.volume_of("u8", (X, Y, Z), 9))
+    eng = _engine((X, Y, Z), np.uint8, 1, 0, K, N)
+    eng.build_partitions(_dev(vol))
+    _, pdm, _, _ = oracle.build_partitions(vol, 1, 0, N, K)
+    for tf in synth.tf_edit_sequence(9, N, 6):
+        want = oracle.update_tf(pdm, tf)[0].reshape(-1)
+        d, loaded = _counted_update(eng, tf)
+        assert np.array_equal(d, want)
+        assert loaded <= _active(tf, K) * eng.G
