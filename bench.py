@@ -50,20 +50,33 @@ SPIN_CYCLES = 200_000
 # byte of PDM planes that the same launches load (the kernel's own count), writes per
 # block of the grid, so that the record scales to other edits and sizes.
 NCU_TRAFFIC = {
+    # k_update_fused, the first five edits of each workload's sequence (the bench's warm-up
+    # session), DRAM read against the PDM bytes the same launches load: the combine loads
+    # 16-byte chunks, DRAM moves larger atoms, so a chunk loaded next to finished ones costs
+    # more than its 16 bytes (about 1.4x on the region-by-region maps, 1.01 on ct, where
+    # nearly every chunk of every active plane is loaded)
+    "ct": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.009514,
+           "write_per_block": 0.000391},
+    "mid": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.456732,
+            "write_per_block": 0.065193},
+    "large": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.451585,
+              "write_per_block": 0.560779},
 }
 
 
-# Warp instructions of the one-time precompute (its five launches: partition table, POM
-# masks, x pass, y pass, z pass) from one ncu capture (smsp__inst_executed.sum, one pass),
-# keyed by workload, with the hash of the kernel code it was taken on; the precompute's ALU
-# roofline is reported as null once that code has changed.
+# Warp instructions of the one-time precompute (its eight launches: partition table, POM
+# masks, x pass, y pass, z pass, plane cover, plane order, region minima) from one ncu
+# capture (smsp__inst_executed.sum, one pass), keyed by workload, with the hash of the
+# kernel code it was taken on; the precompute's ALU roofline is reported as null once that
+# code has changed.
 NCU_PRECOMPUTE_INST = {
-    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 341,718,056 +
-    # 684,269,568
-    "mid": {"source_sha": "0aa7ad3784d871da", "warp_instructions": 1730017179.0},
+    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 229,095,856 +
+    # 442,675,200 + 628,352 + 1,062 + 48,168,960
+    "mid": {"source_sha": "c1ab55bb8c2d949e", "warp_instructions": 1424598985.0},
     # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,014,630,284 +
-    # 1,369,804,552 (y, 256-block lines) + 2,685,460,480 (z, 449-block lines)
-    "large": {"source_sha": "0aa7ad3784d871da", "warp_instructions": 6883998972.0},
+    # 918,354,416 (y, 256-block lines) + 1,701,677,056 (z, 449-block lines) + 628,352 +
+    # 1,062 + 193,105,920
+    "large": {"source_sha": "c1ab55bb8c2d949e", "warp_instructions": 5642500746.0},
 }
 
 
