@@ -346,15 +346,12 @@ __device__ __forceinline__ void combine_tiles_planar(const uint8_t* __restrict__
     cp_async_wait0();
 }
 
-constexpr int kRPM = kRegionChunks / 32;                      // chunks per lane per region
-static_assert(kRPM <= kPM, "a region's chunks fit one stage's slots");
-
 // D' region by region, without the range index: warp w of the grid (w = warp * gridDim.x
 // + block, so that small maps spread over every SM) takes regions w, w + warps, ...  For a
 // region it lists the active planes (the CTA's list, in the plane order) in ascending order
 // of their minimum over the region, ties kept in list order, and reads them one plane per
-// step, lane l loading chunks r * kRegionChunks + 32 k + l (k < kRPM) of the plane: 512
-// contiguous bytes per instruction.  A chunk whose minimum is 0 loads no further plane, and the region stops
+// step, lane l loading chunks r * 256 + 32 k + l (k < 8) of the plane: 512 contiguous bytes
+// per instruction.  A chunk whose minimum is 0 loads no further plane, and the region stops
 // as soon as the next plane's regional minimum is at least the largest minimum of the
 // region so far: that plane, and every later one, is at least every byte of D' there.
 // The first plane is folded before the second is issued (a region that one plane settles
@@ -389,19 +386,19 @@ __device__ __forceinline__ void combine_regions(const uint8_t* __restrict__ pdm,
         const int64_t c0 = r * kRegionChunks + lane;
         unsigned live = 0;                                    // bit k: chunk k may still fall
 #pragma unroll
-        for (int k = 0; k < kRPM; ++k)
+        for (int k = 0; k < kPM; ++k)
             if (c0 + 32 * k < nvec) live |= 1u << k;
         const unsigned valid = live;
-        ByteMin16 acc[kRPM];
+        ByteMin16 acc[kPM];
 #pragma unroll
-        for (int k = 0; k < kRPM; ++k) acc[k].reset();
+        for (int k = 0; k < kPM; ++k) acc[k].reset();
         auto issue = [&](int q, int slot) {
             const uint8_t* src = pdm + int64_t(w_list[q]) * plane;
             unsigned issued = 0;
 #pragma unroll
-            for (int k = 0; k < kRPM; ++k)
+            for (int k = 0; k < kPM; ++k)
                 if ((live >> k) & 1u) {
-                    cp_async16(stage + (slot * kRPM + k) * ld, src + ((c0 + 32 * k) << 4));
+                    cp_async16(stage + (slot * kPM + k) * ld, src + ((c0 + 32 * k) << 4));
                     ++issued;
                 }
             cp_async_commit();
@@ -411,9 +408,9 @@ __device__ __forceinline__ void combine_regions(const uint8_t* __restrict__ pdm,
         auto fold = [&](int slot) {
             unsigned tmax = 0;
 #pragma unroll
-            for (int k = 0; k < kRPM; ++k) {
+            for (int k = 0; k < kPM; ++k) {
                 if ((live >> k) & 1u) {
-                    acc[k].fold(stage[(slot * kRPM + k) * ld]);
+                    acc[k].fold(stage[(slot * kPM + k) * ld]);
                     const unsigned mk = acc[k].max_byte();
                     if (mk == 0u) live &= ~(1u << k);
                     tmax = max(tmax, mk);
@@ -440,7 +437,7 @@ __device__ __forceinline__ void combine_regions(const uint8_t* __restrict__ pdm,
             }
         }
 #pragma unroll
-        for (int k = 0; k < kRPM; ++k)
+        for (int k = 0; k < kPM; ++k)
             if ((valid >> k) & 1u)
                 __stcs(reinterpret_cast<uint4*>(out) + c0 + 32 * k, acc[k].value());
         __syncwarp();                                         // w_key / w_list are reused
