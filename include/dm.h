@@ -111,11 +111,11 @@ dm_status dm_query_sizes(const dm_ctx *ctx, dm_sizes *out);
  * the full recompute is never used in DM_OCC_MINMAX mode), d_scratch (scratch_bytes,
  * 256-byte aligned).  d_mask is only written and read by dm_build_partitions (the POMs are
  * an intermediate, §5) and may be released afterwards by binding NULL.  Rebinding is
- * allowed between calls.  The scratch buffer holds two per-context tables that
+ * allowed between calls.  The scratch buffer holds per-context tables that
  * dm_build_partitions and dm_mark_built write: the partition of every intensity, and the
- * order in which the updates read the planes (below).  Binding another pdm or scratch
- * buffer marks the context unbuilt, and the updates return DM_ERR_NOT_BOUND until one of
- * those two calls has run on the new buffers.
+ * plane order and region bounds with which the updates read the planes (below).  Binding
+ * another pdm or scratch buffer marks the context unbuilt, and the updates return
+ * DM_ERR_NOT_BOUND until one of those two calls has run on the new buffers.
  */
 dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *d_scratch);
 
@@ -124,8 +124,10 @@ dm_status dm_bind(dm_ctx *ctx, void *d_mask, void *d_pdm, void *d_minmax, void *
  * (dims / dtype of the config) build the partition table, the K POMs as per-block bit
  * masks over each block's footprint (b^3 voxels plus the apron), the block min/max (if
  * d_minmax is bound), and the K PDMs as Chebyshev distance transforms of the POMs,
- * clamped to uint8 (§3.2).  Last, the plane order: the K planes ranked by their count of
- * zero bytes (occupied blocks) on a fixed sample, most first.  Asynchronous on `stream`.
+ * clamped to uint8 (§3.2).  Last, what the update uses to read few bytes: the plane order
+ * (the K planes ranked by their count of zero bytes on a fixed sample, most first) and the
+ * region bounds (each plane's minimum over every region of 4096 blocks), in the scratch.
+ * Asynchronous on `stream`.
  */
 dm_status dm_build_partitions(dm_ctx *ctx, const void *d_volume, void *stream);
 
@@ -160,8 +162,12 @@ dm_status dm_build_partitions_batch(dm_ctx *const *ctxs, const void *const *d_vo
  * active.  d_active_mask_out: optional device uint64 [ceil(K/64)] receiving S as a bit
  * set.  Reads the PDMs built by dm_build_partitions.  Asynchronous; no host round trip.
  * Without the range index the active planes are read in the context's plane order, and a
- * 16-byte chunk of D' whose minimum is already 0 in every byte reads no further plane, so
- * the traffic is at most (|S| + 1) * G bytes (D' is the same in any order).
+ * 16-byte chunk of D' whose minimum is already 0 in every byte reads no further plane; on
+ * maps of about 5 M blocks or more each region of 4096 blocks reads its planes in
+ * ascending order of their minimum over the region (bounds built with the maps) and stops
+ * once the next plane's regional minimum is at least the region's largest minimum so far.
+ * The traffic is at most (|S| + 1) * G bytes and D' is the same as when every active plane
+ * is read.
  */
 dm_status dm_update_tf(dm_ctx *ctx, const float *d_tf_rgba, uint8_t *d_out,
                        uint64_t *d_active_mask_out, void *stream);
@@ -195,8 +201,8 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
  * context, and later copies them back into the bound buffers of a context with the same
  * hash, declares them built with dm_mark_built(ctx, hash); the call fails with
  * DM_ERR_INVALID_ARG when the hash differs, and with DM_ERR_NOT_BOUND when pdm / scratch
- * are not bound.  The partition table and the plane order in scratch are rebuilt on
- * `stream` (the order from the planes as they are at that point of the stream).  The paper
+ * are not bound.  The partition table, the plane order and the region bounds in scratch
+ * are rebuilt on `stream` (from the planes as they are at that point of the stream).  The paper
  * recomputes the maps at every load (§3.1, one-time initialisation).
  */
 dm_status dm_config_hash(const dm_ctx *ctx, uint64_t *out);
