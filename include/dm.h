@@ -202,8 +202,8 @@ dm_status dm_full_recompute(dm_ctx *ctx, const void *d_volume, const float *d_tf
  * hash, declares them built with dm_mark_built(ctx, hash); the call fails with
  * DM_ERR_INVALID_ARG when the hash differs, and with DM_ERR_NOT_BOUND when pdm / scratch
  * are not bound.  The partition table, the plane order and the region bounds in scratch
- * are rebuilt on `stream` (from the planes as they are at that point of the stream).  The paper
- * recomputes the maps at every load (§3.1, one-time initialisation).
+ * are rebuilt on `stream` (from the planes as they are at that point of the stream).  The
+ * paper recomputes the maps at every load (§3.1, one-time initialisation).
  */
 dm_status dm_config_hash(const dm_ctx *ctx, uint64_t *out);
 dm_status dm_mark_built(dm_ctx *ctx, uint64_t hash, int32_t with_minmax, void *stream);
@@ -248,10 +248,11 @@ dm_status dm_update_tf_batch(const dm_batch_item *items, int32_t n,
  * plane that one of a group's TFs needs once and folds it into each of those TFs' maps,
  * so a group's HBM traffic is at most (|S_1 u ... u S_E| + E) * G bytes instead of
  * sum_e (|S_e| + 1) * G (planes in the plane order; a chunk at 0 in every byte of every
- * TF of the group reads no further plane).  The active sets live in d_workspace, a caller-allocated device
- * buffer of at least dm_batch_workspace_bytes(n) bytes, 256-byte aligned, which must not
- * be used by other work while the call's kernels run (no context's scratch is written, so
- * calls on other streams may share contexts but not a workspace).  Up to
+ * TF of the group reads no further plane).  The active sets live in d_workspace, a
+ * caller-allocated device buffer of at least dm_batch_workspace_bytes(n) bytes, 256-byte
+ * aligned, which must not be used by other work while the call's kernels run (no
+ * context's scratch is written, so calls on other streams may share contexts but not a
+ * workspace).  Up to
  * DM_BATCH_MAX_ITEMS groups share a launch pair; more are split.  Outputs must not overlap.
  * Errors as for dm_update_tf_batch (a repeated context is allowed), plus
  * DM_ERR_INVALID_ARG for a missing, misaligned or short workspace.  Asynchronous;
