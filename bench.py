@@ -536,6 +536,7 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
         [pct(upd, 50), pct(upd, 99), pct(full, 50), pct(full, 99), region_ms], ws)
     pre_ms = float(np.median(pre))
     pre_bytes = s_bytes * V + w["K"] * G
+    traffic = ncu_traffic(name, G, float(loaded.mean()))
     res = {
         "workload": workload_name(name, w), "volume_xyz": [X, Y, Z], "grid_G": G,
         "edits_per_step": E, "volume_sha256": vol_sha, "region_ms": region_max,
@@ -562,7 +563,12 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
         "roofline": {"kernel": "k_update_fused (step 1 + Eq. 1)", "bound": "hbm",
                      "achieved": achieved, "peak": peak[0], "unit": "GB/s",
                      "frac": achieved / peak[0] if achieved else None,
-                     "traffic": ncu_traffic(name, G, float(loaded.mean())),
+                     "traffic": traffic,
+                     # DRAM bytes moved (the traffic record) per second of the mean launch,
+                     # against the same peak: the combine loads 16-byte chunks, DRAM moves
+                     # larger atoms, so this runs above `frac` where chunks finish early
+                     "dram_frac": (traffic / (upd_a.mean() * 1e-3) / 1e9 / peak[0]
+                                   if traffic and fused else None),
                      "peak_source": peak[1],
                      "algorithmic_bytes_per_launch": float(bytes_upd.mean()),
                      "mean_launch_us": float(upd_a.mean() * 1e3)},

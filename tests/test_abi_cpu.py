@@ -309,3 +309,20 @@ def test_batched_precompute_is_refused_on_the_host():
     finally:
         for ctx in ctxs:
             A.dm_destroy(ctx)
+
+
+def test_profile_counter_is_checked_on_the_host():
+    """dm_set_profile_counter takes an 8-byte aligned device address or NULL; a misaligned
+    counter is refused with DM_ERR_INVALID_ARG before any launch could use it."""
+    c, keep = cfg()
+    ctx = A.dm_create(c)
+    try:
+        A.dm_set_profile_counter(ctx, 1 << 20)              # aligned: accepted (not used)
+        A.dm_set_profile_counter(ctx, None)                 # stop
+        with pytest.raises(A.DmError) as e:
+            A.dm_set_profile_counter(ctx, (1 << 20) + 4)
+        assert e.value.status == A.DM_ERR_INVALID_ARG
+        assert "misaligned" in str(e.value)
+        assert A.load().dm_set_profile_counter(None, None) == A.DM_ERR_INVALID_ARG
+    finally:
+        A.dm_destroy(ctx)
