@@ -574,7 +574,10 @@ def session_leg(dev, name, steps, warmup, flush, peak, ws, edits=None, e2e=True,
                      "mean_launch_us": float(upd_a.mean() * 1e3)},
         "clocks": clk,
         "e2e": e2e_res,
-        "gpu_launches": steps * (8 + E * ((1 if fused else 2) + 4)),
+        # the precompute: partition table, POM, x, y, z, plane cover and order, then the
+        # region bounds from the masks' rows (2D x pass, 2D line pass, reduction) where
+        # the grid's rows tile its regions (every bench workload), else one pass over planes
+        "gpu_launches": steps * (10 + E * ((1 if fused else 2) + 4)),
     }
     if idx:
         idx["speedup_vs_full_recompute_p50"] = p50f / idx["p50_ms"]

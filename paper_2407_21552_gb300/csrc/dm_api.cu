@@ -27,6 +27,8 @@ struct dm_ctx {
     // scratch layout (byte offsets)
     size_t off_lut, off_cnt, off_act, off_nact, off_smask, off_cover, off_order, off_rmin, off_tf,
         off_out;
+    bool rows_ok;                   // region bounds from the masks' rows (the single build)
+    size_t off_proj, off_d2;        // their scratch (rows_ok)
     void* d_mask;
     void* d_pdm;
     void* d_minmax;
@@ -165,11 +167,16 @@ dm_status dm_create(dm_ctx** out, const dm_config* cfg)
     x->off_act = o;   o = align_up(o + size_t(dmk::kMaxPartitions + 8) * 2, 256);
     x->off_nact = o;  o = align_up(o + 64, 64);
     x->off_smask = o; o = align_up(o + 64, 256);
-    x->off_cover = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 4, 256);
+    x->off_cover = o; o = align_up(o + size_t(dmk::kMaxPartitions) * dmk::kCoverSplit * 4, 256);
     x->off_order = o; o = align_up(o + size_t(dmk::kMaxPartitions) * 2, 256);
     x->off_rmin = o;  o = align_up(o + size_t(dmk::num_regions(g.G)) * size_t(K), 256);
     x->off_tf = o;    o = align_up(o + size_t(N) * 16, 256);
     x->off_out = o;   o = align_up(o + size_t(g.G), 256);
+    x->rows_ok = dmk::bounds_from_rows_ok(g, K);
+    x->off_proj = o;
+    if (x->rows_ok) o = align_up(o + dmk::bounds_rows_proj_bytes(g, K), 256);
+    x->off_d2 = o;
+    if (x->rows_ok) o = align_up(o + dmk::bounds_rows_d2_bytes(g, K), 256);
     s.scratch_bytes = o;
     int dev = 0;
     x->num_sms = 152;
@@ -223,6 +230,7 @@ static dmk::PlaneOrderItem plane_order_item(const dm_ctx* c)
     it.cover = reinterpret_cast<uint32_t*>(scratch + c->off_cover);
     it.order = reinterpret_cast<uint16_t*>(scratch + c->off_order);
     it.rmin = scratch + c->off_rmin;
+    it.bounds_from_planes = 1;
     return it;
 }
 
@@ -274,15 +282,25 @@ dm_status dm_build_partitions(dm_ctx* ctx, const void* d_volume, void* stream)
     e = dmk::launch_pom_build(d_volume, ctx->geo, N, K, lut, static_cast<uint64_t*>(ctx->d_mask),
                               ctx->d_minmax, shift, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "POM build");
-    e = dmk::launch_xpass_mask(static_cast<const uint64_t*>(ctx->d_mask), K, ctx->geo, pdm, s);
+    uint64_t* proj = reinterpret_cast<uint64_t*>(scratch + ctx->off_proj);
+    bool projected = false;                  // the row ORs for the region bounds, if taken
+    e = dmk::launch_xpass_mask(static_cast<const uint64_t*>(ctx->d_mask), K, ctx->geo, pdm, s,
+                               ctx->rows_ok ? proj : nullptr, &projected);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM x pass");
     e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM y pass");
     e = dmk::launch_line_pass(pdm, K, ctx->geo.plane, ctx->geo, 2, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "PDM z pass");
-    const dmk::PlaneOrderItem po = plane_order_item(ctx);
+    dmk::PlaneOrderItem po = plane_order_item(ctx);
+    po.bounds_from_planes = ctx->rows_ok ? 0 : 1;
     e = dmk::launch_plane_order(&po, 1, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plane order");
+    if (ctx->rows_ok) {
+        e = dmk::launch_bounds_from_rows(static_cast<const uint64_t*>(ctx->d_mask), ctx->geo, K,
+                                         proj, projected, scratch + ctx->off_d2,
+                                         scratch + ctx->off_rmin, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "region bounds");
+    }
     if (ctx->J > 0) {
         e = dmk::launch_build_index(pdm, ctx->geo.plane, ctx->geo.G, K, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "range index");

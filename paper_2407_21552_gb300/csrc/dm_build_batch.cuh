@@ -50,19 +50,34 @@ cudaError_t launch_line_pass_batch(const BuildItem* items, int n, int axis, cuda
 //  * the region bounds: for each region of kRegionBlocks consecutive blocks and each plane,
 //    the plane's minimum over the region.  No byte of D' in a region can be lowered by a
 //    plane whose regional minimum is at least the region's current maximum.
+constexpr int kCoverSplit = 8;         // CTAs that count one plane's sampled zero bytes
+
 struct PlaneOrderItem {
     const uint8_t* pdm;                // K planes, `plane` bytes apart
     int64_t plane;
     int64_t G;
     int K;
-    uint32_t* cover;                   // [K] sampled zero-byte counts (device, written)
+    uint32_t* cover;                   // [K][kCoverSplit] sampled zero-byte counts (written)
     uint16_t* order;                   // [K] partitions, most covered first (device, written)
     uint8_t* rmin;                     // [regions(G)][K] regional minima (device, written)
+    int bounds_from_planes;            // 1: rmin from the planes; 0: the caller fills it
 };
 
 // Three launches over up to kMaxBuildBatch contexts: one CTA per plane counts, one CTA per
 // context ranks, one warp per (region, plane) takes the minimum.  Runs after the context's
 // z pass on the same stream.
 cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t s);
+
+// The region bounds of a context whose regions are whole rows (bounds_from_rows_ok), from
+// its POM masks rather than its planes: the masks ORed along each row, a 2D distance
+// transform of those (x pass and line pass over the rows), the minimum over each region's
+// rows.  proj and d2 are scratch of bounds_rows_proj_bytes / bounds_rows_d2_bytes;
+// projected: the x pass already wrote proj (launch_xpass_mask's proj argument).
+bool bounds_from_rows_ok(const Geometry& g, int K);
+size_t bounds_rows_proj_bytes(const Geometry& g, int K);
+size_t bounds_rows_d2_bytes(const Geometry& g, int K);
+cudaError_t launch_bounds_from_rows(const uint64_t* mask, const Geometry& g, int K,
+                                    uint64_t* proj, bool projected, uint8_t* d2, uint8_t* rmin,
+                                    cudaStream_t s);
 
 }  // namespace dmk

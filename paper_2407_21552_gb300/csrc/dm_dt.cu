@@ -51,6 +51,9 @@ struct XGeom {
     int vec16;          // rows are 16-byte aligned: store 16 outputs as one vector
     int rpc;            // block rows per CTA of the K-map pass (short rows share a CTA)
     int warp_rows;      // rows of at most 96 blocks, at most 64 maps: one warp per row
+    // optional (one row per CTA): proj[row][w] = the row's mask words ORed along x, the
+    // occupancy of each map in the row
+    uint64_t* proj;
 };
 
 struct SrcMinMax8 {     // min/max occupancy: one visible intensity in [min, max]
@@ -193,8 +196,20 @@ __device__ __forceinline__ void xpass_mask_row(const uint64_t* __restrict__ mask
             }
         }
         __syncthreads();
-        for (int q = tid; q < np; q += kThreads)
+        bool occ = false;                                    // map tid occupies the row
+        for (int q = tid; q < np; q += kThreads) {
             nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
+            if (xg.proj) {
+                uint32_t any = 0;
+                for (int wi = 0; wi < nw; ++wi) any |= s_bits[q * nw + wi];
+                occ = any != 0u;
+            }
+        }
+        if (xg.proj) {                                       // uniform; np <= 64 < kThreads
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
+            if (lane == 0 && warp < 2)
+                reinterpret_cast<uint32_t*>(xg.proj + int64_t(row) * W + w)[warp] = bal;
+        }
         __syncthreads();
         for (int it = tid; it < np * nh; it += kThreads) {
             const int q = it / nh, hw = it - q * nh;
@@ -446,6 +461,7 @@ XGeom xgeom(const Geometry& g, int64_t plane, const void* out)
               ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     x.rpc = 1;
     x.warp_rows = 0;
+    x.proj = nullptr;
     return x;
 }
 
@@ -681,9 +697,10 @@ size_t xpass_smem(int gx, int K)
 }
 
 cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, uint8_t* pdm,
-                              cudaStream_t s)
+                              cudaStream_t s, uint64_t* proj, bool* projected)
 {
     XGeom xg = xgeom(g, g.plane, pdm);
+    if (projected) *projected = false;
     if (xpass_warp_rows_ok(xg.nw, K)) {
         xg.warp_rows = 1;
         const unsigned ctas = unsigned((xg.rows + kThreads / 32 - 1) / (kThreads / 32));
@@ -709,6 +726,8 @@ cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, ui
         }                                                                                    \
         e = ensure_dynamic_smem<k_xpass_mask<WW>>(int(smem));                                \
         if (e != cudaSuccess) return e;                                                      \
+        xg.proj = proj;                                                                      \
+        if (projected) *projected = proj != nullptr;                                         \
         return launch_pdl(k_xpass_mask<WW>, dim3(xg.rows), dim3(kThreads), smem, s, mask, K, \
                           xg, pdm);
         DM_XPASS_CASE(1)

@@ -254,8 +254,11 @@ cudaError_t launch_occ_exact(const void* vol, const Geometry& g, int N, const in
 
 // ---------------------------------------------------------------- distance transform
 // x pass: 1D distance along x to the nearest occupied block, saturating at 255.
+// proj (optional): where the one-row-per-CTA form runs, it also writes each row's mask words
+// ORed along x to proj[row][W] and sets *projected.
 cudaError_t launch_xpass_mask(const uint64_t* mask, int K, const Geometry& g, uint8_t* pdm,
-                              cudaStream_t s);
+                              cudaStream_t s, uint64_t* proj = nullptr,
+                              bool* projected = nullptr);
 cudaError_t launch_xpass_minmax(const void* minmax, const int32_t* cnt, const Geometry& g,
                                 uint8_t* out, cudaStream_t s);
 cudaError_t launch_xpass_occ(uint8_t* occ_inout, const Geometry& g, cudaStream_t s);

@@ -637,11 +637,13 @@ k_index_level(uint8_t* __restrict__ pdm, int64_t plane, int64_t G, int prev_base
 
 // ---------------------------------------------------------------- plane order
 // Zero bytes of each plane on a fixed sample (kCoverSamples 16-byte chunks at an even
-// stride, or bytes where the plane is not 16-byte aligned): one CTA per plane, no atomics,
-// so the count is the same on every run; a thread issues its loads 8 at a time.
+// stride, or bytes where the plane is not 16-byte aligned): kCoverSplit CTAs per plane,
+// each writing its part of the count (no atomics, so the count is the same on every run);
+// a thread issues all its loads before it uses any.
 constexpr int kCoverSamples = 8192;
 constexpr int kOrderThreads = 256;
 constexpr int kCoverPer = kCoverSamples / kOrderThreads;
+static_assert(kCoverPer % kCoverSplit == 0, "each CTA of a plane takes whole rounds");
 static_assert(kMaxPartitions <= kOrderThreads, "one thread per partition ranks the planes");
 
 struct PlaneOrderBatch {
@@ -661,33 +663,34 @@ k_plane_cover(const __grid_constant__ PlaneOrderBatch B)
     __shared__ uint32_t s_w[kOrderThreads / 32];
     const int i = batch_item_of(B.start, B.n, int(blockIdx.x));
     const PlaneOrderItem& it = B.it[i];
-    const int p = int(blockIdx.x) - B.start[i];
+    const int local = int(blockIdx.x) - B.start[i];
+    const int p = local / kCoverSplit, q = local - p * kCoverSplit;   // plane, its part
     const uint8_t* src = it.pdm + int64_t(p) * it.plane;
     const int tid = threadIdx.x;
     pdl_wait();
-    uint32_t z = 0;                                            // zero bytes x 8 (vector path)
+    uint32_t z = 0;                                            // zero bytes x 8
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && it.G >= 16) {
         const int64_t nvec = it.G >> 4;
         const int64_t ns = nvec < kCoverSamples ? nvec : kCoverSamples;
         const int64_t step = nvec / ns;
         const uint4* v4 = reinterpret_cast<const uint4*>(src);
-        constexpr int kRound = 8;                              // loads in flight
-        for (int r0 = 0; r0 < kCoverPer; r0 += kRound) {
-            uint4 v[kRound];
+        constexpr int kPer = kCoverPer / kCoverSplit;          // loads per thread, all at once
+        uint4 v[kPer];
 #pragma unroll
-            for (int r = 0; r < kRound; ++r) {
-                const int64_t j = int64_t(r0 + r) * kOrderThreads + tid;
-                v[r] = j < ns ? __ldcs(v4 + j * step) : make_uint4(1u, 1u, 1u, 1u);
-            }
-#pragma unroll
-            for (int r = 0; r < kRound; ++r)
-                z += __popc(__vcmpeq4(v[r].x, 0u)) + __popc(__vcmpeq4(v[r].y, 0u)) +
-                     __popc(__vcmpeq4(v[r].z, 0u)) + __popc(__vcmpeq4(v[r].w, 0u));
+        for (int r = 0; r < kPer; ++r) {
+            const int64_t j = int64_t(r * kCoverSplit + q) * kOrderThreads + tid;
+            v[r] = j < ns ? __ldcs(v4 + j * step) : make_uint4(1u, 1u, 1u, 1u);
         }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r)
+            z += __popc(__vcmpeq4(v[r].x, 0u)) + __popc(__vcmpeq4(v[r].y, 0u)) +
+                 __popc(__vcmpeq4(v[r].z, 0u)) + __popc(__vcmpeq4(v[r].w, 0u));
     } else {
         const int64_t ns = it.G < 16 * kCoverSamples ? it.G : 16 * kCoverSamples;
         const int64_t step = ns > 0 ? it.G / ns : 1;
-        for (int64_t j = tid; j < ns; j += kOrderThreads) z += src[j * step] == 0 ? 8u : 0u;
+        for (int64_t j = int64_t(q) * kOrderThreads + tid; j < ns;
+             j += int64_t(kOrderThreads) * kCoverSplit)
+            z += src[j * step] == 0 ? 8u : 0u;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, d);
@@ -696,7 +699,7 @@ k_plane_cover(const __grid_constant__ PlaneOrderBatch B)
     if (tid == 0) {
         uint32_t t = 0;
         for (int w = 0; w < kOrderThreads / 32; ++w) t += s_w[w];
-        it.cover[p] = t >> 3;
+        it.cover[p * kCoverSplit + q] = t >> 3;
     }
 }
 
@@ -709,7 +712,11 @@ k_plane_order(const __grid_constant__ PlaneOrderBatch B)
     const PlaneOrderItem& it = B.it[blockIdx.x];
     const int tid = threadIdx.x;
     pdl_wait();
-    if (tid < it.K) s_c[tid] = it.cover[tid];
+    if (tid < it.K) {
+        uint32_t c = 0;
+        for (int q = 0; q < kCoverSplit; ++q) c += it.cover[tid * kCoverSplit + q];
+        s_c[tid] = c;
+    }
     __syncthreads();
     if (tid < it.K) {
         const uint32_t c = s_c[tid];
@@ -755,6 +762,57 @@ k_region_min(const __grid_constant__ PlaneOrderBatch B)
     for (int64_t b = done + lane; b < b1; b += 32) m = min(m, unsigned(src[b]));
     m = __reduce_min_sync(0xFFFFFFFFu, m);
     if (lane == 0) it.rmin[r * it.K + p] = uint8_t(m);
+}
+
+// ---------------------------------------------------------------- region bounds by rows
+// Where a region is whole rows of blocks (4096 a multiple of gx), the minimum of a PDM over
+// a region is the minimum over its rows (y, z) of D2(y, z), the 2D chessboard distance
+// transform of the partition's occupancy ORed along x: a block of the row can sit above
+// the nearest occupied block in x, so x adds nothing to the distance.  D2 is built with
+// the x pass and the line pass over the projected masks (y as x, z as y), about gx times
+// fewer bytes than the PDMs; the regional minima then come from D2.
+
+// P[row][w] = OR over x of mask[(row * gx + x) * W + w]: one warp per row.
+__global__ void __launch_bounds__(256)
+k_row_project(const uint64_t* __restrict__ mask, int W, int gx, int64_t rows,
+              uint64_t* __restrict__ proj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = int64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    pdl_wait();
+    if (row >= rows) return;                                 // warp-uniform
+    const uint64_t* src = mask + row * gx * W;
+    for (int w = 0; w < W; ++w) {
+        uint64_t m = 0;
+        for (int x = lane; x < gx; x += 32) m |= src[int64_t(x) * W + w];
+        const unsigned lo = __reduce_or_sync(0xFFFFFFFFu, unsigned(m));
+        const unsigned hi = __reduce_or_sync(0xFFFFFFFFu, unsigned(m >> 32));
+        if (lane == 0) proj[row * W + w] = (uint64_t(hi) << 32) | lo;
+    }
+}
+
+// rmin[r][p] = min over the rows of region r of D2_p: one thread per (plane, region), so
+// that neighbouring threads read neighbouring regions' rows; 16-byte loads where a region
+// is whole 16-row vectors.
+__global__ void __launch_bounds__(256)
+k_region_min_rows(const uint8_t* __restrict__ d2, int64_t plane2, int64_t rows,
+                  int rows_per_region, int K, int64_t nreg, uint8_t* __restrict__ rmin)
+{
+    const int64_t u = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    pdl_wait();
+    if (u >= nreg * K) return;
+    const int p = int(u / nreg);
+    const int64_t r = u - int64_t(p) * nreg;
+    const int64_t q0 = r * rows_per_region;
+    const int64_t q1 = q0 + rows_per_region < rows ? q0 + rows_per_region : rows;
+    const uint8_t* src = d2 + int64_t(p) * plane2;           // plane2: a multiple of 64
+    unsigned m = 255u;
+    int64_t q = q0;
+    if (rows_per_region % 16 == 0)
+        for (; q + 16 <= q1; q += 16)
+            m = min(m, bytemin16(*reinterpret_cast<const uint4*>(src + q)));
+    for (; q < q1; ++q) m = min(m, unsigned(src[q]));
+    rmin[r * K + p] = uint8_t(m);
 }
 
 }  // namespace
@@ -851,21 +909,79 @@ cudaError_t launch_plane_order(const PlaneOrderItem* items, int n, cudaStream_t 
         if (items[k].K < 1 || items[k].K > kMaxPartitions) return cudaErrorInvalidValue;
         B.it[k] = items[k];
         B.start[k] = ctas;
-        ctas += items[k].K;
+        ctas += items[k].K * kCoverSplit;
     }
     B.start[n] = ctas;
-    int64_t rctas = 0;
-    for (int k = 0; k < n; ++k) {
-        B.rstart[k] = int(rctas);
-        rctas += (num_regions(items[k].G) * items[k].K + kRminWarps - 1) / kRminWarps;
-        if (rctas > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
-    }
-    B.rstart[n] = int(rctas);
     cudaError_t e = launch_pdl(k_plane_cover, dim3(unsigned(ctas)), dim3(kOrderThreads), 0, s, B);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_plane_order, dim3(unsigned(n)), dim3(kOrderThreads), 0, s, B);
-    if (e != cudaSuccess || rctas == 0) return e;
-    return launch_pdl(k_region_min, dim3(unsigned(rctas)), dim3(kRminWarps * 32), 0, s, B);
+    if (e != cudaSuccess) return e;
+    // the region minima read from the planes, for the items that ask for it
+    PlaneOrderBatch R;
+    R.n = 0;
+    int64_t rctas = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!items[k].bounds_from_planes) continue;
+        R.it[R.n] = items[k];
+        R.rstart[R.n++] = int(rctas);
+        rctas += (num_regions(items[k].G) * items[k].K + kRminWarps - 1) / kRminWarps;
+        if (rctas > int64_t(0x7FFFFFFF)) return cudaErrorInvalidConfiguration;
+    }
+    if (R.n == 0) return cudaSuccess;
+    R.rstart[R.n] = int(rctas);
+    return launch_pdl(k_region_min, dim3(unsigned(rctas)), dim3(kRminWarps * 32), 0, s, R);
+}
+
+// The projected grid: rows (y, z) of the volume's grid as a one-slice grid, y along x.
+static Geometry row_geometry(const Geometry& g)
+{
+    Geometry g2 = g;
+    g2.gx = g.gy;
+    g2.gy = g.gz;
+    g2.gz = 1;
+    g2.G = int64_t(g.gy) * g.gz;
+    g2.plane = (g2.G + 63) / 64 * 64;
+    return g2;
+}
+
+bool bounds_from_rows_ok(const Geometry& g, int K)
+{
+    if (g.gx < 32 || kRegionBlocks % g.gx != 0) return false;
+    const Geometry g2 = row_geometry(g);
+    return g2.gx <= 10240 && xpass_smem(g2.gx, K) <= size_t(kXpassSmemLimit) &&
+           line_pass_smem(g2.gy) <= size_t(kLineSmemLimit);
+}
+
+size_t bounds_rows_proj_bytes(const Geometry& g, int K)
+{
+    return size_t(row_geometry(g).G) * size_t((K + 63) / 64) * 8;
+}
+
+size_t bounds_rows_d2_bytes(const Geometry& g, int K)
+{
+    return size_t(row_geometry(g).plane) * size_t(K);
+}
+
+cudaError_t launch_bounds_from_rows(const uint64_t* mask, const Geometry& g, int K,
+                                    uint64_t* proj, bool projected, uint8_t* d2, uint8_t* rmin,
+                                    cudaStream_t s)
+{
+    const Geometry g2 = row_geometry(g);
+    const int W = (K + 63) / 64;
+    cudaError_t e = cudaSuccess;
+    if (!projected) {                                        // the x pass did not write proj
+        e = launch_pdl(k_row_project, dim3(unsigned((g2.G + 7) / 8)), dim3(256), 0, s, mask, W,
+                       int(g.gx), g2.G, proj);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_xpass_mask(proj, K, g2, d2, s);              // distance along y
+    if (e != cudaSuccess) return e;
+    e = launch_line_pass(d2, K, g2.plane, g2, 1, s);        // then the max-min along z
+    if (e != cudaSuccess) return e;
+    const int64_t nreg = num_regions(g.G);
+    const int64_t n = nreg * K;
+    return launch_pdl(k_region_min_rows, dim3(unsigned((n + 255) / 256)), dim3(256), 0, s, d2,
+                      g2.plane, g2.G, int(kRegionBlocks / g.gx), K, nreg, rmin);
 }
 
 }  // namespace dmk

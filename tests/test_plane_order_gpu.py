@@ -184,3 +184,25 @@ def test_region_path_matches_the_oracle():
         d, loaded = _counted_update(eng, tf)
         assert np.array_equal(d, want)
         assert loaded <= _active(tf, K) * eng.G
+
+
+@pytest.mark.parametrize("dims", [(512, 256, 48), (64, 512, 160)])
+def test_row_bounds_equal_plane_bounds(dims):
+    # gx (512, or 64) divides 4096: dm_build_partitions takes the region bounds from the
+    # masks' rows (ORed by the x pass itself for 512-block rows, by a separate kernel for
+    # 64-block rows, which the x pass takes one warp per row); dm_mark_built (offload +
+    # reload) takes them from the planes.  Both are the exact regional minima, so the
+    # update (region by region at these 5-6 M blocks) reads the same bytes after either.
+    N, K = 256, 16
+    X, Y, Z = dims
+    vol = synth.as_numpy(synth.volume_of("u8", (X, Y, Z), 11))
+    eng = _engine((X, Y, Z), np.uint8, 1, 0, K, N)
+    eng.build_partitions(_dev(vol))
+    tfs = synth.tf_edit_sequence(11, N, 5)
+    first = [_counted_update(eng, tf) for tf in tfs]
+    eng.offload()
+    eng.reload()
+    for tf, (d1, c1) in zip(tfs, first):
+        d2, c2 = _counted_update(eng, tf)
+        assert np.array_equal(d1, d2)
+        assert c1 == c2
