@@ -55,28 +55,29 @@ NCU_TRAFFIC = {
     # 16-byte chunks, DRAM moves larger atoms, so a chunk loaded next to finished ones costs
     # more than its 16 bytes (about 1.4x on the region-by-region maps, 1.01 on ct, where
     # nearly every chunk of every active plane is loaded)
-    "ct": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.009514,
-           "write_per_block": 0.000391},
-    "mid": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.456732,
-            "write_per_block": 0.065193},
-    "large": {"source_sha": "af6ce866254440c6", "read_per_loaded_byte": 1.451585,
-              "write_per_block": 0.560779},
+    "ct": {"source_sha": "1376791f47d4a5d7", "read_per_loaded_byte": 1.009510,
+           "write_per_block": 0.000000},
+    "mid": {"source_sha": "1376791f47d4a5d7", "read_per_loaded_byte": 1.456792,
+            "write_per_block": 0.072824},
+    "large": {"source_sha": "1376791f47d4a5d7", "read_per_loaded_byte": 1.451583,
+              "write_per_block": 0.556511},
 }
 
 
-# Warp instructions of the one-time precompute (its eight launches: partition table, POM
-# masks, x pass, y pass, z pass, plane cover, plane order, region minima) from one ncu
+# Warp instructions of the one-time precompute (its ten launches on these workloads:
+# partition table, POM masks, x pass, y pass, z pass, plane cover, plane order, and the
+# region bounds from the masks' rows: 2D x pass, 2D line pass, reduction) from one ncu
 # capture (smsp__inst_executed.sum, one pass), keyed by workload, with the hash of the
 # kernel code it was taken on; the precompute's ALU roofline is reported as null once that
 # code has changed.
 NCU_PRECOMPUTE_INST = {
-    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 253,111,747 + 229,095,856 +
-    # 442,675,200 + 628,352 + 1,062 + 48,168,960
-    "mid": {"source_sha": "c1ab55bb8c2d949e", "warp_instructions": 1424598985.0},
-    # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,014,630,284 +
-    # 918,354,416 (y, 256-block lines) + 1,701,677,056 (z, 449-block lines) + 628,352 +
-    # 1,062 + 193,105,920
-    "large": {"source_sha": "c1ab55bb8c2d949e", "warp_instructions": 5642500746.0},
+    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 258,788,803 + 229,095,856 +
+    # 442,675,200 + 957,440 + 1,158 + 1,003,557 + 1,701,416 + 508,928
+    "mid": {"source_sha": "fdee5839023134c7", "warp_instructions": 1385650166.0},
+    # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,037,389,196 +
+    # 918,354,416 (y, 256-block lines) + 1,701,677,056 (z, 449-block lines) + 957,440 +
+    # 1,158 + 4,023,119 + 6,536,912 + 2,040,256
+    "large": {"source_sha": "fdee5839023134c7", "warp_instructions": 5485083209.0},
 }
 
 
