@@ -71,13 +71,13 @@ NCU_TRAFFIC = {
 # kernel code it was taken on; the precompute's ALU roofline is reported as null once that
 # code has changed.
 NCU_PRECOMPUTE_INST = {
-    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 258,788,803 + 229,095,856 +
-    # 442,675,200 + 957,440 + 1,158 + 1,003,557 + 1,701,416 + 508,928
-    "mid": {"source_sha": "fdee5839023134c7", "warp_instructions": 1385650166.0},
-    # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,037,389,196 +
-    # 918,354,416 (y, 256-block lines) + 1,701,677,056 (z, 449-block lines) + 957,440 +
-    # 1,158 + 4,023,119 + 6,536,912 + 2,040,256
-    "large": {"source_sha": "fdee5839023134c7", "warp_instructions": 5485083209.0},
+    # mid (1024 x 1024 x 448, K = 64): 10,112 + 450,907,696 + 265,555,395 + 229,095,856 +
+    # 442,675,200 + 957,440 + 1,158 + 1,026,181 + 1,701,416 + 508,928
+    "mid": {"source_sha": "b8d26ebe65fb68c4", "warp_instructions": 1392439382.0},
+    # large (1024 x 1024 x 1795, K = 64): 10,112 + 1,814,093,544 + 1,064,515,980 +
+    # 918,354,416 (y, 256-block lines) + 1,701,677,056 (z, 449-block lines) +
+    # 957,440 + 1,158 + 4,113,817 + 6,536,912 + 2,040,256
+    "large": {"source_sha": "b8d26ebe65fb68c4", "warp_instructions": 5512300691.0},
 }
 
 

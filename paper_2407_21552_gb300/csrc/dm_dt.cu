@@ -176,16 +176,19 @@ __device__ __forceinline__ void xpass_mask_row(const uint64_t* __restrict__ mask
     int16_t* s_prev = reinterpret_cast<int16_t*>(s_mem + cap * nw);
     int16_t* s_next = s_prev + cap * nw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ uint64_t s_por[kThreads / 32];                // the row's OR, per warp
     const int64_t rbase = int64_t(row) * xg.gx;
     const int nh = 2 * nw;                                   // 16-block items per bit line
 #pragma unroll 1
     for (int w = 0; w < W; ++w) {
         const int np = min(64, K - w * 64);
         if (w) __syncthreads();                              // previous chunk consumed
+        uint64_t por = 0;                                    // this thread's mask words ORed
         for (int x0 = 0; x0 < xg.gx; x0 += kThreads) {
             if (x0 + warp * 32 >= xg.gx) continue;           // warp-uniform: no blocks here
             const int x = x0 + tid;
             const uint64_t m = x < xg.gx ? mask[(rbase + x) * W + w] : 0;
+            por |= m;
             const int wi = (x0 >> 5) + warp;
             // bit lines of 32 blocks: lane q receives partition q's word (and 32 + q's)
             const uint32_t lo = warp_transpose32(uint32_t(m), lane);
@@ -195,21 +198,19 @@ __device__ __forceinline__ void xpass_mask_row(const uint64_t* __restrict__ mask
                 if (lane + 32 < np) s_bits[(lane + 32) * nw + wi] = hi;
             }
         }
+        if (xg.proj) {                                       // uniform
+            const unsigned lo = __reduce_or_sync(0xFFFFFFFFu, unsigned(por));
+            const unsigned hi = __reduce_or_sync(0xFFFFFFFFu, unsigned(por >> 32));
+            if (lane == 0) s_por[warp] = (uint64_t(hi) << 32) | lo;
+        }
         __syncthreads();
-        bool occ = false;                                    // map tid occupies the row
-        for (int q = tid; q < np; q += kThreads) {
+        if (xg.proj && tid == 0) {
+            uint64_t all = 0;
+            for (int k = 0; k < kThreads / 32; ++k) all |= s_por[k];
+            xg.proj[int64_t(row) * W + w] = all;
+        }
+        for (int q = tid; q < np; q += kThreads)
             nearest_tables(s_bits + q * nw, nw, s_prev + q * nw, s_next + q * nw);
-            if (xg.proj) {
-                uint32_t any = 0;
-                for (int wi = 0; wi < nw; ++wi) any |= s_bits[q * nw + wi];
-                occ = any != 0u;
-            }
-        }
-        if (xg.proj) {                                       // uniform; np <= 64 < kThreads
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
-            if (lane == 0 && warp < 2)
-                reinterpret_cast<uint32_t*>(xg.proj + int64_t(row) * W + w)[warp] = bal;
-        }
         __syncthreads();
         for (int it = tid; it < np * nh; it += kThreads) {
             const int q = it / nh, hw = it - q * nh;
