@@ -59,6 +59,18 @@ MUTANTS = [
     ("DT without its backward pass",
      "int after = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));",
      "int after = 0;"),
+    ("footprint loses one apron voxel on the high side",
+     "*hi = c * b + b - 1 + a;",
+     "*hi = c * b + b - 2 + a;"),
+    ("forward DT pass wraps from the end of a row to the start of the next",
+     "if (nz < 0 || ny < 0 || ny >= gy || nx < 0 || nx >= gx) continue;",
+     "if (nz < 0 || ny < 0 || ny >= gy || nx < 0) continue;"),
+    ("shell search reports one more than the radius",
+     "if (occ[(nz * gy + ny) * gx + nx]) return (int)r;",
+     "if (occ[(nz * gy + ny) * gx + nx]) return (int)r + 1;"),
+    ("shell search gives up one radius early",
+     "for (int64_t r = 0; r < 255; ++r) {",
+     "for (int64_t r = 0; r < 254; ++r) {"),
     ("an empty S combines to 0 instead of 255",
      "for (int64_t i = 0; i < G; ++i) out[i] = 255;",
      "for (int64_t i = 0; i < G; ++i) out[i] = 0;"),

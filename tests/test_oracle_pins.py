@@ -158,6 +158,19 @@ def test_dt_at_matches_library_dt():
             assert oracle.dt_at(occ, x, y, z) == ref[z, y, x]
 
 
+def test_dt_at_clamps_at_255_on_long_line():
+    # one occupied block at the end of a 600-block line: the shell search must reach
+    # radius 254 and report 255 beyond it, like the full transform
+    occ = np.zeros((1, 1, 600), np.uint8)
+    occ[0, 0, 0] = 1
+    for x, want in [(0, 0), (1, 1), (253, 253), (254, 254), (255, 255), (599, 255)]:
+        assert oracle.dt_at(occ, x, 0, 0) == want, x
+    occ_z = np.zeros((600, 1, 1), np.uint8)
+    occ_z[599, 0, 0] = 1
+    for z, want in [(599, 0), (345, 254), (344, 255)]:
+        assert oracle.dt_at(occ_z, 0, 0, z) == want, z
+
+
 def test_dt_lipschitz_and_zero_iff_occupied():
     rng = np.random.default_rng(4)
     occ = (rng.uniform(size=(10, 12, 14)) < 0.02).astype(np.uint8)
